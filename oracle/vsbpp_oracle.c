@@ -1,0 +1,407 @@
+/*
+ * vsbpp_oracle.c -- plain, slow, single-threaded CPU oracle for the hybrid
+ * P-system heuristics of Alenezi, Aboelfotoh, Albdaiwi & Almulla,
+ * "Heuristics for the Variable Sized Bin Packing Problem Using a Hybrid
+ * P System and CUDA Architecture" (arXiv:1602.08735).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark do.  It shares no code, header or constant table with
+ * the CUDA path: every constant below is restated here on purpose.
+ *
+ * What it computes (one function per passage of the paper):
+ *   - the VSBPP instance and objective (Section 1 "Formal Definition",
+ *     Section 6.1): items w_1..w_m, bin types B_1 > ... > B_n > 0, unlimited
+ *     supply, minimise the total capacity of the used bins;
+ *   - Rule 1 / step 1 of Section 6.3: the item list is split into sublists;
+ *     each sublist is an independent membrane system with its own bins
+ *     (Rule 2 gives every thread its own bin membranes);
+ *   - Rules 3-6 of Section 6.3: items leave the sublist one per step, are
+ *     tagged with a criterion FF/BF/WF (Section 1 defines the three), enter
+ *     the chosen bin membrane (Rule 4, whose polarity is the bin load), and a
+ *     bin whose load reaches half its capacity divides off one empty bin of
+ *     the same type (Rule 5);
+ *   - Section 6.4: the second heuristic packs every permutation of each small
+ *     sublist and keeps the cheapest (ties: lowest permutation index);
+ *   - the "second kernel" of Section 7: total capacity of used bins.
+ *
+ * Readings taken where the paper is silent or garbled (each restated next to
+ * the code that implements it):
+ *   G1  sublists are contiguous chunks of the list, in list order;
+ *   G2  items leave a sublist in list order, one per step;
+ *   G3  by default no bin is open at the start; preopen=1 gives the literal
+ *       Rule 2 (one empty bin of each type, types in order);
+ *   G4  when no open bin has room, a bin of the smallest type that holds the
+ *       item is opened and appended (the paper has no rule for this case);
+ *   G5  Rule 4 fit test: residual capacity >= w (Remark 2 of Section 6.3);
+ *   G6  ties in FF/BF/WF go to the lowest creation index (Section 1);
+ *   G7  Rule 5 fires once per bin, when 2*load first reaches >= B (real half);
+ *   G8  "used" bins are those with load > 0; bin ids are dense in creation
+ *       order among used bins, sublists concatenated in order;
+ *   G9  permutations are enumerated in lexicographic order of positions,
+ *       rank 0 = identity;
+ *   G10 ties between permutations go to the lowest rank;
+ *   G12 the RANDOM criterion draws c = SplitMix64(seed, key) mod 3 with
+ *       0=FF, 1=BF, 2=WF; key = item index (first heuristic) or
+ *       (sublist*720 + rank)*8 + step (second heuristic).  SplitMix64 is the
+ *       published generator of Steele, Lea & Flood (OOPSLA 2014): the
+ *       key-th output (0-based) of the stream seeded with `seed`.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* status codes (same numeric values as the library's public interface) */
+#define OR_OK       0
+#define OR_EINVAL  (-1)
+#define OR_ETOOBIG (-2)
+#define OR_ENOMEM  (-3)
+
+/* criteria and heuristics */
+#define OR_FF 0
+#define OR_BF 1
+#define OR_WF 2
+#define OR_RANDOM 3
+#define OR_H1 1
+#define OR_H2 2
+
+#define OR_H2_DEFAULT_SUBLIST 5
+#define OR_H2_MAX_SUBLIST 6
+
+/* ------------------------------------------------------------------------ */
+/* SplitMix64 (Steele, Lea & Flood 2014): state advances by the golden-ratio  */
+/* increment; the output is the state passed through the variant-13 mixer.   */
+/* The key-th output of the stream seeded with `seed` is therefore the mix of */
+/* seed + (key+1)*gamma.                                                      */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t key)
+{
+    uint64_t z = seed + (key + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static int32_t or_random_criterion(uint64_t seed, uint64_t key)
+{
+    return (int32_t)(oracle_splitmix64(seed, key) % 3u);
+}
+
+/* A bin membrane (b, x, B_type, I) with polarity = load (Rule 4). */
+typedef struct {
+    int64_t load;
+    int32_t type;
+} or_bin;
+
+/*
+ * One membrane system of Section 6.3 packing the sequence seq[0..k) with the
+ * criterion crit[q] for step q.  bins must have room for 2k + n entries (each
+ * step appends at most one bin by G4 and one by Rule 5; preopen adds n).
+ * raw[q] receives the creation index of the bin that took step q's item.
+ * Returns the number of bins created.
+ */
+static int64_t or_membrane_run(const int32_t *seq, const int32_t *crit, int64_t k,
+                               const int32_t *B, int32_t n, int32_t preopen,
+                               or_bin *bins, int64_t *raw)
+{
+    int64_t nb = 0;
+    if (preopen) {                         /* Rule 2 taken literally (G3) */
+        for (int32_t i = 0; i < n; ++i) {
+            bins[nb].load = 0;
+            bins[nb].type = i;
+            ++nb;
+        }
+    }
+    for (int64_t q = 0; q < k; ++q) {      /* Rule 3: one item per step (G2) */
+        const int64_t w = seq[q];
+        const int32_t c = crit[q];
+        int64_t chosen = -1;
+        int64_t chosen_res = 0;
+        /* Rule 4: every bin membrane tests whether w fits (G5); the
+         * criterion picks one, lowest creation index on ties (G6). */
+        for (int64_t x = 0; x < nb; ++x) {
+            const int64_t res = (int64_t)B[bins[x].type] - bins[x].load;
+            if (res < w)
+                continue;
+            if (chosen < 0 ||
+                (c == OR_BF && res < chosen_res) ||
+                (c == OR_WF && res > chosen_res)) {
+                chosen = x;
+                chosen_res = res;
+            }
+            if (c == OR_FF)
+                break;
+        }
+        if (chosen < 0) {
+            /* G4: nothing fits; open the smallest type whose capacity holds w.
+             * Types are sorted by decreasing capacity, so that is the last
+             * index i with B[i] >= w. */
+            int32_t t = 0;
+            for (int32_t i = 0; i < n; ++i)
+                if (B[i] >= w)
+                    t = i;
+            bins[nb].load = 0;
+            bins[nb].type = t;
+            chosen = nb;
+            ++nb;
+        }
+        {
+            const int64_t cap = B[bins[chosen].type];
+            const int64_t before = bins[chosen].load;
+            const int64_t after = before + w;
+            bins[chosen].load = after;     /* Rule 4: polarity k -> k + w */
+            /* Rule 5 (G7): the bin divides when its load first reaches half
+             * of its capacity, i.e. 2*before < cap <= 2*after. */
+            if (2 * before < cap && cap <= 2 * after) {
+                bins[nb].load = 0;
+                bins[nb].type = bins[chosen].type;
+                ++nb;
+            }
+        }
+        raw[q] = chosen;
+    }
+    return nb;
+}
+
+/*
+ * Objective of Section 1 over one membrane system (G8): dense[x] receives the
+ * rank of bin x among used bins in creation order (or -1 when unused).
+ * Returns the number of used bins; *cap_sum receives their total capacity.
+ */
+static int64_t or_used_bins(const or_bin *bins, int64_t nb, const int32_t *B,
+                            int64_t *dense, int64_t *cap_sum)
+{
+    int64_t used = 0, sum = 0;
+    for (int64_t x = 0; x < nb; ++x) {
+        if (bins[x].load > 0) {
+            dense[x] = used++;
+            sum += B[bins[x].type];
+        } else {
+            dense[x] = -1;
+        }
+    }
+    *cap_sum = sum;
+    return used;
+}
+
+/* Lexicographic successor of a permutation (Narayana Pandita's method).
+ * Returns 0 when p is the last permutation. */
+static int or_next_permutation(int32_t *p, int32_t k)
+{
+    int32_t i = k - 2;
+    while (i >= 0 && p[i] >= p[i + 1])
+        --i;
+    if (i < 0)
+        return 0;
+    int32_t j = k - 1;
+    while (p[j] <= p[i])
+        --j;
+    int32_t t = p[i]; p[i] = p[j]; p[j] = t;
+    for (int32_t a = i + 1, b = k - 1; a < b; ++a, --b) {
+        t = p[a]; p[a] = p[b]; p[b] = t;
+    }
+    return 1;
+}
+
+/* Validation of the instance and parameters (Section 6.1 assumptions). */
+static int or_validate(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                       int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                       int32_t preopen)
+{
+    if (m < 0 || n < 1 || !B || (m > 0 && !w))
+        return OR_EINVAL;
+    if (heuristic != OR_H1 && heuristic != OR_H2)
+        return OR_EINVAL;
+    if (criterion < OR_FF || criterion > OR_RANDOM)
+        return OR_EINVAL;
+    if (preopen != 0 && preopen != 1)
+        return OR_EINVAL;
+    if (sublist_size < 0)
+        return OR_EINVAL;
+    if (heuristic == OR_H2 && sublist_size > OR_H2_MAX_SUBLIST)
+        return OR_EINVAL;
+    for (int32_t i = 0; i < n; ++i) {
+        if (B[i] <= 0)
+            return OR_EINVAL;
+        if (i > 0 && B[i] >= B[i - 1])
+            return OR_EINVAL;          /* B_1 > B_2 > ... > B_n > 0 */
+    }
+    for (int64_t j = 0; j < m; ++j) {   /* first offending item decides */
+        if (w[j] < 1)
+            return OR_EINVAL;
+        if (w[j] > B[0])
+            return OR_ETOOBIG;          /* w_max <= B_1 is assumed */
+    }
+    return OR_OK;
+}
+
+/*
+ * Pack one instance.  bin_of_item[m] receives dense bin ids, bin_type[<= m]
+ * receives the 0-based type of each used bin (0 = largest capacity).
+ */
+int oracle_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                int32_t preopen, uint64_t seed,
+                int32_t *bin_of_item, int32_t *bin_type,
+                int64_t *num_bins, int64_t *total_capacity)
+{
+    if (num_bins) *num_bins = 0;
+    if (total_capacity) *total_capacity = 0;
+    int rc = or_validate(w, m, B, n, heuristic, criterion, sublist_size, preopen);
+    if (rc != OR_OK)
+        return rc;
+    if (m == 0)
+        return OR_OK;
+
+    int64_t s;
+    if (heuristic == OR_H1)
+        s = sublist_size == 0 ? m : sublist_size;        /* default: one system */
+    else
+        s = sublist_size == 0 ? OR_H2_DEFAULT_SUBLIST : sublist_size;
+    if (s > m)
+        s = m;
+
+    const int64_t bin_room = 2 * s + n;
+    or_bin *bins = (or_bin *)malloc(sizeof(or_bin) * (size_t)bin_room);
+    int64_t *raw = (int64_t *)malloc(sizeof(int64_t) * (size_t)s);
+    int64_t *dense = (int64_t *)malloc(sizeof(int64_t) * (size_t)bin_room);
+    int32_t *seq = (int32_t *)malloc(sizeof(int32_t) * (size_t)s);
+    int32_t *crit = (int32_t *)malloc(sizeof(int32_t) * (size_t)s);
+    int64_t *best_item_bin = (int64_t *)malloc(sizeof(int64_t) * (size_t)s);
+    int32_t *best_types = (int32_t *)malloc(sizeof(int32_t) * (size_t)bin_room);
+    if (!bins || !raw || !dense || !seq || !crit || !best_item_bin || !best_types) {
+        free(bins); free(raw); free(dense); free(seq); free(crit);
+        free(best_item_bin); free(best_types);
+        return OR_ENOMEM;
+    }
+
+    int64_t bin_offset = 0;      /* bins of earlier sublists (G11) */
+    int64_t total = 0;
+    for (int64_t g = 0; g * s < m; ++g) {
+        const int64_t a = g * s;
+        const int64_t k = (m - a < s) ? (m - a) : s;
+        if (heuristic == OR_H1) {
+            for (int64_t q = 0; q < k; ++q) {
+                seq[q] = w[a + q];
+                crit[q] = criterion == OR_RANDOM
+                              ? or_random_criterion(seed, (uint64_t)(a + q))
+                              : criterion;
+            }
+            const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw);
+            int64_t cap_sum = 0;
+            const int64_t used = or_used_bins(bins, nb, B, dense, &cap_sum);
+            for (int64_t q = 0; q < k; ++q)
+                bin_of_item[a + q] = (int32_t)(bin_offset + dense[raw[q]]);
+            for (int64_t x = 0; x < nb; ++x)
+                if (dense[x] >= 0)
+                    bin_type[bin_offset + dense[x]] = bins[x].type;
+            bin_offset += used;
+            total += cap_sum;
+        } else {
+            /* Section 6.4: every permutation of the sublist packs with
+             * Rules 2-6; the cheapest one wins, lowest rank on ties. */
+            int32_t perm[OR_H2_MAX_SUBLIST];
+            for (int32_t q = 0; q < (int32_t)k; ++q)
+                perm[q] = q;
+            int64_t best_total = -1, best_used = 0;
+            int64_t rank = 0;
+            do {
+                for (int64_t q = 0; q < k; ++q) {
+                    seq[q] = w[a + perm[q]];
+                    crit[q] = criterion == OR_RANDOM
+                                  ? or_random_criterion(
+                                        seed, (uint64_t)((g * 720 + rank) * 8 + q))
+                                  : criterion;
+                }
+                const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw);
+                int64_t cap_sum = 0;
+                const int64_t used = or_used_bins(bins, nb, B, dense, &cap_sum);
+                if (best_total < 0 || cap_sum < best_total) {
+                    best_total = cap_sum;
+                    best_used = used;
+                    for (int64_t q = 0; q < k; ++q)
+                        best_item_bin[perm[q]] = dense[raw[q]];
+                    for (int64_t x = 0; x < nb; ++x)
+                        if (dense[x] >= 0)
+                            best_types[dense[x]] = bins[x].type;
+                }
+                ++rank;
+            } while (or_next_permutation(perm, (int32_t)k));
+            for (int64_t q = 0; q < k; ++q)
+                bin_of_item[a + q] = (int32_t)(bin_offset + best_item_bin[q]);
+            for (int64_t d = 0; d < best_used; ++d)
+                bin_type[bin_offset + d] = best_types[d];
+            bin_offset += best_used;
+            total += best_total;
+        }
+    }
+
+    free(bins); free(raw); free(dense); free(seq); free(crit);
+    free(best_item_bin); free(best_types);
+    if (num_bins) *num_bins = bin_offset;
+    if (total_capacity) *total_capacity = total;
+    return OR_OK;
+}
+
+/*
+ * Exact VSBPP optimum (Section 1 "Formal Definition") by dynamic programming
+ * over item subsets: a packing is a partition of the items into groups, each
+ * group costing the smallest capacity B_i that holds its weight.  With
+ * f(S) = min over groups T containing the lowest item of S of
+ * cap(sum T) + f(S \ T), OPT = f(all items).  O(3^m); m <= 20 accepted.
+ * Returns -1 on invalid input.
+ */
+int64_t oracle_opt_bruteforce(const int32_t *w, int32_t m, const int32_t *B, int32_t n)
+{
+    if (m < 0 || m > 20 || n < 1)
+        return -1;
+    if (m == 0)
+        return 0;
+    const uint32_t full = (1u << m) - 1u;
+    int64_t *sum = (int64_t *)malloc(sizeof(int64_t) * ((size_t)full + 1));
+    int64_t *cap = (int64_t *)malloc(sizeof(int64_t) * ((size_t)full + 1));
+    int64_t *f = (int64_t *)malloc(sizeof(int64_t) * ((size_t)full + 1));
+    if (!sum || !cap || !f) {
+        free(sum); free(cap); free(f);
+        return -1;
+    }
+    sum[0] = 0;
+    for (uint32_t S = 1; S <= full; ++S) {
+        uint32_t low = S & (~S + 1u);
+        int32_t bit = 0;
+        while ((1u << bit) != low)
+            ++bit;
+        sum[S] = sum[S ^ low] + w[bit];
+    }
+    for (uint32_t S = 0; S <= full; ++S) {
+        cap[S] = -1;                            /* -1: no type holds it */
+        for (int32_t i = n - 1; i >= 0; --i) {  /* smallest capacity first */
+            if ((int64_t)B[i] >= sum[S]) {
+                cap[S] = B[i];
+                break;
+            }
+        }
+    }
+    const int64_t INF = INT64_MAX / 4;
+    f[0] = 0;
+    for (uint32_t S = 1; S <= full; ++S) {
+        const uint32_t low = S & (~S + 1u);
+        const uint32_t rest = S ^ low;
+        int64_t best = INF;
+        uint32_t sub = rest;
+        for (;;) {
+            const uint32_t T = sub | low;
+            if (cap[T] > 0 && f[S ^ T] < INF) {
+                const int64_t v = cap[T] + f[S ^ T];
+                if (v < best)
+                    best = v;
+            }
+            if (sub == 0)
+                break;
+            sub = (sub - 1u) & rest;
+        }
+        f[S] = best;
+    }
+    const int64_t out = f[full] >= INF ? -1 : f[full];
+    free(sum); free(cap); free(f);
+    return out;
+}

@@ -1,0 +1,286 @@
+"""Pins that tie the CPU oracle to something other than itself.
+
+Each ``pin_*`` function takes an ``oracle.OracleLib`` and raises
+AssertionError when the oracle disagrees with what the paper or the
+mathematics fixes:
+
+  * hand-worked packings (tests/golden/hand_examples.json, traced by hand from
+    Section 6.3 Rules 2-6, Section 6.4 and the FF/BF/WF definitions of
+    Section 1);
+  * the published SplitMix64 test vectors (RANDOM criterion, Rule 3);
+  * with one bin type (n = 1, classical bin packing, Section 1), FF and BF
+    reduce to the textbook First-Fit and Best-Fit written out below in a
+    different form (no empty bins, no division rule);
+  * the exact optimum from an independent set-partition enumeration, and
+    heuristic >= optimum;
+  * closed forms: a single item costs min{B_i >= w}; m items of weight B_1
+    cost m*B_1;
+  * the second heuristic equals the cheapest permutation, enumerated here with
+    itertools (Section 6.4);
+  * invariants of any packing (each item once, no bin over capacity, total =
+    sum of used capacities >= sum of weights).
+
+The same functions run against copies of the oracle with planted mistakes
+(tests/test_oracle_mutants.py) to show that each plausible slip is caught.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load_golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ----------------------------------------------------------------- textbook
+def textbook_first_fit(w, C):
+    """Classical First-Fit: put each item in the first opened bin with room,
+    else open a new bin.  Returns (bin index per item, number of bins)."""
+    loads = []
+    out = []
+    for x in w:
+        for i, ld in enumerate(loads):
+            if ld + x <= C:
+                loads[i] += x
+                out.append(i)
+                break
+        else:
+            loads.append(x)
+            out.append(len(loads) - 1)
+    return out, len(loads)
+
+
+def textbook_best_fit(w, C):
+    """Classical Best-Fit: the opened bin with the least room that still holds
+    the item (lowest index on ties), else a new bin."""
+    loads = []
+    out = []
+    for x in w:
+        best, room = -1, None
+        for i, ld in enumerate(loads):
+            r = C - ld
+            if r >= x and (room is None or r < room):
+                best, room = i, r
+        if best < 0:
+            loads.append(x)
+            out.append(len(loads) - 1)
+        else:
+            loads[best] += x
+            out.append(best)
+    return out, len(loads)
+
+
+def set_partition_optimum(w, B):
+    """Exact VSBPP optimum by enumerating every set partition of the items
+    (restricted growth strings); cost of a block = smallest B_i >= its sum."""
+    m = len(w)
+    if m == 0:
+        return 0
+    caps = sorted(B)
+    best = None
+    labels = [0] * m
+
+    def cost(lbl):
+        sums = {}
+        for x, l in zip(w, lbl):
+            sums[l] = sums.get(l, 0) + x
+        tot = 0
+        for s in sums.values():
+            c = next((c for c in caps if c >= s), None)
+            if c is None:
+                return None
+            tot += c
+        return tot
+
+    def rec(i, k):
+        nonlocal best
+        if i == m:
+            c = cost(labels)
+            if c is not None and (best is None or c < best):
+                best = c
+            return
+        for l in range(k + 1):
+            labels[i] = l
+            rec(i + 1, max(k, l + 1))
+
+    rec(0, 0)
+    return best
+
+
+def check_packing(w, B, res, m_expected=None):
+    """Invariants every packing must satisfy."""
+    w = np.asarray(w, dtype=np.int64)
+    B = np.asarray(B, dtype=np.int64)
+    assert res.status == 0
+    m = w.shape[0]
+    boi = np.asarray(res.bin_of_item, dtype=np.int64)
+    bty = np.asarray(res.bin_type, dtype=np.int64)
+    assert boi.shape[0] == m
+    assert bty.shape[0] == res.num_bins
+    if m == 0:
+        assert res.num_bins == 0 and res.total == 0
+        return
+    assert boi.min() >= 0 and boi.max() < res.num_bins
+    loads = np.bincount(boi, weights=w, minlength=res.num_bins)
+    assert np.all(loads > 0), "every reported bin holds an item"
+    assert np.all(bty >= 0) and np.all(bty < B.shape[0])
+    assert np.all(loads <= B[bty]), "no bin over capacity"
+    assert res.total == int(B[bty].sum())
+    assert res.total >= int(w.sum())
+    assert res.num_bins <= m
+    # dense ids in creation order: first appearance of each id is increasing
+    # within one membrane system; ids are a permutation-free labelling.
+    assert np.unique(boi).shape[0] == res.num_bins
+
+
+# --------------------------------------------------------------------- pins
+def pin_hand_examples(lib):
+    d = load_golden("hand_examples.json")
+    for ex in d["examples"]:
+        r = lib.pack(ex["w"], ex["B"], ex["heuristic"], ex["criterion"], ex["sublist_size"],
+                     ex["preopen"], ex["seed"])
+        assert r.status == 0, ex["name"]
+        assert r.bin_of_item.tolist() == ex["bin_of_item"], ex["name"]
+        assert r.bin_type.tolist() == ex["bin_type"], ex["name"]
+        assert r.total == ex["total"], ex["name"]
+        if "opt" in ex:
+            assert lib.opt_bruteforce(ex["w"], ex["B"]) == ex["opt"], ex["name"]
+
+
+def pin_splitmix64(lib):
+    d = load_golden("splitmix64_vectors.json")
+    for k, v in enumerate(d["outputs"]):
+        assert lib.splitmix64(d["seed"], k) == int(v)
+
+
+def pin_textbook_n1(lib, trials=150, seed=11):
+    rng = np.random.default_rng(seed)
+    for t in range(trials):
+        C = int(rng.integers(1, 60))
+        m = int(rng.integers(0, 40))
+        w = rng.integers(1, C + 1, size=m).tolist()
+        for crit, ref in ((0, textbook_first_fit), (1, textbook_best_fit)):
+            r = lib.pack(w, [C], 1, crit)
+            idx, nbins = ref(w, C)
+            assert r.status == 0
+            assert r.bin_of_item.tolist() == idx, (crit, C, w)
+            assert r.num_bins == nbins
+            assert r.total == nbins * C
+
+
+def pin_optimum(lib, trials=60, seed=12):
+    rng = np.random.default_rng(seed)
+    for t in range(trials):
+        m = int(rng.integers(0, 8))
+        n = int(rng.integers(1, 4))
+        B = sorted(rng.choice(np.arange(3, 40), size=n, replace=False).tolist(), reverse=True)
+        w = rng.integers(1, B[0] + 1, size=m).tolist()
+        opt = lib.opt_bruteforce(w, B)
+        assert opt == set_partition_optimum(w, B), (w, B)
+        for h, s in ((1, 0), (2, 0)):
+            for crit in (0, 1, 2):
+                r = lib.pack(w, B, h, crit, s)
+                assert r.total >= opt, (w, B, h, crit)
+
+
+def pin_closed_forms(lib, seed=13):
+    rng = np.random.default_rng(seed)
+    for t in range(40):
+        n = int(rng.integers(1, 6))
+        B = sorted(rng.choice(np.arange(1, 500), size=n, replace=False).tolist(), reverse=True)
+        x = int(rng.integers(1, B[0] + 1))
+        want = min(b for b in B if b >= x)
+        for h in (1, 2):
+            for crit in (0, 1, 2, 3):
+                r = lib.pack([x], B, h, crit, 0, 0, t)
+                assert r.total == want and r.num_bins == 1
+                assert r.bin_type.tolist() == [B.index(want)]
+        m = int(rng.integers(1, 30))
+        r = lib.pack([B[0]] * m, B, 1, int(rng.integers(0, 3)))
+        assert r.total == m * B[0] and r.num_bins == m
+        assert r.bin_of_item.tolist() == list(range(m))
+        assert r.bin_type.tolist() == [0] * m
+
+
+def pin_h2_is_best_permutation(lib, trials=60, seed=14):
+    rng = np.random.default_rng(seed)
+    for t in range(trials):
+        k = int(rng.integers(1, 6))
+        n = int(rng.integers(1, 4))
+        B = sorted(rng.choice(np.arange(2, 30), size=n, replace=False).tolist(), reverse=True)
+        w = rng.integers(1, B[0] + 1, size=k).tolist()
+        crit = int(rng.integers(0, 3))
+        pre = int(rng.integers(0, 2))
+        best = None
+        for perm in itertools.permutations(range(k)):       # lexicographic
+            seq = [w[p] for p in perm]
+            r = lib.pack(seq, B, 1, crit, 0, pre)
+            if best is None or r.total < best[0]:
+                item_bin = [0] * k
+                for q, p in enumerate(perm):
+                    item_bin[p] = int(r.bin_of_item[q])
+                best = (r.total, item_bin, r.bin_type.tolist())
+        r2 = lib.pack(w, B, 2, crit, k, pre)
+        assert r2.total == best[0], (w, B, crit)
+        assert r2.bin_of_item.tolist() == best[1], (w, B, crit)
+        assert r2.bin_type.tolist() == best[2]
+
+
+def pin_invariants(lib, trials=200, seed=15):
+    rng = np.random.default_rng(seed)
+    for t in range(trials):
+        m = int(rng.integers(0, 60))
+        n = int(rng.integers(1, 8))
+        cap_hi = int(rng.choice([20, 100, 1000, 40000]))
+        B = sorted(rng.choice(np.arange(1, cap_hi + 1), size=min(n, cap_hi), replace=False).tolist(),
+                   reverse=True)
+        w = rng.integers(1, B[0] + 1, size=m).tolist()
+        h = int(rng.integers(1, 3))
+        s = int(rng.integers(0, 7)) if h == 2 else int(rng.choice([0, 0, 1, 3, 10]))
+        crit = int(rng.integers(0, 4))
+        pre = int(rng.integers(0, 2))
+        r = lib.pack(w, B, h, crit, s, pre, t)
+        check_packing(w, B, r)
+
+
+def pin_errors(lib):
+    B = [100, 50]
+    assert lib.pack([1, 2], [], 1, 0).status == -1          # n = 0
+    assert lib.pack([1, 2], [50, 100], 1, 0).status == -1   # not decreasing
+    assert lib.pack([1, 2], [50, 50], 1, 0).status == -1    # not strictly
+    assert lib.pack([1, 2], [50, 0], 1, 0).status == -1     # B_n must be > 0
+    assert lib.pack([0, 2], B, 1, 0).status == -1           # w >= 1
+    assert lib.pack([101], B, 1, 0).status == -2            # w <= B_1
+    assert lib.pack([0, 101], B, 1, 0).status == -1         # first offender decides
+    assert lib.pack([101, 0], B, 1, 0).status == -2
+    assert lib.pack([1], B, 3, 0).status == -1              # heuristic id
+    assert lib.pack([1], B, 1, 4).status == -1              # criterion id
+    assert lib.pack([1], B, 1, 0, -1).status == -1          # sublist size
+    assert lib.pack([1], B, 2, 0, 7).status == -1           # H2 sublist <= 6
+    assert lib.pack([1], B, 1, 0, 0, 2).status == -1        # preopen flag
+    r = lib.pack([], B, 1, 0)
+    assert r.status == 0 and r.num_bins == 0 and r.total == 0
+
+
+ALL_PINS = [pin_hand_examples, pin_splitmix64, pin_textbook_n1, pin_optimum,
+            pin_closed_forms, pin_h2_is_best_permutation, pin_invariants, pin_errors]
+
+
+def failing_pins(lib):
+    """Names of the pins this oracle copy fails (used by the mutant tests)."""
+    bad = []
+    for p in ALL_PINS:
+        try:
+            p(lib)
+        except AssertionError:
+            bad.append(p.__name__)
+        except Exception as e:     # a crash counts as a detected mistake too
+            bad.append(f"{p.__name__}:{type(e).__name__}")
+    return bad

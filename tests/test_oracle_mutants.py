@@ -1,0 +1,74 @@
+"""Planted mistakes in a copy of the oracle (CPU only): each plausible slip
+-- a wrong tie-break, a misread rule, a dropped term, an off-by-one key --
+must make at least one pin in tests/oracle_pins.py fail.  The mistakes are
+planted by editing a temporary copy of the C source; the real oracle is
+never modified."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+TESTS = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(TESTS)
+
+# Runs the pins against one compiled copy in a child process, so a planted
+# mistake that corrupts memory (e.g. reporting more bins than there is room
+# for) is reported as a crash instead of taking the test session down.
+_RUNNER = (
+    "import json, sys; sys.path[:0] = [%r, %r]\n"
+    "import oracle, oracle_pins as P\n"
+    "print(json.dumps(P.failing_pins(oracle.OracleLib(sys.argv[1]))))\n"
+) % (ROOT, TESTS)
+
+
+def failing_pins_isolated(path):
+    r = subprocess.run([sys.executable, "-c", _RUNNER, path], capture_output=True, text=True,
+                       timeout=600)
+    if r.returncode != 0:
+        return [f"crashed(rc={r.returncode})"]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+MUTANTS = {
+    "bf_tie_highest_index": ("(c == OR_BF && res < chosen_res)", "(c == OR_BF && res <= chosen_res)"),
+    "wf_tie_highest_index": ("(c == OR_WF && res > chosen_res)", "(c == OR_WF && res >= chosen_res)"),
+    "fit_strict": ("if (res < w)\n                continue;", "if (res <= w)\n                continue;"),
+    "rule5_floor_half": ("if (2 * before < cap && cap <= 2 * after) {",
+                         "if (before < cap / 2 && cap / 2 <= after) {"),
+    "rule5_dropped": ("if (2 * before < cap && cap <= 2 * after) {", "if (0) {"),
+    "rule5_wrong_type": ("bins[nb].type = bins[chosen].type;", "bins[nb].type = 0;"),
+    "fallback_largest_type": ("if (B[i] >= w)\n                    t = i;", "if (B[i] >= w)\n                    t = 0;"),
+    "used_counts_empty_bins": ("if (bins[x].load > 0) {", "if (bins[x].load >= 0) {"),
+    "h2_tie_last_rank": ("if (best_total < 0 || cap_sum < best_total) {",
+                         "if (best_total < 0 || cap_sum <= best_total) {"),
+    "h2_assignment_not_permuted": ("best_item_bin[perm[q]] = dense[raw[q]];",
+                                   "best_item_bin[q] = dense[raw[q]];"),
+    "sublist_offset_dropped": ("bin_of_item[a + q] = (int32_t)(bin_offset + dense[raw[q]]);",
+                               "bin_of_item[a + q] = (int32_t)(dense[raw[q]]);"),
+    "random_key_off_by_one": ("or_random_criterion(seed, (uint64_t)(a + q))",
+                              "or_random_criterion(seed, (uint64_t)(a + q + 1))"),
+    "splitmix_constant_typo": ("0xBF58476D1CE4E5B9ull", "0xBF58476D1CE4E5B8ull"),
+    "preopen_reversed": ("bins[nb].type = i;\n            ++nb;", "bins[nb].type = n - 1 - i;\n            ++nb;"),
+    "too_big_against_smallest": ("if (w[j] > B[0])", "if (w[j] > B[n - 1])"),
+    "opt_largest_capacity": ("for (int32_t i = n - 1; i >= 0; --i) {  /* smallest capacity first */",
+                             "for (int32_t i = 0; i < n; ++i) {"),
+    "total_counts_loads": ("sum += B[bins[x].type];", "sum += bins[x].load;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    path = oracle.compile_variant(src.replace(old, new), str(tmp_path / f"mut_{name}.so"))
+    bad = failing_pins_isolated(path)
+    assert bad, f"planted mistake {name} passed every pin"
+
+
+def test_unmodified_copy_passes(tmp_path):
+    path = oracle.compile_variant(oracle.source_text(), str(tmp_path / "same.so"))
+    assert failing_pins_isolated(path) == []
