@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Items packed per second on the batched VSBPP workload, on GB300.
+
+Workload (config 3): 4096 independent instances in one batch, m per instance
+log-uniform in [100, 10^4], n in {3,5,7}, capacities distinct integers in
+[20, 1000] sorted descending, weights uniform in [1, B_1] (seeded synthetic
+data standing in for the paper's benchmark files).
+
+One step = one pass of the whole hot path over the batch: the first
+heuristic (Section 6.3) with FF, BF and WF, and the second heuristic
+(Section 6.4, 5-item sublists, BF), each a CUDA-graph replay of the batched
+persistent launch.  items_per_step = 4 * sum(m).  L2 is flushed (a 256 MiB
+write) before every timed step, outside the timed region.
+
+Also reported: the same step through the plain path (one kernel launch per
+instance), end-to-end throughput with host buffers (copies timed), the
+fit-test roofline of the dominant kernel, SM clocks sampled during the timed
+region, and the CPU oracle on a bounded sample on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PASSES = [("H1-FF", 1, 0, 0), ("H1-BF", 1, 1, 0), ("H1-WF", 1, 2, 0), ("H2-BF", 2, 1, 5)]
+# kernels one step launches: three first-heuristic passes x (validate, order,
+# scatter, large/small/wide packing kernels) + second heuristic (validate,
+# sublist scan, permutation kernel, compose)
+LAUNCHES_PER_STEP = 3 * 6 + 4
+WORKLOAD = "config3: 4096 VSBPP instances, m log-uniform [100,1e4], n in {3,5,7}, B in [20,1000], w~U[1,B1]"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1024, help="instances in the oracle sample")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                                 else ".", f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        try:
+            self.f.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+            os.remove(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for k, nm in enumerate(names):
+                    if r[4 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if sm:
+            out.update(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), samples=len(sm),
+                       reasons=sorted(reasons))
+        return out
+
+
+# ------------------------------------------------------------------ oracle
+def cpu_baseline(batch, sample_n: int, seed: int = 123):
+    """The oracle, as it stands, on a bounded random sample of the workload,
+    one instance per host thread across all cores."""
+    import oracle
+    from paper_1602_08735_gb300 import instances as I
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(batch.N, size=min(sample_n, batch.N), replace=False))
+    sub = batch.subset(idx)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    for (_, h, c, s) in PASSES:
+        oracle.pack_many(sub.w_all, sub.w_off, sub.B_all, sub.B_off, h, c, s, 0, 0, nthreads=cores)
+    dt = time.perf_counter() - t0
+    items = 4 * sub.total_items
+    return {"value": items / dt, "unit": "items/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(idx)} of {batch.N} instances ({sub.total_items} items) x 4 passes "
+                      f"(H1 FF/BF/WF, H2 BF), {dt:.2f} s wall"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1602_08735_gb300 import instances as I
+    batch = I.config3(seed=3, N=args.instances)
+    sample_n = min(args.cpu_sample, batch.N)
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(7)
+    times, items = [], 0
+    for k in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(batch.N, size=sample_n, replace=False))
+        sub = batch.subset(idx)
+        t0 = time.perf_counter()
+        for (_, h, c, s) in PASSES:
+            oracle.pack_many(sub.w_all, sub.w_off, sub.B_all, sub.B_off, h, c, s, 0, 0)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            items += 4 * sub.total_items
+    value = items / sum(times)
+    cores = os.cpu_count() or 1
+    line = {
+        "impl": "reference", "metric": "items packed/s", "value": value, "unit": "items/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances": batch.N, "sample_instances_per_step": sample_n,
+                   "passes": [p[0] for p in PASSES]},
+        "cpu_baseline": {"value": value, "unit": "items/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample_n} random instances of {batch.N} per step x 4 passes"},
+        "e2e": {"value": value, "unit": "items/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_1602_08735_gb300 import build as B
+    from paper_1602_08735_gb300 import instances as I
+    from paper_1602_08735_gb300 import native
+
+    B.build()
+    native.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    batch = I.config3(seed=3 + rank, N=args.instances)
+    db = native.DeviceBatch.from_host(batch, device=dev)
+    outs = [native.DeviceResult.empty(db.N, db.total_items, device=dev) for _ in PASSES]
+    plans = [native.Plan(db.N, db.total_items, db.max_m, h, c, s) for (_, h, c, s) in PASSES]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        for pl, out in zip(plans, outs):
+            pl.run(db, out, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    for out, (name, *_r) in zip(outs, PASSES):
+        st = out.status[:db.N]
+        assert int((st != 0).sum().item()) == 0, f"{name}: instances failed"
+
+    # fit tests of each first-heuristic pass (counters on, one untimed pass)
+    native.counters_enable(True)
+    native.counters_read(reset=True)
+    fit_tests = {}
+    for (name, h, c, s), out in zip(PASSES, outs):
+        if h != 1:
+            continue
+        rc = native.pack_batch(db, out, h, c, s, stream=stream)
+        assert rc == 0
+        fit_tests[name] = native.counters_read(reset=True)
+    native.counters_enable(False)
+
+    # ---- timed region: device-resident inputs, graph replays, L2 flushed per step
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(PASSES) + 1)] for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            for j, (pl, out) in enumerate(zip(plans, outs)):
+                pl.run(db, out, stream)
+                ev[k][j + 1].record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    pass_ms = np.zeros(len(PASSES))
+    for k in range(args.steps):
+        for j in range(len(PASSES)):
+            pass_ms[j] += ev[k][j].elapsed_time(ev[k][j + 1])
+    pass_ms /= args.steps
+    step_ms_local = float(pass_ms.sum())
+    step_ms = max_over_ranks(step_ms_local, ws)
+    items_per_step_local = 4 * db.total_items
+    items_per_step = sum_over_ranks(items_per_step_local, ws)
+    value = items_per_step / (step_ms / 1e3)
+    clocks = clk.summary()
+
+    # ---- end to end through the public API with host buffers
+    pin = lambda t: t.cpu().pin_memory()
+    h_in = [pin(db.w_all), pin(db.w_off), pin(db.B_all), pin(db.B_off)]
+    h_out = [[torch.empty_like(x, device="cpu").pin_memory() for x in
+              (o.bin_of_item, o.bin_type, o.num_bins, o.total, o.status)] for o in outs]
+    h2d = sum(int(x.numel() * x.element_size()) for x in h_in)
+    d2h = sum(int(x.numel() * x.element_size()) for row in h_out for x in row)
+    e2e_steps = max(1, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for k in range(e2e_steps):
+        flush.zero_()
+        e0.record(stream)
+        for dst, src in zip((db.w_all, db.w_off, db.B_all, db.B_off), h_in):
+            dst.copy_(src, non_blocking=True)
+        step()
+        for o, row in zip(outs, h_out):
+            for src, dst in zip((o.bin_of_item, o.bin_type, o.num_bins, o.total, o.status), row):
+                dst.copy_(src, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms = max_over_ranks(e2e_ms / e2e_steps, ws)
+    e2e_value = items_per_step / (e2e_ms / 1e3)
+
+    # ---- plain path: one launch per instance, one step
+    plain = None
+    if not args.no_plain:
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        flush.zero_()
+        p0.record(stream)
+        for (name, h, c, s), out in zip(PASSES, outs):
+            rc = native.pack_plain(db, out, h, c, s, stream=stream)
+            assert rc == 0
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = max_over_ranks(p0.elapsed_time(p1), ws)
+        plain_value = items_per_step / (plain_ms / 1e3)
+        plain = {"items_per_s": plain_value, "ms_per_step": plain_ms, "speedup_batched_vs_plain": value / plain_value,
+                 "launches_per_step": 2 * db.N * 0 + (3 * (db.N + 3) + 4 * db.N)}
+
+    # ---- roofline of the dominant kernel (first heuristic, BF pass)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    smem_peak_gbs = sms * 128 * f_mhz * 1e6 / 1e9
+    bf_j = [p[0] for p in PASSES].index("H1-BF")
+    bf_bytes = 4.0 * fit_tests["H1-BF"]["fit_tests"]           # one 32-bit slot read per fit test
+    achieved = bf_bytes / (pass_ms[bf_j] / 1e3) / 1e9
+    roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak_gbs, "unit": "GB/s",
+                "frac": achieved / smem_peak_gbs, "traffic": None,
+                "kernel": "h1_pack_kernel (first heuristic, BF pass)",
+                "peak_source": f"derived: {sms} SMs x 128 B/clk shared-memory bandwidth x {f_mhz:.0f} MHz",
+                "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
+                "fit_tests_per_launch": fit_tests["H1-BF"]["fit_tests"],
+                "note": "achieved uses the whole H1-BF pass time (validate/order/scatter included)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(batch, args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": "items packed/s", "value": value, "unit": "items/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instances": db.N, "items_per_step": int(items_per_step),
+                       "passes": [p[0] for p in PASSES], "l2": "flushed before each timed step",
+                       "graph": "each pass is a CUDA-graph replay of the batched persistent launch",
+                       "parallelism": f"instances sharded, {ws} GPU(s), no collective"},
+            "passes_ms": {p[0]: float(t) for p, t in zip(PASSES, pass_ms)},
+            "e2e": {"value": e2e_value, "unit": "items/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "plain": plain,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "fit_tests": fit_tests,
+        }
+        print(json.dumps(line), flush=True)
+    for pl in plans:
+        pl.close()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

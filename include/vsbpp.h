@@ -1,0 +1,306 @@
+/*
+ * vsbpp.h -- C ABI of the GB300 (sm_103a) engine for the hybrid-P-system
+ * heuristics for the Variable Sized Bin Packing Problem (VSBPP) of Alenezi,
+ * Aboelfotoh, Albdaiwi & Almulla (arXiv:1602.08735).
+ *
+ * The problem (Section 1 "Formal Definition", Section 6.1): n bin types with
+ * capacities B_1 > B_2 > ... > B_n > 0 in unlimited supply, a list of m
+ * indivisible items with integer weights 1 <= w_j <= B_1; pack every item and
+ * minimise the total capacity of the bins used.
+ *
+ * The method (Sections 6.2-6.4): a "hybrid P system" in which every open bin
+ * is a membrane whose label carries (bin index, type) and whose polarity
+ * carries the load.  Items leave their sublist membrane one per step (Rule 3)
+ * in list order, every bin membrane tests whether the item fits (Rule 4),
+ * first-fit / best-fit / worst-fit (Section 1) picks one bin, the lowest
+ * creation index winning ties, the bin's load grows by w, and a bin whose
+ * load first reaches half its capacity divides off one empty bin of its type
+ * (Rule 5).  When no bin has room, a bin of the smallest type that holds the
+ * item is opened.  The second heuristic (Section 6.4) packs every
+ * permutation of each small sublist and keeps the cheapest.
+ *
+ * Conventions shared by every entry point:
+ *   - all integers are exact; no floating point anywhere on the path;
+ *   - capacities B[0..n) are given largest first; "type t" is index t into B
+ *     (type 0 = B_1);  1 <= n <= VSBPP_MAX_TYPES;
+ *   - bin ids are dense, 0-based, in creation order among used bins (bins
+ *     with at least one item); with several sublists, the bins of sublist g
+ *     follow those of sublist g-1;
+ *   - a packing of m items uses at most m bins, so bin_type needs room for m
+ *     entries;
+ *   - total_capacity is the sum of B[type] over the used bins (int64);
+ *   - the library never allocates or frees caller-owned buffers; all output
+ *     buffers are written in full on success;
+ *   - no C++ exception crosses this interface; every function returns a
+ *     status code (VSBPP_OK or a negative VSBPP_E* value).
+ *
+ * Validation (identical for every entry point, first failing check wins):
+ *   m >= 0; 1 <= n <= VSBPP_MAX_TYPES; B strictly decreasing and > 0;
+ *   parameters in range; then the items in list order: w_j < 1 gives
+ *   VSBPP_EINVAL, w_j > B_1 gives VSBPP_ETOOBIG.  m = 0 is valid and gives
+ *   zero bins and total 0.  On an error the output arrays of that instance
+ *   are unspecified and num_bins = total = 0.
+ *
+ * Threading: every entry point may be called from any host thread; calls are
+ * serialised internally per process.  Device entry points are asynchronous
+ * with respect to the host and ordered on the caller's stream.
+ */
+#ifndef VSBPP_H
+#define VSBPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VSBPP_VERSION 10000          /* 1.0.0 */
+#define VSBPP_MAX_TYPES 32           /* bin types per instance */
+#define VSBPP_H2_MAX_SUBLIST 6       /* 6! = 720 permutations per sublist */
+
+/* Selection criterion of Rule 3 / Rule 4 (Section 1 defines FF, BF, WF). */
+typedef enum {
+    VSBPP_FF = 0,      /* lowest-index bin with room                          */
+    VSBPP_BF = 1,      /* bin with the least room left that fits; lowest index */
+    VSBPP_WF = 2,      /* bin with the most room left; lowest index            */
+    VSBPP_RANDOM = 3   /* per item, c = SplitMix64(seed, key) mod 3 (0=FF,1=BF,2=WF);
+                          key = item index within the instance (first heuristic)
+                          or (sublist*720 + permutation rank)*8 + step (second) */
+} vsbpp_criterion;
+
+/* The two heuristics of Section 6. */
+typedef enum {
+    VSBPP_H1 = 1,      /* Section 6.3: each sublist packed in list order        */
+    VSBPP_H2 = 2       /* Section 6.4: best permutation of each small sublist   */
+} vsbpp_heuristic;
+
+/* Run parameters.  Zero-initialise and set what you need. */
+typedef struct {
+    int32_t  heuristic;     /* VSBPP_H1 or VSBPP_H2                                     */
+    int32_t  criterion;     /* vsbpp_criterion                                          */
+    int64_t  sublist_size;  /* Rule 1 sublist length s.  H1: 0 means s = m (one membrane
+                               system per instance).  H2: 0 means 5; at most 6.  The
+                               list is cut into contiguous chunks of s items in order.   */
+    int32_t  preopen;       /* 0: no bin open at the start (a bin opens when nothing
+                               fits).  1: literal Rule 2, one empty bin of every type,
+                               types in order, before the first item.                    */
+    int32_t  reserved;      /* must be 0                                                 */
+    uint64_t seed;          /* used by VSBPP_RANDOM only                                 */
+} vsbpp_params;
+
+/* Status codes. */
+enum {
+    VSBPP_OK = 0,
+    VSBPP_EINVAL = -1,      /* malformed instance or parameter                     */
+    VSBPP_ETOOBIG = -2,     /* an item heavier than B_1                            */
+    VSBPP_ENOMEM = -3,      /* device or host memory could not be obtained         */
+    VSBPP_ECUDA = -4,       /* a CUDA call failed (see vsbpp_last_cuda_error)      */
+    VSBPP_ETIMEDOUT = -5,   /* a bounded wait ran out                              */
+    VSBPP_EBUSY = -6,       /* serving: no slot or memory budget available now     */
+    VSBPP_ENOTFOUND = -7,   /* serving: unknown ticket                             */
+    VSBPP_ECAPACITY = -8    /* an instance exceeds a size limit of the entry point */
+};
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *vsbpp_strerror(int code);
+
+/* Library version, VSBPP_VERSION of the build. */
+int vsbpp_version(void);
+
+/* Last CUDA error code seen by the library on this process (cudaError_t as int). */
+int vsbpp_last_cuda_error(void);
+
+/*
+ * vsbpp_pack -- pack one instance held in HOST memory; synchronous.
+ *
+ *   w[m]            item weights (host, int32), list order
+ *   B[n]            capacities, strictly decreasing (host, int32)
+ *   p               run parameters (host); NULL means H1, BF, s = m, no preopen
+ *   bin_of_item[m]  out (host): dense bin id of each item
+ *   bin_type[m]     out (host): type of bin k for k < *num_bins
+ *   num_bins        out (host): number of used bins
+ *   total_capacity  out (host): sum of B[bin_type[k]]
+ *
+ * Copies the instance to the device, runs the same kernels as
+ * vsbpp_pack_device on the library's own stream, copies the result back and
+ * returns when it is complete.  Returns the instance's status code.
+ */
+int vsbpp_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+               const vsbpp_params *p,
+               int32_t *bin_of_item, int32_t *bin_type,
+               int64_t *num_bins, int64_t *total_capacity);
+
+/*
+ * vsbpp_pack_device -- pack one instance held in DEVICE memory; asynchronous.
+ *
+ * Same arguments as vsbpp_pack, but w, B and every output pointer are device
+ * pointers (e.g. the data pointers of CUDA tensors) and the work is enqueued
+ * on `stream` (a cudaStream_t; NULL = legacy default stream).  The return
+ * value only reports host-side argument checks (m, n, p, pointers); the
+ * instance's own status (including weight checks) is written to the device
+ * word *status when the stream reaches it.
+ */
+int vsbpp_pack_device(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                      const vsbpp_params *p,
+                      int32_t *bin_of_item, int32_t *bin_type,
+                      int64_t *num_bins, int64_t *total_capacity,
+                      int32_t *status, void *stream);
+
+/*
+ * vsbpp_pack_batch -- pack N independent instances in one persistent,
+ * work-stealing launch; asynchronous on `stream`.  All array arguments are
+ * DEVICE pointers in CSR form:
+ *
+ *   w_all[w_off[N]]     item weights, instance i = w_all[w_off[i] .. w_off[i+1])
+ *   w_off[N+1]          int64 offsets, w_off[0] = 0, non-decreasing
+ *   B_all[B_off[N]]     capacities, instance i = B_all[B_off[i] .. B_off[i+1])
+ *   B_off[N+1]          int32 offsets
+ *   max_m               host-side upper bound on any instance's m (sizes the
+ *                       on-chip state); an instance with m > max_m gets status
+ *                       VSBPP_ECAPACITY
+ *   bin_of_item_all     out [w_off[N]]: dense bin ids, aligned with w_all
+ *   bin_type_all        out [w_off[N]]: instance i's bin types at
+ *                       bin_type_all[w_off[i] .. w_off[i] + num_bins[i])
+ *   num_bins[N], total[N], status[N]   out, per instance
+ *
+ * Instances are handed out largest first to resident thread groups through an
+ * atomic queue (work stealing).  The first call for a given shape may
+ * allocate scratch memory (cudaMalloc) and must not be made while `stream`
+ * is being captured; vsbpp_plan_* below pre-allocates and records a CUDA
+ * graph.  Returns a host-side status.
+ */
+int vsbpp_pack_batch(int64_t N, const int32_t *w_all, const int64_t *w_off,
+                     const int32_t *B_all, const int32_t *B_off, int64_t max_m,
+                     const vsbpp_params *p,
+                     int32_t *bin_of_item_all, int32_t *bin_type_all,
+                     int64_t *num_bins, int64_t *total, int32_t *status,
+                     void *stream);
+
+/*
+ * vsbpp_pack_plain -- the same batch, packed the plain way: one kernel launch
+ * per instance, one instance after another on `stream`, each launch a single
+ * thread block with the per-instance kernel.  Same arguments and results as
+ * vsbpp_pack_batch; kept as the baseline the batched path is measured
+ * against.
+ */
+int vsbpp_pack_plain(int64_t N, const int32_t *w_all, const int64_t *w_off,
+                     const int32_t *B_all, const int32_t *B_off, int64_t max_m,
+                     const vsbpp_params *p,
+                     int32_t *bin_of_item_all, int32_t *bin_type_all,
+                     int64_t *num_bins, int64_t *total, int32_t *status,
+                     void *stream);
+
+/*
+ * Work counters (tracing).  While enabled, the first-heuristic kernels add
+ * to two device counters: the items they pack, and the fit tests the method
+ * performs -- for every item, one per bin membrane alive when it arrives
+ * (Rule 4 tests every open bin), whether or not a kernel stops a first-fit
+ * scan early.  Enabling affects launches made (or plans recorded) afterwards.
+ * vsbpp_counters_read synchronises the device, copies the counters and, if
+ * reset != 0, sets them back to zero.
+ */
+typedef struct {
+    uint64_t items;
+    uint64_t fit_tests;
+} vsbpp_counters;
+
+int vsbpp_counters_enable(int enable);
+int vsbpp_counters_read(vsbpp_counters *out, int reset);
+
+/*
+ * Plans: a batch shape recorded once into a CUDA graph and replayed.
+ *
+ * vsbpp_plan_create fixes N, an upper bound total_m >= w_off[N], max_m and
+ * the parameters, allocates all scratch memory, and picks the launch
+ * configuration (thread-group size per size class, items staged per step)
+ * from the autotuner's table.  vsbpp_plan_run records the launch sequence
+ * into a CUDA graph the first time it sees a set of pointers and replays the
+ * graph on `stream` afterwards (new pointers re-record).  It never allocates,
+ * so it may itself be called during a stream capture.
+ */
+typedef struct vsbpp_plan vsbpp_plan;
+int vsbpp_plan_create(int64_t N, int64_t total_m, int64_t max_m, const vsbpp_params *p,
+                      vsbpp_plan **out);
+int vsbpp_plan_run(vsbpp_plan *plan, const int32_t *w_all, const int64_t *w_off,
+                   const int32_t *B_all, const int32_t *B_off,
+                   int32_t *bin_of_item_all, int32_t *bin_type_all,
+                   int64_t *num_bins, int64_t *total, int32_t *status, void *stream);
+int vsbpp_plan_destroy(vsbpp_plan *plan);
+
+/*
+ * Launch configuration and autotuner.
+ *
+ * The batched first-heuristic kernel runs thread groups of `warps` warps per
+ * instance; instances with m <= small_m go to single-warp groups.  The
+ * autotuner times candidate configurations on the caller's batch (device CSR
+ * arrays as in vsbpp_pack_batch; the outputs are scratch it may overwrite) and
+ * installs the fastest for the batch's heuristic; vsbpp_tune_save/load keep
+ * the table in a small JSON file.
+ */
+typedef struct {
+    int32_t large_warps;    /* warps per group for instances with m > small_m (1..32, power of 2) */
+    int32_t small_m;        /* instances at or below this size use one warp each (>= 0)           */
+    int32_t small_warps_per_block; /* warps per thread block in the single-warp kernel (1..32)     */
+    int32_t chunk;          /* items staged in shared memory per step (multiple of 32)            */
+} vsbpp_config;
+
+int vsbpp_get_config(vsbpp_config *out);
+int vsbpp_set_config(const vsbpp_config *cfg);
+int vsbpp_autotune(int64_t N, const int32_t *w_all, const int64_t *w_off,
+                   const int32_t *B_all, const int32_t *B_off, int64_t max_m,
+                   const vsbpp_params *p,
+                   int32_t *bin_of_item_all, int32_t *bin_type_all,
+                   int64_t *num_bins, int64_t *total, int32_t *status,
+                   void *stream, vsbpp_config *best, double *best_ms);
+int vsbpp_tune_save(const char *path);
+int vsbpp_tune_load(const char *path);
+
+/*
+ * Serving: continuous batching of packing requests.
+ *
+ * vsbpp_server_create starts a server that keeps request state resident on
+ * the device.  A request is admitted when a slot is free and its device
+ * memory (an upper bound from m and n) fits within device_mem_budget bytes;
+ * admitted requests are packed by the same kernels while other requests are
+ * in flight, on `lanes` concurrent streams.  Requests submitted while the GPU
+ * is busy wait in a host queue until slots and memory free up.
+ *
+ *   vsbpp_server_submit copies the request (host pointers) and returns a
+ *     ticket at once; VSBPP_EBUSY when the host queue is full (max_queued
+ *     waiting requests), VSBPP_ECAPACITY when the request alone needs more
+ *     device memory than the whole budget.  A request holds
+ *     12*m + 4*n bytes (rounded up to 256-byte blocks) plus 256 bytes of
+ *     device memory while admitted, on top of the library's per-lane scratch.
+ *   vsbpp_server_poll waits up to timeout_us microseconds (0: do not wait,
+ *     < 0: wait without limit) for the ticket and copies the result into the
+ *     host buffers; VSBPP_ETIMEDOUT if it is not finished in time.  A ticket
+ *     is released by the poll that returns its result.
+ *   vsbpp_server_stats reports completed requests and latency percentiles
+ *     (submit to completion, microseconds) over the last completed requests.
+ */
+typedef struct vsbpp_server vsbpp_server;
+typedef struct {
+    int64_t completed;
+    int64_t items_packed;
+    double  p50_us, p99_us, max_us;
+    double  busy_s;          /* seconds from the first admission to the last completion */
+} vsbpp_server_stats_t;
+
+int vsbpp_server_create(size_t device_mem_budget, int32_t max_slots, int32_t lanes,
+                        int32_t max_queued, vsbpp_server **out);
+int vsbpp_server_submit(vsbpp_server *srv, const int32_t *w, int64_t m,
+                        const int32_t *B, int32_t n, const vsbpp_params *p,
+                        uint64_t *ticket);
+int vsbpp_server_poll(vsbpp_server *srv, uint64_t ticket,
+                      int32_t *bin_of_item, int32_t *bin_type,
+                      int64_t *num_bins, int64_t *total_capacity,
+                      int64_t timeout_us);
+int vsbpp_server_stats(vsbpp_server *srv, vsbpp_server_stats_t *out);
+int vsbpp_server_destroy(vsbpp_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VSBPP_H */

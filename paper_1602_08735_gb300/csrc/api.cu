@@ -1,0 +1,854 @@
+// api.cu -- the C ABI of include/vsbpp.h: argument checks, scratch memory,
+// launch planning (thread-group sizes, shared-memory capacities, persistent
+// grids), CUDA-graph plans, and the host-memory convenience call.
+//
+// Every pack goes through the same device pipeline:
+//   validate -> (first heuristic, one system per instance)
+//                 order by size class and log2(m), largest first
+//                 -> large-group kernel, single-warp kernel, wide-slot kernel
+//            -> (sublists: first heuristic with s < m, or second heuristic)
+//                 sublist prefix sums -> per-sublist kernel -> compose
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace vsbpp;
+
+namespace {
+
+std::recursive_mutex g_mu;
+std::atomic<int> g_last_cuda{0};
+unsigned long long* g_counters = nullptr;   // device {items, fit tests} or null
+
+struct DeviceInfo {
+    int dev = -1;
+    int sms = 0;
+    int max_smem_optin = 0;
+};
+
+DeviceInfo& device_info() {
+    static DeviceInfo di;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (di.dev != dev) {
+        di.dev = dev;
+        cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&di.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    return di;
+}
+
+vsbpp_config g_cfg = {
+    /*large_warps=*/8,
+    /*small_m=*/1024,
+    /*small_warps_per_block=*/8,
+    /*chunk=*/1024,
+};
+
+int record(cudaError_t e) {
+    if (e == cudaSuccess) return VSBPP_OK;
+    g_last_cuda.store(static_cast<int>(e));
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? VSBPP_ENOMEM : VSBPP_ECUDA;
+}
+
+#define VS_TRY(expr)                              \
+    do {                                          \
+        const int _rc = record(expr);             \
+        if (_rc != VSBPP_OK) return _rc;          \
+    } while (0)
+
+template <typename T>
+int grow(T*& p, int64_t& cap, int64_t need) {
+    if (need <= cap && p) return VSBPP_OK;
+    int64_t n = std::max<int64_t>(need, 1);
+    n = std::max<int64_t>(n, cap + cap / 2);
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, static_cast<size_t>(n) * sizeof(T));
+    if (e != cudaSuccess) return record(e);
+    p = static_cast<T*>(q);
+    cap = n;
+    return VSBPP_OK;
+}
+
+// Scratch owned by the library for one stream (or one plan).
+struct Scratch {
+    int32_t* cls = nullptr;        int64_t cap_cls = 0;
+    int32_t* order = nullptr;      int64_t cap_order = 0;
+    int64_t* nu = nullptr;         int64_t cap_nu = 0;
+    int64_t* unit_base = nullptr;  int64_t cap_unit_base = 0;
+    int32_t* unit_count = nullptr; int64_t cap_unit_count = 0;
+    int64_t* unit_total = nullptr; int64_t cap_unit_total = 0;
+    int32_t* local_types = nullptr; int64_t cap_local_types = 0;
+    uint8_t* fixed = nullptr;      // histogram, cursors, segments, queues
+    // host-memory call staging
+    int32_t* h_w = nullptr;    int64_t cap_h_w = 0;
+    int32_t* h_B = nullptr;    int64_t cap_h_B = 0;
+    int32_t* h_boi = nullptr;  int64_t cap_h_boi = 0;
+    int32_t* h_bt = nullptr;   int64_t cap_h_bt = 0;
+    int64_t* h_small = nullptr; int64_t cap_h_small = 0;   // num_bins, total, status
+
+    uint32_t* kc_slots = nullptr; int64_t cap_kc_slots = 0;   // global-memory bins
+
+    uint32_t* hist() const { return reinterpret_cast<uint32_t*>(fixed); }
+    int64_t* cursor() const { return reinterpret_cast<int64_t*>(fixed + kClasses * kBuckets * 4); }
+    int64_t* seg() const { return cursor() + kClasses * kBuckets; }
+    int64_t* seg_units() const { return seg() + 8; }
+    unsigned long long* queue() const { return reinterpret_cast<unsigned long long*>(seg_units() + 8); }
+    static size_t fixed_bytes() { return kClasses * kBuckets * 4 + kClasses * kBuckets * 8 + 24 * 8; }
+
+    int ensure_fixed() {
+        if (fixed) return VSBPP_OK;
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, fixed_bytes());
+        if (e != cudaSuccess) return record(e);
+        e = cudaMemset(q, 0, fixed_bytes());
+        if (e != cudaSuccess) {
+            cudaFree(q);
+            return record(e);
+        }
+        fixed = static_cast<uint8_t*>(q);
+        return VSBPP_OK;
+    }
+
+    void release() {
+        cudaFree(cls); cudaFree(order); cudaFree(nu); cudaFree(unit_base); cudaFree(unit_count);
+        cudaFree(unit_total); cudaFree(local_types); cudaFree(fixed); cudaFree(kc_slots);
+        cudaFree(h_w); cudaFree(h_B); cudaFree(h_boi); cudaFree(h_bt); cudaFree(h_small);
+        *this = Scratch();
+    }
+};
+
+std::map<cudaStream_t, Scratch>& stream_scratch() {
+    static std::map<cudaStream_t, Scratch> m;
+    return m;
+}
+
+// ------------------------------------------------------------ launch plan
+struct Mode {
+    int heuristic;
+    int compose;          // 1: sublists (first heuristic with s < max_m, or second heuristic)
+    int64_t s;            // sublist size in compose mode
+};
+
+struct H1Shape {
+    int G, groups;
+    int chunk;
+    int slot_cap;
+    int smem;
+    int grid;
+    int64_t cap_m;        // largest membrane system (items) the shape holds
+};
+
+// Global-memory kernel for membrane systems beyond shared memory.
+struct KCShape {
+    bool enabled = false;
+    int64_t cap_m = 0;        // largest m it holds
+    int64_t bin_cap = 0;      // bins of scratch per block
+    int pres_words = 0;       // 0 unless the criterion needs residual presence (BF, RANDOM)
+    int max_B1 = 0;
+    int smem = 0;
+    int grid = 0;
+};
+
+struct LaunchPlan {
+    Mode mode;
+    vsbpp_config cfg;
+    H1Shape large{}, small{}, wide{}, sub{};
+    KCShape kc{};
+    int h2_threads = 0, h2_smem = 0, h2_grid = 0, h2_max_bins = 0;
+    int prep_grid = 0;
+};
+
+int round4(int64_t x) { return static_cast<int>((x + 3) & ~int64_t(3)); }
+
+// Largest m whose group footprint fits `budget` bytes (slot_cap = 2m + 32).
+int64_t cap_for_budget(int budget, int chunk, int slot_size) {
+    int64_t lo = 0, hi = 1 << 22;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) / 2;
+        const int64_t sc = round4(2 * mid + kMaxTypes);
+        const int64_t bytes = h1_group_bytes(static_cast<int>(std::min<int64_t>(sc, 1 << 26)), chunk, slot_size);
+        if (bytes <= budget) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int chunk, int smem_max,
+               int sms, int64_t hard_cap) {
+    const int slot_size = wide ? 8 : 4;
+    sh.chunk = chunk;
+    int64_t cap = std::min<int64_t>(want_m, cap_for_budget(smem_max / groups, chunk, slot_size));
+    cap = std::min<int64_t>(cap, hard_cap);
+    cap = std::max<int64_t>(cap, 1);
+    sh.G = G;
+    sh.groups = groups;
+    sh.cap_m = cap;
+    sh.slot_cap = round4(2 * cap + kMaxTypes);
+    sh.smem = h1_group_bytes(sh.slot_cap, chunk, slot_size) * groups;
+    if (sh.smem > smem_max) return VSBPP_ECAPACITY;
+    const int occ = h1_blocks_per_sm(wide, G, groups, sh.smem);
+    if (occ <= 0) return record(cudaErrorInvalidConfiguration);
+    sh.grid = occ * sms;
+    return VSBPP_OK;
+}
+
+int check_params(const vsbpp_params* p) {
+    if (!p) return VSBPP_OK;
+    if (p->heuristic != VSBPP_H1 && p->heuristic != VSBPP_H2) return VSBPP_EINVAL;
+    if (p->criterion < VSBPP_FF || p->criterion > VSBPP_RANDOM) return VSBPP_EINVAL;
+    if (p->preopen != 0 && p->preopen != 1) return VSBPP_EINVAL;
+    if (p->reserved != 0) return VSBPP_EINVAL;
+    if (p->sublist_size < 0) return VSBPP_EINVAL;
+    if (p->heuristic == VSBPP_H2 && p->sublist_size > VSBPP_H2_MAX_SUBLIST) return VSBPP_EINVAL;
+    return VSBPP_OK;
+}
+
+vsbpp_params defaults(const vsbpp_params* p) {
+    vsbpp_params q;
+    std::memset(&q, 0, sizeof(q));
+    q.heuristic = VSBPP_H1;
+    q.criterion = VSBPP_BF;
+    if (p) q = *p;
+    return q;
+}
+
+// Persistent grids never need more groups than there are units of work.
+void cap_grid(H1Shape& sh, int64_t units) {
+    const int64_t blocks = (std::max<int64_t>(units, 1) + sh.groups - 1) / sh.groups;
+    if (blocks < sh.grid) sh.grid = static_cast<int>(blocks);
+}
+
+int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp) {
+    const DeviceInfo& di = device_info();
+    if (di.sms <= 0) return record(cudaErrorNoDevice);
+    lp.cfg = g_cfg;
+    const int chunk = lp.cfg.chunk;
+    const int smax = di.max_smem_optin;
+    max_m = std::max<int64_t>(max_m, 1);
+    lp.prep_grid = di.sms * 8;
+    if (prm.heuristic == VSBPP_H2) {
+        const int s = static_cast<int>(prm.sublist_size == 0 ? 5 : prm.sublist_size);
+        lp.mode = {VSBPP_H2, 1, s};
+        int f = 1;
+        for (int x = 2; x <= s; ++x) f *= x;
+        lp.h2_threads = std::max(32, (f + 31) / 32 * 32);
+        lp.h2_max_bins = 2 * s + (prm.preopen ? kMaxTypes : 0);
+        lp.h2_smem = h2_smem_bytes(lp.h2_threads, lp.h2_max_bins);
+        const int occ = h2_blocks_per_sm(lp.h2_threads, lp.h2_smem);
+        if (occ <= 0) return record(cudaErrorInvalidConfiguration);
+        lp.h2_grid = occ * di.sms;
+        const int64_t units = N * ((max_m + s - 1) / s);
+        if (units < lp.h2_grid) lp.h2_grid = static_cast<int>(std::max<int64_t>(units, 1));
+        return VSBPP_OK;
+    }
+    const int64_t s = prm.sublist_size;
+    if (s > 0 && s < max_m) {
+        lp.mode = {VSBPP_H1, 1, s};
+        const bool one_warp = s <= lp.cfg.small_m;
+        const int G = one_warp ? 1 : lp.cfg.large_warps;
+        const int groups = one_warp ? lp.cfg.small_warps_per_block : 1;
+        const int sub_chunk = one_warp ? std::min(chunk, 256) : chunk;
+        int rc = make_shape(lp.sub, true, G, groups, s, sub_chunk, smax, di.sms, 1 << 30);
+        if (rc != VSBPP_OK) return rc;
+        if (lp.sub.cap_m < s) return VSBPP_ECAPACITY;
+        cap_grid(lp.sub, N * ((max_m + s - 1) / s));
+        return VSBPP_OK;
+    }
+    lp.mode = {VSBPP_H1, 0, 0};
+    int rc = make_shape(lp.large, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752);
+    if (rc != VSBPP_OK) return rc;
+    rc = make_shape(lp.small, false, 1, lp.cfg.small_warps_per_block,
+                    std::min<int64_t>(max_m, std::max(1, lp.cfg.small_m)), std::min(chunk, 256), smax,
+                    di.sms, 32752);
+    if (rc != VSBPP_OK) return rc;
+    rc = make_shape(lp.wide, true, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30);
+    if (rc != VSBPP_OK) return rc;
+    cap_grid(lp.large, N);
+    cap_grid(lp.small, N);
+    cap_grid(lp.wide, N);
+    if (max_m > lp.large.cap_m) {
+        KCShape& kc = lp.kc;
+        kc.enabled = true;
+        const int64_t want_bins = std::min<int64_t>(2 * max_m + kMaxTypes, int64_t(kMaxTiles) * kTileBins);
+        kc.bin_cap = (want_bins + kTileBins - 1) / kTileBins * kTileBins;
+        kc.cap_m = (kc.bin_cap - kMaxTypes) / 2;
+        const int tiles = static_cast<int>(kc.bin_cap / kTileBins);
+        const bool track = prm.criterion == VSBPP_BF || prm.criterion == VSBPP_RANDOM;
+        kc.pres_words = track ? (tiles + 31) / 32 : 0;
+        int b1 = 32767;
+        while (b1 > 0 && kc_smem_bytes(b1, kc.pres_words) > smax) b1 = b1 * 7 / 8;
+        kc.max_B1 = b1;
+        kc.smem = kc_smem_bytes(kc.max_B1, kc.pres_words);
+        const int occ = kc_blocks_per_sm(kc.smem);
+        if (occ <= 0) return record(cudaErrorInvalidConfiguration);
+        kc.grid = static_cast<int>(std::min<int64_t>(int64_t(occ) * di.sms, std::max<int64_t>(N, 1)));
+    }
+    return VSBPP_OK;
+}
+
+int ensure_scratch(Scratch& sc, const LaunchPlan& lp, int64_t N, int64_t total_m) {
+    int rc = sc.ensure_fixed();
+    if (rc) return rc;
+    if ((rc = grow(sc.cls, sc.cap_cls, N))) return rc;
+    if (!lp.mode.compose) {
+        if ((rc = grow(sc.order, sc.cap_order, N))) return rc;
+        if (lp.kc.enabled && (rc = grow(sc.kc_slots, sc.cap_kc_slots, int64_t(lp.kc.grid) * lp.kc.bin_cap)))
+            return rc;
+        return VSBPP_OK;
+    }
+    const int64_t U = total_m / std::max<int64_t>(lp.mode.s, 1) + N;   // >= sum ceil(m_i/s)
+    if ((rc = grow(sc.nu, sc.cap_nu, N))) return rc;
+    if ((rc = grow(sc.unit_base, sc.cap_unit_base, N + 1))) return rc;
+    if ((rc = grow(sc.unit_count, sc.cap_unit_count, U))) return rc;
+    if ((rc = grow(sc.unit_total, sc.cap_unit_total, U))) return rc;
+    if ((rc = grow(sc.local_types, sc.cap_local_types, total_m))) return rc;
+    return VSBPP_OK;
+}
+
+H1Params h1_params(const BatchView& in, const OutView& out, const vsbpp_params& prm,
+                   const H1Shape& sh) {
+    H1Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.in = in;
+    p.out = out;
+    p.units.unit_base = nullptr;
+    p.units.sublist = 0;
+    p.units.num_units = 0;
+    p.criterion = prm.criterion;
+    p.preopen = prm.preopen;
+    p.seed = prm.seed;
+    p.chunk = sh.chunk;
+    p.slot_cap = sh.slot_cap;
+    p.group_bytes = sh.smem / sh.groups;
+    p.cls = nullptr;
+    p.want_cls = 0;
+    p.counters = g_counters;
+    return p;
+}
+
+// Enqueue the whole pipeline on `st`.  plain = one launch per instance.
+int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutView& out0,
+            const vsbpp_params& prm, bool plain, cudaStream_t st) {
+    if (in.N == 0) return VSBPP_OK;
+    OutView out = out0;
+    PrepParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.in = in;
+    pp.out = out;
+    pp.preopen = prm.preopen;
+    pp.cls = sc.cls;
+    pp.hist = sc.hist();
+    pp.narrow_max_B = SlotTraits<uint32_t>::kMaxCap;
+    const int prep_grid = static_cast<int>(std::min<int64_t>(lp.prep_grid, (in.N + 7) / 8));
+
+    if (!lp.mode.compose) {
+        pp.classify = 1;
+        pp.small_m = plain ? 0 : lp.cfg.small_m;      // plain path: no single-warp class
+        pp.narrow_cap = lp.large.cap_m;
+        pp.small_cap = lp.small.cap_m;
+        pp.wide_cap = lp.wide.cap_m;
+        pp.huge_cap = lp.kc.enabled ? lp.kc.cap_m : 0;
+        pp.huge_max_B1 = lp.kc.max_B1;
+        VS_TRY(validate_launch(pp, prep_grid, st));
+        VS_TRY(order_launch(sc.hist(), sc.cursor(), sc.seg(), sc.queue(), st));
+        VS_TRY(scatter_launch(in, sc.cls, sc.cursor(), sc.order, prep_grid, st));
+        const H1Shape* shapes[3] = {&lp.large, &lp.small, &lp.wide};
+        for (int c = 0; c < 3; ++c) {
+            const H1Shape& sh = *shapes[c];
+            if (plain && c == kClassLarge) {
+                // the plain path: one single-block launch per instance, in turn
+                for (int64_t i = 0; i < in.N; ++i) {
+                    H1Params p = h1_params(in, out, prm, sh);
+                    p.range_begin = i;
+                    p.range_end = i + 1;
+                    p.cls = sc.cls;
+                    p.want_cls = kClassLarge;
+                    VS_TRY(h1_launch(false, p, sh.G, 1, 1, sh.smem, st));
+                }
+                continue;
+            }
+            // (plain path: the rare wide-slot and global-memory instances
+            // share one work-stealing launch per class)
+            H1Params p = h1_params(in, out, prm, sh);
+            p.order = sc.order;
+            p.seg = sc.seg();
+            p.segment = c;
+            p.queue = sc.queue() + c;
+            VS_TRY(h1_launch(c == kClassWide, p, sh.G, sh.groups, sh.grid, sh.smem, st));
+        }
+        if (lp.kc.enabled) {
+            KCParams kp;
+            std::memset(&kp, 0, sizeof(kp));
+            kp.in = in;
+            kp.out = out;
+            kp.criterion = prm.criterion;
+            kp.preopen = prm.preopen;
+            kp.seed = prm.seed;
+            kp.order = sc.order;
+            kp.seg = sc.seg();
+            kp.segment = kClassHuge;
+            kp.queue = sc.queue() + kClassHuge;
+            kp.slots_all = sc.kc_slots;
+            kp.bin_cap = lp.kc.bin_cap;
+            kp.max_B1 = lp.kc.max_B1;
+            kp.pres_words = lp.kc.pres_words;
+            kp.counters = g_counters;
+            VS_TRY(kc_launch(kp, lp.kc.grid, lp.kc.smem, st));
+        }
+        return VSBPP_OK;
+    }
+
+    // compose mode: sublists of s items
+    out.local_types = sc.local_types;
+    out.unit_count = sc.unit_count;
+    out.unit_total = sc.unit_total;
+    pp.out = out;
+    pp.classify = 0;
+    pp.nu = sc.nu;
+    pp.sublist = lp.mode.s;
+    pp.cls = nullptr;
+    VS_TRY(validate_launch(pp, prep_grid, st));
+    VS_TRY(unit_scan_launch(in.N, sc.nu, sc.unit_base, sc.seg_units(), sc.queue(), st));
+    ComposeParams cp;
+    cp.in = in;
+    cp.out = out;
+    cp.unit_base = sc.unit_base;
+    cp.sublist = lp.mode.s;
+    cp.only_instance = -1;
+    const int64_t instances = plain ? in.N : 1;
+    for (int64_t it = 0; it < instances; ++it) {
+        const int64_t only = plain ? it : -1;
+        if (lp.mode.heuristic == VSBPP_H2) {
+            H2Params hp;
+            std::memset(&hp, 0, sizeof(hp));
+            hp.in = in;
+            hp.out = out;
+            hp.units.unit_base = sc.unit_base;
+            hp.units.sublist = lp.mode.s;
+            hp.criterion = prm.criterion;
+            hp.preopen = prm.preopen;
+            hp.seed = prm.seed;
+            hp.sublist = static_cast<int32_t>(lp.mode.s);
+            hp.max_bins = lp.h2_max_bins;
+            hp.only_instance = only;
+            VS_TRY(h2_launch(hp, lp.h2_threads, plain ? 1 : lp.h2_grid, lp.h2_smem, st));
+        } else {
+            H1Params p = h1_params(in, out, prm, lp.sub);
+            p.units.unit_base = sc.unit_base;
+            p.units.sublist = lp.mode.s;
+            p.compose = 1;
+            if (plain) {
+                // one launch for this instance's sublists: positions from unit_base
+                p.seg = sc.unit_base;
+                p.segment = static_cast<int32_t>(it);
+                VS_TRY(h1_launch(true, p, lp.sub.G, lp.sub.groups, 1, lp.sub.smem, st));
+            } else {
+                p.seg = sc.seg_units();
+                p.segment = 0;
+                p.queue = sc.queue();
+                VS_TRY(h1_launch(true, p, lp.sub.G, lp.sub.groups, lp.sub.grid, lp.sub.smem, st));
+            }
+        }
+        cp.only_instance = only;
+        VS_TRY(compose_launch(cp, plain ? 1 : prep_grid, st));
+    }
+    return VSBPP_OK;
+}
+
+int check_instance_args(int64_t m, int32_t n, const void* w, const void* B) {
+    if (m < 0 || n < 1 || n > VSBPP_MAX_TYPES) return VSBPP_EINVAL;
+    if (!B || (m > 0 && !w)) return VSBPP_EINVAL;
+    return VSBPP_OK;
+}
+
+int batch_common(int64_t N, const int32_t* w_all, const int64_t* w_off, const int32_t* B_all,
+                 const int32_t* B_off, int64_t max_m, const vsbpp_params* p, int32_t* boi,
+                 int32_t* bt, int64_t* nb, int64_t* tot, int32_t* status, void* stream, bool plain) {
+    if (N < 0 || max_m < 0) return VSBPP_EINVAL;
+    if (N == 0) return VSBPP_OK;
+    if (!w_off || !B_all || !B_off || !nb || !tot || !status || !boi || !bt) return VSBPP_EINVAL;
+    int rc = check_params(p);
+    if (rc) return rc;
+    const vsbpp_params prm = defaults(p);
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    LaunchPlan lp;
+    if ((rc = build_plan(prm, max_m, N, lp))) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Scratch& sc = stream_scratch()[st];
+    // sublist scratch is sized from the host-side bound N * max_m, so the call
+    // never has to read the device offsets back
+    const int64_t total_m = lp.mode.compose ? N * std::max<int64_t>(max_m, 1) : 0;
+    if ((rc = ensure_scratch(sc, lp, N, total_m))) return rc;
+    BatchView in{N, w_all, w_off, 0, B_all, B_off, 0};
+    OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
+    return enqueue(lp, sc, in, out, prm, plain, st);
+}
+
+// A recorded batch shape (vsbpp_plan_*).
+struct PlanImpl {
+    int64_t N = 0, total_m = 0, max_m = 0;
+    vsbpp_params prm{};
+    LaunchPlan lp;
+    Scratch sc;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* key[10] = {};
+    int graphs_recorded = 0;
+};
+
+// Times one configuration on a batch: best of `reps` device-timed runs.
+int time_config(const vsbpp_config& cfg, int64_t N, const int32_t* w_all, const int64_t* w_off,
+                const int32_t* B_all, const int32_t* B_off, int64_t max_m, const vsbpp_params& prm,
+                int32_t* boi, int32_t* bt, int64_t* nb, int64_t* tot, int32_t* status,
+                cudaStream_t st, int reps, double* ms_out) {
+    const vsbpp_config saved = g_cfg;
+    g_cfg = cfg;
+    LaunchPlan lp;
+    int rc = build_plan(prm, max_m, N, lp);
+    if (rc) {
+        g_cfg = saved;
+        return rc;
+    }
+    Scratch& sc = stream_scratch()[st];
+    const int64_t total_m = lp.mode.compose ? N * std::max<int64_t>(max_m, 1) : 0;
+    if ((rc = ensure_scratch(sc, lp, N, total_m))) {
+        g_cfg = saved;
+        return rc;
+    }
+    BatchView in{N, w_all, w_off, 0, B_all, B_off, 0};
+    OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    for (int r = 0; r <= reps && rc == VSBPP_OK; ++r) {
+        cudaEventRecord(e0, st);
+        rc = enqueue(lp, sc, in, out, prm, false, st);
+        cudaEventRecord(e1, st);
+        if (rc == VSBPP_OK) rc = record(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) best = std::min(best, static_cast<double>(ms));   // first run warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_cfg = saved;
+    *ms_out = best;
+    return rc;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+const char* vsbpp_strerror(int code) {
+    switch (code) {
+        case VSBPP_OK: return "ok";
+        case VSBPP_EINVAL: return "invalid argument or instance";
+        case VSBPP_ETOOBIG: return "an item is heavier than the largest bin capacity";
+        case VSBPP_ENOMEM: return "out of memory";
+        case VSBPP_ECUDA: return "CUDA error";
+        case VSBPP_ETIMEDOUT: return "timed out";
+        case VSBPP_EBUSY: return "busy: no slot or memory budget available";
+        case VSBPP_ENOTFOUND: return "unknown ticket";
+        case VSBPP_ECAPACITY: return "instance exceeds a size limit of this entry point";
+        default: return "unknown status code";
+    }
+}
+
+int vsbpp_version(void) { return VSBPP_VERSION; }
+
+int vsbpp_last_cuda_error(void) { return g_last_cuda.load(); }
+
+int vsbpp_pack_device(const int32_t* w, int64_t m, const int32_t* B, int32_t n, const vsbpp_params* p,
+                      int32_t* bin_of_item, int32_t* bin_type, int64_t* num_bins,
+                      int64_t* total_capacity, int32_t* status, void* stream) {
+    int rc = check_instance_args(m, n, w, B);
+    if (rc) return rc;
+    if (!num_bins || !total_capacity || !status || (m > 0 && (!bin_of_item || !bin_type)))
+        return VSBPP_EINVAL;
+    if ((rc = check_params(p))) return rc;
+    const vsbpp_params prm = defaults(p);
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    LaunchPlan lp;
+    if ((rc = build_plan(prm, std::max<int64_t>(m, 1), 1, lp))) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Scratch& sc = stream_scratch()[st];
+    if ((rc = ensure_scratch(sc, lp, 1, m))) return rc;
+    BatchView in{1, w, nullptr, m, B, nullptr, n};
+    OutView out{bin_of_item, bin_type, num_bins, total_capacity, status, nullptr, nullptr, nullptr};
+    return enqueue(lp, sc, in, out, prm, false, st);
+}
+
+int vsbpp_pack(const int32_t* w, int64_t m, const int32_t* B, int32_t n, const vsbpp_params* p,
+               int32_t* bin_of_item, int32_t* bin_type, int64_t* num_bins, int64_t* total_capacity) {
+    int rc = check_instance_args(m, n, w, B);
+    if (rc) return rc;
+    if (!num_bins || !total_capacity || (m > 0 && (!bin_of_item || !bin_type))) return VSBPP_EINVAL;
+    if ((rc = check_params(p))) return rc;
+    *num_bins = 0;
+    *total_capacity = 0;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    static cudaStream_t own = nullptr;
+    if (!own) VS_TRY(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    Scratch& sc = stream_scratch()[own];
+    if ((rc = grow(sc.h_w, sc.cap_h_w, m))) return rc;
+    if ((rc = grow(sc.h_B, sc.cap_h_B, n))) return rc;
+    if ((rc = grow(sc.h_boi, sc.cap_h_boi, m))) return rc;
+    if ((rc = grow(sc.h_bt, sc.cap_h_bt, m))) return rc;
+    if ((rc = grow(sc.h_small, sc.cap_h_small, 3))) return rc;
+    if (m > 0) VS_TRY(cudaMemcpyAsync(sc.h_w, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, own));
+    VS_TRY(cudaMemcpyAsync(sc.h_B, B, sizeof(int32_t) * n, cudaMemcpyHostToDevice, own));
+    int32_t* d_status = reinterpret_cast<int32_t*>(sc.h_small + 2);
+    rc = vsbpp_pack_device(sc.h_w, m, sc.h_B, n, p, sc.h_boi, sc.h_bt, sc.h_small, sc.h_small + 1,
+                           d_status, own);
+    if (rc) return rc;
+    int64_t small[3] = {0, 0, 0};
+    VS_TRY(cudaMemcpyAsync(small, sc.h_small, sizeof(small), cudaMemcpyDeviceToHost, own));
+    VS_TRY(cudaStreamSynchronize(own));
+    const int32_t st = static_cast<int32_t>(small[2] & 0xFFFFFFFF);
+    if (st != VSBPP_OK) return st;
+    if (m > 0) {
+        VS_TRY(cudaMemcpyAsync(bin_of_item, sc.h_boi, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, own));
+        if (small[0] > 0)
+            VS_TRY(cudaMemcpyAsync(bin_type, sc.h_bt, sizeof(int32_t) * small[0], cudaMemcpyDeviceToHost, own));
+        VS_TRY(cudaStreamSynchronize(own));
+    }
+    *num_bins = small[0];
+    *total_capacity = small[1];
+    return VSBPP_OK;
+}
+
+int vsbpp_pack_batch(int64_t N, const int32_t* w_all, const int64_t* w_off, const int32_t* B_all,
+                     const int32_t* B_off, int64_t max_m, const vsbpp_params* p,
+                     int32_t* bin_of_item_all, int32_t* bin_type_all, int64_t* num_bins,
+                     int64_t* total, int32_t* status, void* stream) {
+    return batch_common(N, w_all, w_off, B_all, B_off, max_m, p, bin_of_item_all, bin_type_all,
+                        num_bins, total, status, stream, false);
+}
+
+int vsbpp_pack_plain(int64_t N, const int32_t* w_all, const int64_t* w_off, const int32_t* B_all,
+                     const int32_t* B_off, int64_t max_m, const vsbpp_params* p,
+                     int32_t* bin_of_item_all, int32_t* bin_type_all, int64_t* num_bins,
+                     int64_t* total, int32_t* status, void* stream) {
+    return batch_common(N, w_all, w_off, B_all, B_off, max_m, p, bin_of_item_all, bin_type_all,
+                        num_bins, total, status, stream, true);
+}
+
+int vsbpp_counters_enable(int enable) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    if (!enable) {
+        g_counters = nullptr;      // the buffer is kept for later reads
+        return VSBPP_OK;
+    }
+    static unsigned long long* buf = nullptr;
+    if (!buf) {
+        void* q = nullptr;
+        VS_TRY(cudaMalloc(&q, 2 * sizeof(unsigned long long)));
+        VS_TRY(cudaMemset(q, 0, 2 * sizeof(unsigned long long)));
+        buf = static_cast<unsigned long long*>(q);
+    }
+    g_counters = buf;
+    return VSBPP_OK;
+}
+
+int vsbpp_counters_read(vsbpp_counters* out, int reset) {
+    if (!out) return VSBPP_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    out->items = 0;
+    out->fit_tests = 0;
+    if (!g_counters) return VSBPP_OK;
+    unsigned long long v[2] = {0, 0};
+    VS_TRY(cudaDeviceSynchronize());
+    VS_TRY(cudaMemcpy(v, g_counters, sizeof(v), cudaMemcpyDeviceToHost));
+    if (reset) VS_TRY(cudaMemset(g_counters, 0, sizeof(v)));
+    out->items = v[0];
+    out->fit_tests = v[1];
+    return VSBPP_OK;
+}
+
+int vsbpp_get_config(vsbpp_config* out) {
+    if (!out) return VSBPP_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    *out = g_cfg;
+    return VSBPP_OK;
+}
+
+int vsbpp_set_config(const vsbpp_config* cfg) {
+    if (!cfg) return VSBPP_EINVAL;
+    if (!h1_shape_supported(cfg->large_warps, 1) || cfg->large_warps < 2) return VSBPP_EINVAL;
+    if (!h1_shape_supported(1, cfg->small_warps_per_block)) return VSBPP_EINVAL;
+    if (cfg->small_m < 0 || cfg->chunk < 32 || cfg->chunk % 32 != 0 || cfg->chunk > 8192)
+        return VSBPP_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    g_cfg = *cfg;
+    return VSBPP_OK;
+}
+
+int vsbpp_plan_create(int64_t N, int64_t total_m, int64_t max_m, const vsbpp_params* p,
+                      vsbpp_plan** out) {
+    if (!out) return VSBPP_EINVAL;
+    *out = nullptr;
+    if (N < 0 || total_m < 0 || max_m < 0) return VSBPP_EINVAL;
+    int rc = check_params(p);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    PlanImpl* pl = new (std::nothrow) PlanImpl();
+    if (!pl) return VSBPP_ENOMEM;
+    pl->N = N;
+    pl->total_m = total_m;
+    pl->max_m = max_m;
+    pl->prm = defaults(p);
+    if ((rc = build_plan(pl->prm, max_m, N, pl->lp)) ||
+        (rc = ensure_scratch(pl->sc, pl->lp, N, std::max<int64_t>(total_m, 1))) ||
+        (rc = record(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking)))) {
+        pl->sc.release();
+        delete pl;
+        return rc;
+    }
+    *out = reinterpret_cast<vsbpp_plan*>(pl);
+    return VSBPP_OK;
+}
+
+int vsbpp_plan_run(vsbpp_plan* plan, const int32_t* w_all, const int64_t* w_off, const int32_t* B_all,
+                   const int32_t* B_off, int32_t* boi, int32_t* bt, int64_t* nb, int64_t* tot,
+                   int32_t* status, void* stream) {
+    if (!plan) return VSBPP_EINVAL;
+    PlanImpl* pl = reinterpret_cast<PlanImpl*>(plan);
+    if (pl->N == 0) return VSBPP_OK;
+    if (!w_off || !B_all || !B_off || !boi || !bt || !nb || !tot || !status) return VSBPP_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    const void* key[10] = {w_all, w_off, B_all, B_off, boi, bt, nb, tot, status, nullptr};
+    if (!pl->exec || std::memcmp(key, pl->key, sizeof(key)) != 0) {
+        BatchView in{pl->N, w_all, w_off, 0, B_all, B_off, 0};
+        OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
+        cudaGraph_t g = nullptr;
+        VS_TRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeRelaxed));
+        const int rc = enqueue(pl->lp, pl->sc, in, out, pl->prm, false, pl->cap);
+        const cudaError_t ce = cudaStreamEndCapture(pl->cap, &g);
+        if (rc != VSBPP_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        VS_TRY(ce);
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        VS_TRY(ie);
+        if (pl->exec) cudaGraphExecDestroy(pl->exec);
+        pl->exec = ex;
+        std::memcpy(pl->key, key, sizeof(key));
+        ++pl->graphs_recorded;
+    }
+    VS_TRY(cudaGraphLaunch(pl->exec, static_cast<cudaStream_t>(stream)));
+    return VSBPP_OK;
+}
+
+int vsbpp_plan_destroy(vsbpp_plan* plan) {
+    if (!plan) return VSBPP_OK;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    PlanImpl* pl = reinterpret_cast<PlanImpl*>(plan);
+    cudaDeviceSynchronize();
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->cap) cudaStreamDestroy(pl->cap);
+    pl->sc.release();
+    delete pl;
+    return VSBPP_OK;
+}
+
+int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const int32_t* B_all,
+                   const int32_t* B_off, int64_t max_m, const vsbpp_params* p, int32_t* boi,
+                   int32_t* bt, int64_t* nb, int64_t* tot, int32_t* status, void* stream,
+                   vsbpp_config* best, double* best_ms) {
+    if (N <= 0 || !w_off || !B_all || !B_off || !boi || !bt || !nb || !tot || !status)
+        return VSBPP_EINVAL;
+    int rc = check_params(p);
+    if (rc) return rc;
+    const vsbpp_params prm = defaults(p);
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Coordinate descent over the four knobs, starting from the current table.
+    vsbpp_config cur = g_cfg;
+    double cur_ms = 0;
+    if ((rc = time_config(cur, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb, tot, status,
+                          st, 3, &cur_ms)))
+        return rc;
+    const int warps[] = {2, 4, 8, 16, 32};
+    const int smalls[] = {0, 128, 512, 1024, 2048, 4096};
+    const int wpb[] = {2, 4, 8, 16};
+    const int chunks[] = {256, 512, 1024, 2048};
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int knob = 0; knob < 4; ++knob) {
+            const int* vals = knob == 0 ? warps : knob == 1 ? smalls : knob == 2 ? wpb : chunks;
+            const int nv = knob == 0 ? 5 : knob == 1 ? 6 : 4;
+            for (int v = 0; v < nv; ++v) {
+                vsbpp_config c = cur;
+                if (knob == 0) c.large_warps = vals[v];
+                if (knob == 1) c.small_m = vals[v];
+                if (knob == 2) c.small_warps_per_block = vals[v];
+                if (knob == 3) c.chunk = vals[v];
+                if (std::memcmp(&c, &cur, sizeof(c)) == 0) continue;
+                double ms = 0;
+                const int r2 = time_config(c, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb,
+                                           tot, status, st, 3, &ms);
+                if (r2 == VSBPP_ECAPACITY) continue;   // shape does not fit this batch
+                if (r2) return r2;
+                if (ms < cur_ms) {
+                    cur = c;
+                    cur_ms = ms;
+                }
+            }
+        }
+    }
+    g_cfg = cur;
+    if (best) *best = cur;
+    if (best_ms) *best_ms = cur_ms;
+    return VSBPP_OK;
+}
+
+int vsbpp_tune_save(const char* path) {
+    if (!path) return VSBPP_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    FILE* f = std::fopen(path, "w");
+    if (!f) return VSBPP_EINVAL;
+    std::fprintf(f, "{\"large_warps\": %d, \"small_m\": %d, \"small_warps_per_block\": %d, \"chunk\": %d}\n",
+                 g_cfg.large_warps, g_cfg.small_m, g_cfg.small_warps_per_block, g_cfg.chunk);
+    std::fclose(f);
+    return VSBPP_OK;
+}
+
+int vsbpp_tune_load(const char* path) {
+    if (!path) return VSBPP_EINVAL;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return VSBPP_EINVAL;
+    char buf[512] = {0};
+    const size_t n = std::fread(buf, 1, sizeof(buf) - 1, f);
+    std::fclose(f);
+    buf[n] = 0;
+    vsbpp_config c = g_cfg;
+    const char* names[4] = {"\"large_warps\"", "\"small_m\"", "\"small_warps_per_block\"", "\"chunk\""};
+    int* fields[4] = {&c.large_warps, &c.small_m, &c.small_warps_per_block, &c.chunk};
+    for (int k = 0; k < 4; ++k) {
+        const char* q = std::strstr(buf, names[k]);
+        if (!q) return VSBPP_EINVAL;
+        q = std::strchr(q, ':');
+        if (!q) return VSBPP_EINVAL;
+        *fields[k] = static_cast<int>(std::strtol(q + 1, nullptr, 10));
+    }
+    return vsbpp_set_config(&c);
+}
+
+}  // extern "C"

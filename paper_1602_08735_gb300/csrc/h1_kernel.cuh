@@ -1,0 +1,457 @@
+// h1_kernel.cuh -- the first heuristic of Section 6.3 on one GB300 SM.
+//
+// One thread group (G warps) runs one membrane system at a time: the items
+// of a unit are taken in list order (Rule 3); for each item every open bin
+// membrane tests whether the item fits (Rule 4, residual >= w) -- the scan
+// below touches every live bin -- and FF / BF / WF (Section 1) picks one,
+// the lowest creation index winning ties.  When nothing fits a bin of the
+// smallest type holding the item is opened; the chosen bin's residual drops
+// by w, and when its load first reaches half its capacity it divides off one
+// empty bin of its type (Rule 5).
+//
+// GB300 layout.  Bin membranes live in shared memory as one packed word per
+// bin, slot = (residual << SHIFT) | creation index, so that each criterion
+// becomes one unsigned min-reduction over the slots:
+//     BF:  min(slot - (w << SHIFT))  -> (r - w, idx); r < w wraps to the top
+//          half of the range, so a non-fitting bin never wins
+//     WF:  min(slot ^ HI)            -> (~r, idx): most room, lowest index
+//     FF:  first slot >= (w << SHIFT) in index order (early exit per warp)
+// Slots are read as 16-byte quads; quad q belongs to thread q mod T of the
+// group, and only that thread ever writes those four slots, so a bin update
+// needs no barrier before the next item's scan.  Each item costs one group
+// barrier (the exchange of per-warp minima through a double-buffered array).
+// Item weights are streamed into shared memory a chunk at a time with
+// cp.async, one chunk ahead of the one being packed.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace vsbpp {
+
+template <typename S>
+struct SlotTraits;
+
+// Narrow slots: 16-bit residual (B_1 <= 32767) and 16-bit index (<= 65536 bins).
+template <>
+struct SlotTraits<uint32_t> {
+    using S = uint32_t;
+    static constexpr int kShift = 16;
+    static constexpr S kNone = 0xFFFFFFFFu;
+    static constexpr S kHi = 0xFFFF0000u;
+    static constexpr S kLo = 0x0000FFFFu;
+    static constexpr S kSign = 0x80000000u;
+    static constexpr int64_t kMaxCap = 32767;
+    static constexpr int64_t kMaxBins = 65536;
+    __device__ static __forceinline__ S warp_min(S v) { return __reduce_min_sync(kFull, v); }
+    __device__ static __forceinline__ void load_quad(const S* p, uint32_t q, S& a, S& b, S& c, S& d) {
+        const uint4 v = reinterpret_cast<const uint4*>(p)[q];
+        a = v.x; b = v.y; c = v.z; d = v.w;
+    }
+    __device__ static __forceinline__ void store_quad(S* p, uint32_t q, S a, S b, S c, S d) {
+        reinterpret_cast<uint4*>(p)[q] = make_uint4(a, b, c, d);
+    }
+};
+
+// Wide slots: 32-bit residual (B_1 < 2^31) and 32-bit index.
+template <>
+struct SlotTraits<unsigned long long> {
+    using S = unsigned long long;
+    static constexpr int kShift = 32;
+    static constexpr S kNone = ~0ull;
+    static constexpr S kHi = 0xFFFFFFFF00000000ull;
+    static constexpr S kLo = 0x00000000FFFFFFFFull;
+    static constexpr S kSign = 0x8000000000000000ull;
+    static constexpr int64_t kMaxCap = 0x7FFFFFFF;
+    static constexpr int64_t kMaxBins = 0x7FFFFFFF;
+    __device__ static __forceinline__ S warp_min(S v) { return warp_min_u64(v); }
+    __device__ static __forceinline__ void load_quad(const S* p, uint32_t q, S& a, S& b, S& c, S& d) {
+        const ulonglong2 v0 = reinterpret_cast<const ulonglong2*>(p)[2 * q];
+        const ulonglong2 v1 = reinterpret_cast<const ulonglong2*>(p)[2 * q + 1];
+        a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+    }
+    __device__ static __forceinline__ void store_quad(S* p, uint32_t q, S a, S b, S c, S d) {
+        reinterpret_cast<ulonglong2*>(p)[2 * q] = make_ulonglong2(a, b);
+        reinterpret_cast<ulonglong2*>(p)[2 * q + 1] = make_ulonglong2(c, d);
+    }
+};
+
+// Launch parameters of the first-heuristic kernel.
+struct H1Params {
+    BatchView in;
+    OutView out;
+    UnitMap units;
+    int32_t criterion;
+    int32_t preopen;
+    uint64_t seed;
+    // Work list: positions [seg[segment], seg[segment+1]) when seg != null,
+    // else [range_begin, range_end); a position x names unit order[x], or
+    // unit x itself when order == null.  With queue != null the groups pull
+    // positions through an atomic counter (work stealing); otherwise static
+    // round robin.  With cls != null a unit whose class differs from
+    // want_cls is skipped (single-instance launches of the plain path).
+    const int32_t* order;
+    const int64_t* seg;
+    int32_t segment;
+    int64_t range_begin, range_end;
+    unsigned long long* queue;
+    const int32_t* cls;
+    int32_t want_cls;
+    unsigned long long* counters;  // null, or {items, fit tests} to add to
+    int32_t compose;        // 1: write sublist-local results (see OutView)
+    int32_t chunk;          // items staged per step (multiple of 32)
+    int32_t slot_cap;       // bins per group (multiple of 4)
+    int32_t group_bytes;    // shared memory per group
+};
+
+// Shared-memory footprint of one group (host and device agree on this).
+__host__ __device__ inline int h1_align16(int x) { return (x + 15) & ~15; }
+__host__ __device__ inline int h1_group_bytes(int slot_cap, int chunk, int slot_size) {
+    return h1_align16(slot_cap * slot_size)      // slots
+         + h1_align16(slot_cap)                  // bin types (uint8)
+         + 2 * chunk * 4                         // double-buffered weights
+         + kMaxTypes * 4                         // capacities
+         + 2 * 32 * slot_size                    // per-warp minima, two buffers
+         + 32 * 8                                // scan / totals exchange
+         + 16;                                   // broadcast words
+}
+
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int G, int GROUPS, typename S>
+struct H1Group {
+    using Tr = SlotTraits<S>;
+    static constexpr int T = 32 * G;
+    static constexpr int kShift = Tr::kShift;
+
+    int tid, lane, warp, gid;
+    S* slots;
+    uint8_t* typ;
+    int32_t* wst;
+    uint32_t* Bs;
+    S* red;
+    uint64_t* xch;
+    long long* bcast;
+
+    __device__ __forceinline__ void sync() const {
+        if constexpr (G == 1) {
+            __syncwarp();
+        } else if constexpr (GROUPS == 1) {
+            __syncthreads();
+        } else {
+            named_barrier(1 + gid, T);
+        }
+    }
+
+    __device__ __forceinline__ static uint32_t owner(uint32_t b) { return (b >> 2) & (T - 1); }
+
+    // Owner-only: create bin b with residual r and type t.  The first slot of a
+    // quad clears the other three so a partial quad never shows stale bins.
+    __device__ __forceinline__ void put_new(uint32_t b, uint64_t r, uint32_t t) const {
+        const S s = (static_cast<S>(r) << kShift) | static_cast<S>(b);
+        if ((b & 3u) == 0u) {
+            Tr::store_quad(slots, b >> 2, s, S(0), S(0), S(0));
+        } else {
+            slots[b] = s;
+        }
+        typ[b] = static_cast<uint8_t>(t);
+    }
+
+    // --- the fit test of Rule 4 over every live bin, one criterion each ---
+    __device__ __forceinline__ S scan_bf(uint32_t nq, uint32_t w) const {
+        const S W = static_cast<S>(w) << kShift;
+        S best = Tr::kNone;
+#pragma unroll 4
+        for (uint32_t q = tid; q < nq; q += T) {
+            S a, b, c, d;
+            Tr::load_quad(slots, q, a, b, c, d);
+            best = min(best, a - W);
+            best = min(best, b - W);
+            best = min(best, c - W);
+            best = min(best, d - W);
+        }
+        return best;
+    }
+
+    __device__ __forceinline__ S scan_wf(uint32_t nq) const {
+        S best = Tr::kNone;
+#pragma unroll 4
+        for (uint32_t q = tid; q < nq; q += T) {
+            S a, b, c, d;
+            Tr::load_quad(slots, q, a, b, c, d);
+            best = min(best, a ^ Tr::kHi);
+            best = min(best, b ^ Tr::kHi);
+            best = min(best, c ^ Tr::kHi);
+            best = min(best, d ^ Tr::kHi);
+        }
+        return best;
+    }
+
+    __device__ __forceinline__ static S ff_key(S s) {
+        return ((s & Tr::kLo) << kShift) | (s >> kShift);   // (idx, r)
+    }
+
+    __device__ __forceinline__ S scan_ff(uint32_t nq, uint32_t w) const {
+        const S W = static_cast<S>(w) << kShift;
+        for (uint32_t base = static_cast<uint32_t>(warp) * 32u; base < nq; base += T) {
+            const uint32_t q = base + static_cast<uint32_t>(lane);
+            S cand = Tr::kNone;
+            if (q < nq) {
+                S a, b, c, d;
+                Tr::load_quad(slots, q, a, b, c, d);
+                if (a >= W) cand = ff_key(a);
+                else if (b >= W) cand = ff_key(b);
+                else if (c >= W) cand = ff_key(c);
+                else if (d >= W) cand = ff_key(d);
+            }
+            if (__any_sync(kFull, cand != Tr::kNone)) return cand;
+        }
+        return Tr::kNone;
+    }
+
+    __device__ __forceinline__ void load_chunk(const int32_t* w, int64_t first, int64_t k,
+                                               int buf, int chunk) const {
+        int32_t* dst = wst + buf * chunk;
+        const int64_t cnt = (k - first) < chunk ? (k - first) : chunk;
+        for (int x = tid; x < cnt; x += T) cp_async4(dst + x, w + first + x);
+        cp_async_commit();
+    }
+
+    // Pack one unit; called by all T threads of the group with identical args.
+    __device__ void pack_unit(const H1Params& p, int64_t uid) const {
+        const int64_t i = p.units.instance_of(uid, p.in.N);
+        if (p.out.status[i] != VSBPP_OK) return;        // rejected by validation
+        if (p.cls && p.cls[i] != p.want_cls) return;
+        const int64_t m = p.in.m(i);
+        int64_t a = 0, k = m;
+        if (p.units.unit_base) {
+            const int64_t g = uid - p.units.unit_base[i];
+            a = g * p.units.sublist;
+            k = (m - a) < p.units.sublist ? (m - a) : p.units.sublist;
+        }
+        const int64_t wb = p.in.w_begin(i);
+        const int32_t* w = p.in.w_all + wb + a;
+        const int32_t n = p.in.n(i);
+        const int32_t* B = p.in.B_all + p.in.B_begin(i);
+        const uint32_t Bl = lane < n ? static_cast<uint32_t>(B[lane]) : 0u;
+        if (warp == 0) Bs[lane] = Bl;
+        int32_t* raw = p.out.bin_of_item + wb + a;
+        int32_t* types_out = p.compose ? (p.out.local_types + wb + a) : (p.out.bin_type + wb);
+        const int chunk = p.chunk;
+
+        uint32_t L = 0;
+        if (p.preopen) {                     // literal Rule 2: one empty bin per type
+            for (int t = 0; t < n; ++t) {
+                if (tid == static_cast<int>(owner(static_cast<uint32_t>(t))))
+                    put_new(static_cast<uint32_t>(t), static_cast<uint32_t>(B[t]), static_cast<uint32_t>(t));
+            }
+            L = static_cast<uint32_t>(n);
+        }
+        if (k > 0) load_chunk(w, 0, k, 0, chunk);
+        unsigned long long fit_tests = 0;      // live bins summed over items (counters)
+
+        for (int64_t j = 0; j < k; ++j) {
+            const int jc = static_cast<int>(j % chunk);
+            const int buf = static_cast<int>((j / chunk) & 1);
+            if (jc == 0) {
+                cp_async_wait_all();
+                sync();                        // this chunk is in shared memory
+                if (j + chunk < k) load_chunk(w, j + chunk, k, buf ^ 1, chunk);
+            }
+            const uint32_t wj = static_cast<uint32_t>(wst[buf * chunk + jc]);
+            const int c = pick_criterion(p.criterion, p.seed, static_cast<uint64_t>(a + j));
+            const uint32_t nq = (L + 3u) >> 2;
+            fit_tests += L;
+
+            S key;
+            if (c == kBF) key = scan_bf(nq, wj);
+            else if (c == kWF) key = scan_wf(nq);
+            else key = scan_ff(nq, wj);
+            key = Tr::warp_min(key);
+            if constexpr (G > 1) {
+                const int par = static_cast<int>(j & 1) * G;
+                if (lane == 0) red[par + warp] = key;
+                sync();
+                key = Tr::warp_min(red[par + (lane % G)]);
+            } else {
+                __syncwarp();
+            }
+
+            // decode the winning slot (uniform across the group)
+            bool hit;
+            uint32_t b;
+            uint64_t r_old;
+            if (c == kFF) {
+                hit = key != Tr::kNone;
+                b = static_cast<uint32_t>(key >> kShift);
+                r_old = static_cast<uint64_t>(key & Tr::kLo);
+            } else if (c == kBF) {
+                hit = key < Tr::kSign;
+                b = static_cast<uint32_t>(key & Tr::kLo);
+                r_old = static_cast<uint64_t>(key >> kShift) + wj;
+            } else {
+                r_old = static_cast<uint64_t>(Tr::kLo - (key >> kShift));
+                hit = r_old >= wj;
+                b = static_cast<uint32_t>(key & Tr::kLo);
+            }
+            uint32_t t;
+            if (hit) {
+                t = typ[b];
+            } else {                           // nothing fits: smallest type holding w
+                t = 31u - static_cast<uint32_t>(__clz(__ballot_sync(kFull, Bl >= wj)));
+                b = L;
+            }
+            const uint64_t Bt = __shfl_sync(kFull, Bl, static_cast<int>(t));
+            if (!hit) r_old = Bt;
+            const uint64_t r_new = r_old - wj;
+            // Rule 5: 2*load_before < B_t <= 2*load_after, in residual terms
+            const bool fire = (Bt < 2 * r_old) && (2 * r_new <= Bt);
+            if (tid == static_cast<int>(owner(b))) {
+                if (hit) slots[b] = (static_cast<S>(r_new) << kShift) | static_cast<S>(b);
+                else put_new(b, r_new, t);
+            }
+            uint32_t Ln = L + (hit ? 0u : 1u);
+            if (fire) {
+                if (tid == static_cast<int>(owner(Ln))) put_new(Ln, Bt, t);
+                ++Ln;
+            }
+            if (tid == 0) raw[j] = static_cast<int32_t>(b);
+            L = Ln;
+        }
+
+        // --- objective (Section 1) and dense ids: used bins in creation order ---
+        sync();
+        const uint32_t per = (L + T - 1) / T;
+        uint32_t b0 = static_cast<uint32_t>(tid) * per;
+        if (b0 > L) b0 = L;
+        const uint32_t b1 = (b0 + per) < L ? (b0 + per) : L;
+        uint32_t cnt = 0;
+        for (uint32_t b = b0; b < b1; ++b)
+            cnt += static_cast<uint32_t>((slots[b] >> kShift) < static_cast<S>(Bs[typ[b]]));
+        uint32_t excl = warp_exclusive_scan(cnt, lane);
+        uint32_t used_total = __shfl_sync(kFull, excl + cnt, 31);
+        if constexpr (G > 1) {
+            uint32_t* wsum = reinterpret_cast<uint32_t*>(xch);
+            if (lane == 31) wsum[warp] = excl + cnt;
+            sync();
+            uint32_t pre = 0, all = 0;
+            for (int x = 0; x < G; ++x) {
+                const uint32_t v = wsum[x];
+                pre += x < warp ? v : 0u;
+                all += v;
+            }
+            excl += pre;
+            used_total = all;
+        }
+        uint32_t d = excl;
+        uint64_t tot = 0;
+        for (uint32_t b = b0; b < b1; ++b) {
+            const S s = slots[b];
+            const uint32_t t = typ[b];
+            const uint32_t cap = Bs[t];
+            if ((s >> kShift) < static_cast<S>(cap)) {
+                slots[b] = ((s >> kShift) << kShift) | static_cast<S>(d);
+                types_out[d] = static_cast<int32_t>(t);
+                tot += cap;
+                ++d;
+            }
+        }
+        sync();
+        for (int64_t j = tid; j < k; j += T)
+            raw[j] = static_cast<int32_t>(slots[static_cast<uint32_t>(raw[j])] & Tr::kLo);
+        tot = warp_sum_u64(tot);
+        if constexpr (G > 1) {
+            // xch held the warp counts of the scan above; every read of them
+            // happened before the barrier that precedes the remap.
+            if (lane == 0) xch[warp] = tot;
+            sync();
+            if (tid == 0) {
+                uint64_t s = 0;
+                for (int x = 0; x < G; ++x) s += xch[x];
+                tot = s;
+            }
+        }
+        if (tid == 0) {
+            if (p.counters) {
+                atomicAdd(p.counters, static_cast<unsigned long long>(k));
+                atomicAdd(p.counters + 1, fit_tests);
+            }
+            if (p.compose) {
+                p.out.unit_count[uid] = static_cast<int32_t>(used_total);
+                p.out.unit_total[uid] = static_cast<int64_t>(tot);
+            } else {
+                p.out.num_bins[i] = static_cast<int64_t>(used_total);
+                p.out.total[i] = static_cast<int64_t>(tot);
+            }
+        }
+        sync();                                 // shared memory is reused by the next unit
+    }
+};
+
+template <int G, int GROUPS, typename S>
+__global__ void __launch_bounds__(32 * G * GROUPS)
+h1_pack_kernel(const H1Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using Grp = H1Group<G, GROUPS, S>;
+    Grp g;
+    g.gid = static_cast<int>(threadIdx.x) / Grp::T;
+    g.tid = static_cast<int>(threadIdx.x) % Grp::T;
+    g.lane = g.tid & 31;
+    g.warp = g.tid >> 5;
+    unsigned char* base = smem + static_cast<size_t>(g.gid) * static_cast<size_t>(p.group_bytes);
+    g.slots = reinterpret_cast<S*>(base);
+    base += h1_align16(p.slot_cap * static_cast<int>(sizeof(S)));
+    g.typ = base;
+    base += h1_align16(p.slot_cap);
+    g.wst = reinterpret_cast<int32_t*>(base);
+    base += 2 * p.chunk * 4;
+    g.Bs = reinterpret_cast<uint32_t*>(base);
+    base += kMaxTypes * 4;
+    g.red = reinterpret_cast<S*>(base);
+    base += 2 * 32 * sizeof(S);
+    g.xch = reinterpret_cast<uint64_t*>(base);
+    base += 32 * 8;
+    g.bcast = reinterpret_cast<long long*>(base);
+
+    int64_t begin, end;
+    if (p.seg) {
+        begin = p.seg[p.segment];
+        end = p.seg[p.segment + 1];
+    } else {
+        begin = p.range_begin;
+        end = p.range_end;
+    }
+    const int64_t count = end - begin;
+    if (count <= 0) return;
+
+    if (p.queue) {
+        for (int iter = 0;; ++iter) {
+            long long u;
+            if constexpr (G == 1) {
+                unsigned long long v = 0;
+                if (g.lane == 0) v = atomicAdd(p.queue, 1ull);
+                u = static_cast<long long>(__shfl_sync(kFull, v, 0));
+            } else {
+                if (g.tid == 0) g.bcast[iter & 1] = static_cast<long long>(atomicAdd(p.queue, 1ull));
+                g.sync();
+                u = g.bcast[iter & 1];
+            }
+            if (u >= count) break;
+            const int64_t uid = p.order ? static_cast<int64_t>(p.order[begin + u]) : begin + u;
+            g.pack_unit(p, uid);
+        }
+    } else {
+        const int64_t first = static_cast<int64_t>(blockIdx.x) * GROUPS + g.gid;
+        const int64_t stride = static_cast<int64_t>(gridDim.x) * GROUPS;
+        for (int64_t u = first; u < count; u += stride) {
+            const int64_t uid = p.order ? static_cast<int64_t>(p.order[begin + u]) : begin + u;
+            g.pack_unit(p, uid);
+        }
+    }
+}
+
+}  // namespace vsbpp

@@ -1,0 +1,40 @@
+// internal.h -- host-side declarations shared by the library's translation
+// units (kernel launchers and the C ABI).  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vsbpp.h"
+#include "device_common.cuh"
+#include "h1_kernel.cuh"
+#include "h2_params.cuh"
+#include "prep_params.cuh"
+#include "kc_params.cuh"
+
+namespace vsbpp {
+
+// First-heuristic kernel: G warps per group, `groups` groups per block,
+// narrow (32-bit) or wide (64-bit) bin slots.  Supported shapes:
+// (G=1, groups in {1,2,4,8,16}) and (G in {2,4,8,16,32}, groups=1).
+bool h1_shape_supported(int G, int groups);
+cudaError_t h1_launch(bool wide, const H1Params& p, int G, int groups, int grid, int smem,
+                      cudaStream_t st);
+int h1_blocks_per_sm(bool wide, int G, int groups, int smem);
+
+cudaError_t kc_launch(const KCParams& p, int grid, int smem, cudaStream_t st);
+int kc_blocks_per_sm(int smem);
+
+cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaStream_t st);
+int h2_blocks_per_sm(int threads, int smem);
+
+cudaError_t validate_launch(const PrepParams& p, int grid, cudaStream_t st);
+cudaError_t order_launch(uint32_t* hist, int64_t* cursor, int64_t* seg, unsigned long long* queue,
+                         cudaStream_t st);
+cudaError_t scatter_launch(const BatchView& in, const int32_t* cls, int64_t* cursor, int32_t* order,
+                           int grid, cudaStream_t st);
+cudaError_t unit_scan_launch(int64_t N, const int64_t* nu, int64_t* unit_base, int64_t* seg_units,
+                             unsigned long long* queue, cudaStream_t st);
+cudaError_t compose_launch(const ComposeParams& p, int grid, cudaStream_t st);
+
+}  // namespace vsbpp
