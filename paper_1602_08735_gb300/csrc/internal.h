@@ -14,6 +14,10 @@
 
 namespace vsbpp {
 
+// Raises a kernel's dynamic shared-memory limit to `smem` bytes on the current
+// device, once per (kernel, device, size) increase.
+cudaError_t ensure_smem_attr(const void* kernel, int smem);
+
 // First-heuristic kernel: G warps per group, `groups` groups per block,
 // narrow (32-bit) or wide (64-bit) bin slots.  Supported shapes:
 // (G=1, groups in {1,2,4,8,16}) and (G in {2,4,8,16,32}, groups=1).

@@ -1,5 +1,9 @@
 // misc_kernels.cu -- launchers for validation, ordering, composition and the
 // second heuristic, plus the dispatch of the first-heuristic kernels.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "internal.h"
 #include "h2_kernel.cuh"
 #include "prep_kernels.cuh"
@@ -11,6 +15,19 @@ cudaError_t h1_launch_narrow_entry(const H1Params&, int, int, int, int, cudaStre
 cudaError_t h1_launch_wide_entry(const H1Params&, int, int, int, int, cudaStream_t);
 int h1_occ_narrow_entry(int, int, int);
 int h1_occ_wide_entry(int, int, int);
+
+cudaError_t ensure_smem_attr(const void* kernel, int smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    int& cur = done[std::make_pair(kernel, dev)];
+    if (smem <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) cur = smem;
+    return e;
+}
 
 bool h1_shape_supported(int G, int groups) {
     if (G == 1) return groups == 1 || groups == 2 || groups == 4 || groups == 8 || groups == 16;
@@ -28,15 +45,14 @@ int h1_blocks_per_sm(bool wide, int G, int groups, int smem) {
 }
 
 cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(h2_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(h2_pack_kernel), smem);
     if (e != cudaSuccess) return e;
     h2_pack_kernel<<<grid, threads, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 int h2_blocks_per_sm(int threads, int smem) {
-    if (cudaFuncSetAttribute(h2_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return 0;
+    if (ensure_smem_attr(reinterpret_cast<const void*>(h2_pack_kernel), smem) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, h2_pack_kernel, threads, smem) != cudaSuccess)
         return 0;
@@ -44,15 +60,14 @@ int h2_blocks_per_sm(int threads, int smem) {
 }
 
 cudaError_t kc_launch(const KCParams& p, int grid, int smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(kc_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(kc_pack_kernel), smem);
     if (e != cudaSuccess) return e;
     kc_pack_kernel<<<grid, 32, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 int kc_blocks_per_sm(int smem) {
-    if (cudaFuncSetAttribute(kc_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return 0;
+    if (ensure_smem_attr(reinterpret_cast<const void*>(kc_pack_kernel), smem) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kc_pack_kernel, 32, smem) != cudaSuccess) return 0;
     return nb;
