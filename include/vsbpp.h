@@ -216,8 +216,9 @@ int vsbpp_counters_read(vsbpp_counters *out, int reset);
  * configuration (thread-group size per size class, items staged per step)
  * from the autotuner's table.  vsbpp_plan_run records the launch sequence
  * into a CUDA graph the first time it sees a set of pointers and replays the
- * graph on `stream` afterwards (new pointers re-record).  It never allocates,
- * so it may itself be called during a stream capture.
+ * graph on `stream` afterwards (new pointers re-record).  It never allocates;
+ * called while `stream` is itself being captured, it adds the launches to the
+ * caller's graph directly instead of replaying its own.
  */
 typedef struct vsbpp_plan vsbpp_plan;
 int vsbpp_plan_create(int64_t N, int64_t total_m, int64_t max_m, const vsbpp_params *p,

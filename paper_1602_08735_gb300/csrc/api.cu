@@ -731,6 +731,16 @@ int vsbpp_plan_run(vsbpp_plan* plan, const int32_t* w_all, const int64_t* w_off,
     if (pl->N == 0) return VSBPP_OK;
     if (!w_off || !B_all || !B_off || !boi || !bt || !nb || !tot || !status) return VSBPP_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(g_mu);
+    cudaStream_t ust = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    VS_TRY(cudaStreamIsCapturing(ust, &cs));
+    if (cs == cudaStreamCaptureStatusActive) {
+        // The caller is recording its own graph: put the launches straight into
+        // it (everything is pre-allocated, so nothing here allocates).
+        BatchView in{pl->N, w_all, w_off, 0, B_all, B_off, 0};
+        OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
+        return enqueue(pl->lp, pl->sc, in, out, pl->prm, false, ust);
+    }
     const void* key[10] = {w_all, w_off, B_all, B_off, boi, bt, nb, tot, status, nullptr};
     if (!pl->exec || std::memcmp(key, pl->key, sizeof(key)) != 0) {
         BatchView in{pl->N, w_all, w_off, 0, B_all, B_off, 0};
@@ -753,7 +763,7 @@ int vsbpp_plan_run(vsbpp_plan* plan, const int32_t* w_all, const int64_t* w_off,
         std::memcpy(pl->key, key, sizeof(key));
         ++pl->graphs_recorded;
     }
-    VS_TRY(cudaGraphLaunch(pl->exec, static_cast<cudaStream_t>(stream)));
+    VS_TRY(cudaGraphLaunch(pl->exec, ust));
     return VSBPP_OK;
 }
 

@@ -369,6 +369,7 @@ class Server:
                  max_queued: int = 1 << 20):
         self._lib = load()
         h = ctypes.c_void_p()
+        self._m = {}
         rc = self._lib.vsbpp_server_create(device_mem_budget, max_slots, lanes, max_queued, ctypes.byref(h))
         if rc != 0:
             raise VsbppError(rc, "vsbpp_server_create")
@@ -386,7 +387,6 @@ class Server:
                                            ctypes.byref(p), ctypes.byref(t))
         if rc != 0:
             raise VsbppError(rc, "vsbpp_server_submit")
-        self._m = getattr(self, "_m", {})
         self._m[int(t.value)] = int(w.shape[0])
         return int(t.value)
 
