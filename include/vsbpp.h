@@ -178,6 +178,41 @@ int vsbpp_pack_batch(int64_t N, const int32_t *w_all, const int64_t *w_off,
                      void *stream);
 
 /*
+ * vsbpp_pack_batch_noalloc -- vsbpp_pack_batch for callers that cannot
+ * allocate device memory.  (The paper has no counterpart: this is a property
+ * of the library, not of the method.)
+ *
+ * Who needs it: code that runs while a stream is being captured into a CUDA
+ * graph in the global capture mode, where cudaMalloc is not permitted; code
+ * that owns a fixed memory reservation or runs inside another allocator's
+ * arena; latency-critical loops that cannot afford an allocation, or the
+ * device-wide synchronisation a cudaFree implies, on their path.  This call
+ * allocates nothing: its scratch (about 0.5 MiB) is one static array in the
+ * library's device image, shared by every call on a device.
+ *
+ * Arguments and results as vsbpp_pack_batch, restricted to the first
+ * heuristic with one membrane system per instance (sublist_size 0 or
+ * >= max_m): N <= VSBPP_NOALLOC_MAX_INSTANCES and max_m <=
+ * VSBPP_NOALLOC_MAX_ITEMS, else VSBPP_ECAPACITY; other parameters as in
+ * vsbpp_pack_batch, a second-heuristic request gives VSBPP_EINVAL.
+ * Instances with B_1 > 32767 get status VSBPP_ECAPACITY.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current); make that first call before any stream
+ * capture begins.  Every call on a device uses the same scratch: calls whose
+ * GPU work may overlap in time (for example on two streams) race and must be
+ * ordered by the caller.  Each call clears what must start at zero.
+ */
+#define VSBPP_NOALLOC_MAX_INSTANCES 65536
+#define VSBPP_NOALLOC_MAX_ITEMS 16384
+int vsbpp_pack_batch_noalloc(int64_t N, const int32_t *w_all, const int64_t *w_off,
+                             const int32_t *B_all, const int32_t *B_off, int64_t max_m,
+                             const vsbpp_params *p,
+                             int32_t *bin_of_item_all, int32_t *bin_type_all,
+                             int64_t *num_bins, int64_t *total, int32_t *status,
+                             void *stream);
+
+/*
  * vsbpp_pack_plain -- the same batch, packed the plain way: one kernel launch
  * per instance, one instance after another on `stream`, each launch a single
  * thread block with the per-instance kernel.  Same arguments and results as

@@ -25,6 +25,7 @@ MAX_TYPES = 32
 EXPORTS = (
     "vsbpp_strerror", "vsbpp_version", "vsbpp_last_cuda_error",
     "vsbpp_pack", "vsbpp_pack_device", "vsbpp_pack_batch", "vsbpp_pack_plain",
+    "vsbpp_pack_batch_noalloc",
     "vsbpp_counters_enable", "vsbpp_counters_read",
     "vsbpp_plan_create", "vsbpp_plan_run", "vsbpp_plan_destroy",
     "vsbpp_get_config", "vsbpp_set_config", "vsbpp_autotune", "vsbpp_tune_save", "vsbpp_tune_load",
@@ -88,7 +89,7 @@ def load(path: str = LIB_PATH):
         lib.vsbpp_pack.argtypes = [vp, i64, vp, i32, pp, vp, vp, i64p, i64p]
         lib.vsbpp_pack_device.restype = ctypes.c_int
         lib.vsbpp_pack_device.argtypes = [vp, i64, vp, i32, pp, vp, vp, vp, vp, vp, vp]
-        for name in ("vsbpp_pack_batch", "vsbpp_pack_plain"):
+        for name in ("vsbpp_pack_batch", "vsbpp_pack_plain", "vsbpp_pack_batch_noalloc"):
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = [i64, vp, vp, vp, vp, i64, pp, vp, vp, vp, vp, vp, vp]
@@ -266,6 +267,15 @@ def pack_plain(db: DeviceBatch, out: DeviceResult, heuristic: int = H1, criterio
                sublist_size: int = 0, preopen: int = 0, seed: int = 0, stream=None, max_m=None) -> int:
     """One launch per instance (vsbpp_pack_plain); async on ``stream``."""
     return _batch_call("vsbpp_pack_plain", db, out,
+                       make_params(heuristic, criterion, sublist_size, preopen, seed), stream, max_m)
+
+
+def pack_batch_noalloc(db: DeviceBatch, out: DeviceResult, heuristic: int = H1, criterion: int = BF,
+                       sublist_size: int = 0, preopen: int = 0, seed: int = 0, stream=None,
+                       max_m=None) -> int:
+    """vsbpp_pack_batch_noalloc: the batched pack with the library's static
+    device scratch (for callers that cannot allocate); async on ``stream``."""
+    return _batch_call("vsbpp_pack_batch_noalloc", db, out,
                        make_params(heuristic, criterion, sublist_size, preopen, seed), stream, max_m)
 
 
