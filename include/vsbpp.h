@@ -279,6 +279,11 @@ typedef struct {
     int32_t small_m;        /* instances at or below this size use one warp each (>= 0)           */
     int32_t small_warps_per_block; /* warps per thread block in the single-warp kernel (1..32)     */
     int32_t chunk;          /* items staged in shared memory per step (multiple of 32)            */
+    int32_t slot_pct;       /* bin slots per membrane system in the shared-memory kernels, as a
+                               percentage of its items (+64); 200 = the worst case (every item
+                               can create two bins).  A system that outgrows its slots is packed
+                               again from the start by a worst-case-sized launch, so the result
+                               never depends on this value (50..200)                           */
 } vsbpp_config;
 
 int vsbpp_get_config(vsbpp_config *out);

@@ -51,6 +51,7 @@ vsbpp_config g_cfg = {
     /*small_m=*/1024,
     /*small_warps_per_block=*/8,
     /*chunk=*/1024,
+    /*slot_pct=*/100,
 };
 
 int record(cudaError_t e) {
@@ -100,13 +101,15 @@ struct Scratch {
     int64_t* h_small = nullptr; int64_t cap_h_small = 0;   // num_bins, total, status
 
     uint32_t* kc_slots = nullptr; int64_t cap_kc_slots = 0;   // global-memory bins
+    int32_t* spill_list = nullptr; int64_t cap_spill_list = 0;  // systems to repack at full size
 
     uint32_t* hist() const { return reinterpret_cast<uint32_t*>(fixed); }
     int64_t* cursor() const { return reinterpret_cast<int64_t*>(fixed + kClasses * kBuckets * 4); }
     int64_t* seg() const { return cursor() + kClasses * kBuckets; }
     int64_t* seg_units() const { return seg() + 8; }
     unsigned long long* queue() const { return reinterpret_cast<unsigned long long*>(seg_units() + 8); }
-    static size_t fixed_bytes() { return kClasses * kBuckets * 4 + kClasses * kBuckets * 8 + 24 * 8; }
+    int64_t* spill_seg() const { return reinterpret_cast<int64_t*>(queue() + 8); }
+    static size_t fixed_bytes() { return kClasses * kBuckets * 4 + kClasses * kBuckets * 8 + 32 * 8; }
 
     int ensure_fixed() {
         if (fixed) return VSBPP_OK;
@@ -125,6 +128,7 @@ struct Scratch {
     void release() {
         cudaFree(cls); cudaFree(order); cudaFree(nu); cudaFree(unit_base); cudaFree(unit_count);
         cudaFree(unit_total); cudaFree(local_types); cudaFree(fixed); cudaFree(kc_slots);
+        cudaFree(spill_list);
         cudaFree(h_w); cudaFree(h_B); cudaFree(h_boi); cudaFree(h_bt); cudaFree(h_small);
         *this = Scratch();
     }
@@ -166,6 +170,7 @@ struct LaunchPlan {
     Mode mode;
     vsbpp_config cfg;
     H1Shape large{}, small{}, wide{}, sub{};
+    H1Shape full{};       // worst-case slots: repacks systems that outgrew large/small
     KCShape kc{};
     int h2_threads = 0, h2_smem = 0, h2_grid = 0, h2_max_bins = 0;
     int prep_grid = 0;
@@ -185,8 +190,10 @@ int64_t cap_for_budget(int budget, int chunk, int slot_size) {
     return lo;
 }
 
+// cap_m = the largest system whose worst case (2m + 32 slots) the shape could
+// hold; slot_cap = pct% of that plus 64 (never above the worst case).
 int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int chunk, int smem_max,
-               int sms, int64_t hard_cap) {
+               int sms, int64_t hard_cap, int pct = 200) {
     const int slot_size = wide ? 8 : 4;
     sh.chunk = chunk;
     int64_t cap = std::min<int64_t>(want_m, cap_for_budget(smem_max / groups, chunk, slot_size));
@@ -195,7 +202,7 @@ int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int ch
     sh.G = G;
     sh.groups = groups;
     sh.cap_m = cap;
-    sh.slot_cap = round4(2 * cap + kMaxTypes);
+    sh.slot_cap = std::min(round4(2 * cap + kMaxTypes), round4(cap * pct / 100 + 64));
     sh.smem = h1_group_bytes(sh.slot_cap, chunk, slot_size) * groups;
     if (sh.smem > smem_max) return VSBPP_ECAPACITY;
     const int occ = h1_blocks_per_sm(wide, G, groups, sh.smem);
@@ -246,7 +253,8 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         lp.h2_threads = std::max(32, (f + 31) / 32 * 32);
         lp.h2_max_bins = 2 * s + (prm.preopen ? kMaxTypes : 0);
         lp.h2_smem = h2_smem_bytes(lp.h2_threads, lp.h2_max_bins);
-        const int occ = h2_blocks_per_sm(lp.h2_threads, lp.h2_smem);
+        const int occ = prm.preopen ? h2_blocks_per_sm(lp.h2_threads, lp.h2_smem)
+                                    : h2_blocks_per_sm_reg(lp.h2_threads, s);
         if (occ <= 0) return record(cudaErrorInvalidConfiguration);
         lp.h2_grid = occ * di.sms;
         const int64_t units = N * ((max_m + s - 1) / s);
@@ -267,17 +275,21 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         return VSBPP_OK;
     }
     lp.mode = {VSBPP_H1, 0, 0};
-    int rc = make_shape(lp.large, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752);
+    int rc = make_shape(lp.full, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752);
+    if (rc != VSBPP_OK) return rc;
+    rc = make_shape(lp.large, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752,
+                    lp.cfg.slot_pct);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.small, false, 1, lp.cfg.small_warps_per_block,
                     std::min<int64_t>(max_m, std::max(1, lp.cfg.small_m)), std::min(chunk, 256), smax,
-                    di.sms, 32752);
+                    di.sms, 32752, lp.cfg.slot_pct);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.wide, true, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30);
     if (rc != VSBPP_OK) return rc;
     cap_grid(lp.large, N);
     cap_grid(lp.small, N);
     cap_grid(lp.wide, N);
+    cap_grid(lp.full, N);
     if (max_m > lp.large.cap_m) {
         KCShape& kc = lp.kc;
         kc.enabled = true;
@@ -304,6 +316,7 @@ int ensure_scratch(Scratch& sc, const LaunchPlan& lp, int64_t N, int64_t total_m
     if ((rc = grow(sc.cls, sc.cap_cls, N))) return rc;
     if (!lp.mode.compose) {
         if ((rc = grow(sc.order, sc.cap_order, N))) return rc;
+        if ((rc = grow(sc.spill_list, sc.cap_spill_list, N))) return rc;
         if (lp.kc.enabled && (rc = grow(sc.kc_slots, sc.cap_kc_slots, int64_t(lp.kc.grid) * lp.kc.bin_cap)))
             return rc;
         return VSBPP_OK;
@@ -356,13 +369,13 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
     if (!lp.mode.compose) {
         pp.classify = 1;
         pp.small_m = plain ? 0 : lp.cfg.small_m;      // plain path: no single-warp class
-        pp.narrow_cap = lp.large.cap_m;
+        pp.narrow_cap = lp.full.cap_m;
         pp.small_cap = lp.small.cap_m;
         pp.wide_cap = lp.wide.cap_m;
         pp.huge_cap = lp.kc.enabled ? lp.kc.cap_m : 0;
         pp.huge_max_B1 = lp.kc.max_B1;
         VS_TRY(validate_launch(pp, prep_grid, st));
-        VS_TRY(order_launch(sc.hist(), sc.cursor(), sc.seg(), sc.queue(), st));
+        VS_TRY(order_launch(sc.hist(), sc.cursor(), sc.seg(), sc.queue(), sc.spill_seg(), st));
         VS_TRY(scatter_launch(in, sc.cls, sc.cursor(), sc.order, prep_grid, st));
         const H1Shape* shapes[3] = {&lp.large, &lp.small, &lp.wide};
         for (int c = 0; c < 3; ++c) {
@@ -375,6 +388,8 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
                     p.range_end = i + 1;
                     p.cls = sc.cls;
                     p.want_cls = kClassLarge;
+                    p.spill_list = sc.spill_list;
+                    p.spill_seg = sc.spill_seg();
                     VS_TRY(h1_launch(false, p, sh.G, 1, 1, sh.smem, st));
                 }
                 continue;
@@ -386,7 +401,20 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
             p.seg = sc.seg();
             p.segment = c;
             p.queue = sc.queue() + c;
+            if (c != kClassWide) {
+                p.spill_list = sc.spill_list;
+                p.spill_seg = sc.spill_seg();
+            }
             VS_TRY(h1_launch(c == kClassWide, p, sh.G, sh.groups, sh.grid, sh.smem, st));
+        }
+        {
+            // systems that outgrew their slots, repacked from the start at full size
+            H1Params p = h1_params(in, out, prm, lp.full);
+            p.order = sc.spill_list;
+            p.seg = sc.spill_seg();
+            p.segment = 0;
+            p.queue = sc.queue() + kClasses;
+            VS_TRY(h1_launch(false, p, lp.full.G, 1, lp.full.grid, lp.full.smem, st));
         }
         if (lp.kc.enabled) {
             KCParams kp;
@@ -693,6 +721,7 @@ int vsbpp_set_config(const vsbpp_config* cfg) {
     if (!h1_shape_supported(1, cfg->small_warps_per_block)) return VSBPP_EINVAL;
     if (cfg->small_m < 0 || cfg->chunk < 32 || cfg->chunk % 32 != 0 || cfg->chunk > 8192)
         return VSBPP_EINVAL;
+    if (cfg->slot_pct < 50 || cfg->slot_pct > 200) return VSBPP_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     g_cfg = *cfg;
     return VSBPP_OK;
@@ -800,9 +829,11 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
     const int smalls[] = {0, 128, 512, 1024, 2048, 4096};
     const int wpb[] = {2, 4, 8, 16};
     const int chunks[] = {256, 512, 1024, 2048};
+    const int pcts[] = {80, 100, 130, 200};
     for (int pass = 0; pass < 2; ++pass) {
-        for (int knob = 0; knob < 4; ++knob) {
-            const int* vals = knob == 0 ? warps : knob == 1 ? smalls : knob == 2 ? wpb : chunks;
+        for (int knob = 0; knob < 5; ++knob) {
+            const int* vals = knob == 0 ? warps : knob == 1 ? smalls : knob == 2 ? wpb
+                              : knob == 3 ? chunks : pcts;
             const int nv = knob == 0 ? 5 : knob == 1 ? 6 : 4;
             for (int v = 0; v < nv; ++v) {
                 vsbpp_config c = cur;
@@ -810,6 +841,7 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
                 if (knob == 1) c.small_m = vals[v];
                 if (knob == 2) c.small_warps_per_block = vals[v];
                 if (knob == 3) c.chunk = vals[v];
+                if (knob == 4) c.slot_pct = vals[v];
                 if (std::memcmp(&c, &cur, sizeof(c)) == 0) continue;
                 double ms = 0;
                 const int r2 = time_config(c, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb,
@@ -834,8 +866,10 @@ int vsbpp_tune_save(const char* path) {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     FILE* f = std::fopen(path, "w");
     if (!f) return VSBPP_EINVAL;
-    std::fprintf(f, "{\"large_warps\": %d, \"small_m\": %d, \"small_warps_per_block\": %d, \"chunk\": %d}\n",
-                 g_cfg.large_warps, g_cfg.small_m, g_cfg.small_warps_per_block, g_cfg.chunk);
+    std::fprintf(f,
+                 "{\"large_warps\": %d, \"small_m\": %d, \"small_warps_per_block\": %d, \"chunk\": %d, "
+                 "\"slot_pct\": %d}\n",
+                 g_cfg.large_warps, g_cfg.small_m, g_cfg.small_warps_per_block, g_cfg.chunk, g_cfg.slot_pct);
     std::fclose(f);
     return VSBPP_OK;
 }
@@ -849,9 +883,10 @@ int vsbpp_tune_load(const char* path) {
     std::fclose(f);
     buf[n] = 0;
     vsbpp_config c = g_cfg;
-    const char* names[4] = {"\"large_warps\"", "\"small_m\"", "\"small_warps_per_block\"", "\"chunk\""};
-    int* fields[4] = {&c.large_warps, &c.small_m, &c.small_warps_per_block, &c.chunk};
-    for (int k = 0; k < 4; ++k) {
+    const char* names[5] = {"\"large_warps\"", "\"small_m\"", "\"small_warps_per_block\"", "\"chunk\"",
+                            "\"slot_pct\""};
+    int* fields[5] = {&c.large_warps, &c.small_m, &c.small_warps_per_block, &c.chunk, &c.slot_pct};
+    for (int k = 0; k < 5; ++k) {
         const char* q = std::strstr(buf, names[k]);
         if (!q) return VSBPP_EINVAL;
         q = std::strchr(q, ':');

@@ -96,6 +96,11 @@ struct H1Params {
     unsigned long long* queue;
     const int32_t* cls;
     int32_t want_cls;
+    // Spill: with spill_list != null, a group whose system would outgrow
+    // slot_cap stops and appends the instance to spill_list (count in
+    // spill_seg[1]); a worst-case-sized launch packs it again from the start.
+    int32_t* spill_list;
+    int64_t* spill_seg;
     unsigned long long* counters;  // null, or {items, fit tests} to add to
     int32_t compose;        // 1: write sublist-local results (see OutView)
     int32_t chunk;          // items staged per step (multiple of 32)
@@ -221,49 +226,35 @@ struct H1Group {
         cp_async_commit();
     }
 
-    // Pack one unit; called by all T threads of the group with identical args.
-    __device__ void pack_unit(const H1Params& p, int64_t uid) const {
-        const int64_t i = p.units.instance_of(uid, p.in.N);
-        if (p.out.status[i] != VSBPP_OK) return;        // rejected by validation
-        if (p.cls && p.cls[i] != p.want_cls) return;
-        const int64_t m = p.in.m(i);
-        int64_t a = 0, k = m;
-        if (p.units.unit_base) {
-            const int64_t g = uid - p.units.unit_base[i];
-            a = g * p.units.sublist;
-            k = (m - a) < p.units.sublist ? (m - a) : p.units.sublist;
-        }
-        const int64_t wb = p.in.w_begin(i);
-        const int32_t* w = p.in.w_all + wb + a;
-        const int32_t n = p.in.n(i);
-        const int32_t* B = p.in.B_all + p.in.B_begin(i);
-        const uint32_t Bl = lane < n ? static_cast<uint32_t>(B[lane]) : 0u;
-        if (warp == 0) Bs[lane] = Bl;
-        int32_t* raw = p.out.bin_of_item + wb + a;
-        int32_t* types_out = p.compose ? (p.out.local_types + wb + a) : (p.out.bin_type + wb);
+    // Rules 3-5 over the unit's items for one criterion CRIT (kRandom: drawn
+    // per item).  Returns false when the unit outgrows its slots (spill).
+    template <int CRIT>
+    __device__ __forceinline__ bool item_loop(const H1Params& p, int64_t i, const int32_t* w,
+                                              int64_t a, int64_t k, int32_t* raw, uint32_t Bl,
+                                              uint32_t& L_io, unsigned long long& fit_tests) const {
         const int chunk = p.chunk;
-
-        uint32_t L = 0;
-        if (p.preopen) {                     // literal Rule 2: one empty bin per type
-            for (int t = 0; t < n; ++t) {
-                if (tid == static_cast<int>(owner(static_cast<uint32_t>(t))))
-                    put_new(static_cast<uint32_t>(t), static_cast<uint32_t>(B[t]), static_cast<uint32_t>(t));
-            }
-            L = static_cast<uint32_t>(n);
-        }
-        if (k > 0) load_chunk(w, 0, k, 0, chunk);
-        unsigned long long fit_tests = 0;      // live bins summed over items (counters)
-
+        uint32_t L = L_io;
+        int jc = 0, buf = 0, par = 0;
         for (int64_t j = 0; j < k; ++j) {
-            const int jc = static_cast<int>(j % chunk);
-            const int buf = static_cast<int>((j / chunk) & 1);
             if (jc == 0) {
                 cp_async_wait_all();
                 sync();                        // this chunk is in shared memory
                 if (j + chunk < k) load_chunk(w, j + chunk, k, buf ^ 1, chunk);
             }
+            if (p.spill_list && L + 2u > static_cast<uint32_t>(p.slot_cap)) {
+                // this system outgrows its slots (each item adds at most two)
+                cp_async_wait_all();
+                if (tid == 0) {
+                    const unsigned long long pos = atomicAdd(
+                        reinterpret_cast<unsigned long long*>(p.spill_seg + 1), 1ull);
+                    p.spill_list[pos] = static_cast<int32_t>(i);
+                }
+                sync();
+                return false;
+            }
             const uint32_t wj = static_cast<uint32_t>(wst[buf * chunk + jc]);
-            const int c = pick_criterion(p.criterion, p.seed, static_cast<uint64_t>(a + j));
+            const int c = CRIT == kRandom ? pick_criterion(kRandom, p.seed, static_cast<uint64_t>(a + j))
+                                          : CRIT;
             const uint32_t nq = (L + 3u) >> 2;
             fit_tests += L;
 
@@ -273,10 +264,10 @@ struct H1Group {
             else key = scan_ff(nq, wj);
             key = Tr::warp_min(key);
             if constexpr (G > 1) {
-                const int par = static_cast<int>(j & 1) * G;
                 if (lane == 0) red[par + warp] = key;
                 sync();
                 key = Tr::warp_min(red[par + (lane % G)]);
+                par ^= G;
             } else {
                 __syncwarp();
             }
@@ -321,7 +312,55 @@ struct H1Group {
             }
             if (tid == 0) raw[j] = static_cast<int32_t>(b);
             L = Ln;
+            if (++jc == chunk) {
+                jc = 0;
+                buf ^= 1;
+            }
         }
+        L_io = L;
+        return true;
+    }
+
+    // Pack one unit; called by all T threads of the group with identical args.
+    __device__ void pack_unit(const H1Params& p, int64_t uid) const {
+        const int64_t i = p.units.instance_of(uid, p.in.N);
+        if (p.out.status[i] != VSBPP_OK) return;        // rejected by validation
+        if (p.cls && p.cls[i] != p.want_cls) return;
+        const int64_t m = p.in.m(i);
+        int64_t a = 0, k = m;
+        if (p.units.unit_base) {
+            const int64_t g = uid - p.units.unit_base[i];
+            a = g * p.units.sublist;
+            k = (m - a) < p.units.sublist ? (m - a) : p.units.sublist;
+        }
+        const int64_t wb = p.in.w_begin(i);
+        const int32_t* w = p.in.w_all + wb + a;
+        const int32_t n = p.in.n(i);
+        const int32_t* B = p.in.B_all + p.in.B_begin(i);
+        const uint32_t Bl = lane < n ? static_cast<uint32_t>(B[lane]) : 0u;
+        if (warp == 0) Bs[lane] = Bl;
+        int32_t* raw = p.out.bin_of_item + wb + a;
+        int32_t* types_out = p.compose ? (p.out.local_types + wb + a) : (p.out.bin_type + wb);
+        const int chunk = p.chunk;
+
+        uint32_t L = 0;
+        if (p.preopen) {                     // literal Rule 2: one empty bin per type
+            for (int t = 0; t < n; ++t) {
+                if (tid == static_cast<int>(owner(static_cast<uint32_t>(t))))
+                    put_new(static_cast<uint32_t>(t), static_cast<uint32_t>(B[t]), static_cast<uint32_t>(t));
+            }
+            L = static_cast<uint32_t>(n);
+        }
+        if (k > 0) load_chunk(w, 0, k, 0, chunk);
+        unsigned long long fit_tests = 0;      // live bins summed over items (counters)
+        bool done;
+        switch (p.criterion) {                 // the item loop, specialised per criterion
+            case kFF: done = item_loop<kFF>(p, i, w, a, k, raw, Bl, L, fit_tests); break;
+            case kBF: done = item_loop<kBF>(p, i, w, a, k, raw, Bl, L, fit_tests); break;
+            case kWF: done = item_loop<kWF>(p, i, w, a, k, raw, Bl, L, fit_tests); break;
+            default: done = item_loop<kRandom>(p, i, w, a, k, raw, Bl, L, fit_tests); break;
+        }
+        if (!done) return;                     // spilled: a full-size launch repacks it
 
         // --- objective (Section 1) and dense ids: used bins in creation order ---
         sync();

@@ -153,4 +153,182 @@ __global__ void h2_pack_kernel(const H2Params p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register version (no preopen): the sublist size S is a compile-time
+// constant, so every loop below has a constant trip count -- at step q at
+// most 2q bins exist -- and one thread's bins, permutation and assignment
+// stay in registers.  Capacities and each item's fallback type (the smallest
+// type holding it) are staged in shared memory once per sublist.
+__device__ __forceinline__ int h2_fact_small(int v) {
+    return v <= 1 ? 1 : v == 2 ? 2 : v == 3 ? 6 : v == 4 ? 24 : v == 5 ? 120 : 720;
+}
+
+// Permutation of lexicographic rank `rank` over k <= S positions.
+template <int S>
+__device__ __forceinline__ void h2_decode(int rank, int k, int (&perm)[S]) {
+    unsigned used = 0;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        perm[q] = 0;
+        if (q < k) {
+            const int f = h2_fact_small(k - 1 - q);
+            int d = rank / f;
+            rank -= d * f;
+            int x = 0;
+#pragma unroll
+            for (int y = S - 1; y >= 0; --y) {       // the d-th unused index, ascending
+                if (y < k && !((used >> y) & 1u)) {
+                    int below = 0;
+#pragma unroll
+                    for (int z = 0; z < S; ++z)
+                        if (z < y && z < k && !((used >> z) & 1u)) ++below;
+                    if (below == d) x = y;
+                }
+            }
+            used |= 1u << x;
+            perm[q] = x;
+        }
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(768) h2_pack_kernel_reg(const H2Params p) {
+    constexpr int kBins = 2 * S;
+    __shared__ unsigned long long wbest[32];
+    __shared__ uint32_t Bs[kMaxTypes];
+    __shared__ uint32_t wsub[8];
+    __shared__ uint32_t tstar[8];
+    const int T = static_cast<int>(blockDim.x);
+    const int tid = static_cast<int>(threadIdx.x);
+    const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
+    int pfull[S];
+    h2_decode<S>(tid, S, pfull);                     // this thread's permutation of S items
+
+    int64_t u_begin = 0, u_end = p.units.unit_base[p.in.N];
+    if (p.only_instance >= 0) {
+        u_begin = p.units.unit_base[p.only_instance];
+        u_end = p.units.unit_base[p.only_instance + 1];
+    }
+    for (int64_t uid = u_begin + blockIdx.x; uid < u_end; uid += gridDim.x) {
+        const int64_t i = p.units.instance_of(uid, p.in.N);
+        if (p.out.status[i] != VSBPP_OK) continue;
+        const int64_t m = p.in.m(i);
+        const int64_t g = uid - p.units.unit_base[i];
+        const int64_t a = g * S;
+        const int k = static_cast<int>((m - a) < S ? (m - a) : S);
+        const int nperm = h2_fact_small(k);
+        const int64_t wb = p.in.w_begin(i);
+        const int32_t* w = p.in.w_all + wb + a;
+        const int32_t n = p.in.n(i);
+        const int32_t* B = p.in.B_all + p.in.B_begin(i);
+        if (tid < kMaxTypes) Bs[tid] = tid < n ? static_cast<uint32_t>(B[tid]) : 0u;
+        if (tid < k) {
+            const int32_t x = w[tid];
+            uint32_t t = 0;
+            for (int y = 0; y < n; ++y)
+                if (B[y] >= x) t = static_cast<uint32_t>(y);
+            wsub[tid] = static_cast<uint32_t>(x);
+            tstar[tid] = t;
+        }
+        __syncthreads();
+
+        unsigned long long key = ~0ull;
+        int perm[S], raw[S];
+        uint32_t res[kBins], typ[kBins];
+#pragma unroll
+        for (int x = 0; x < kBins; ++x) { res[x] = 0; typ[x] = 0; }
+        int L = 0;
+        const bool active = tid < nperm;
+        if (active) {
+            if (k == S) {
+#pragma unroll
+                for (int q = 0; q < S; ++q) perm[q] = pfull[q];
+            } else {
+                h2_decode<S>(tid, k, perm);
+            }
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                raw[q] = 0;
+                if (q < k) {
+                    const int item = perm[q];
+                    const uint32_t wj = wsub[item];
+                    const int c = pick_criterion(p.criterion, p.seed,
+                                                 static_cast<uint64_t>((g * 720 + tid) * 8 + q));
+                    int chosen = -1;
+                    uint32_t cr = 0;
+#pragma unroll
+                    for (int x = 0; x < 2 * q; ++x) {        // Rule 4 over the live bins
+                        const uint32_t r = res[x];
+                        if (x < L && r >= wj &&
+                            (chosen < 0 || (c == kBF && r < cr) || (c == kWF && r > cr))) {
+                            chosen = x;
+                            cr = r;
+                        }
+                    }
+                    uint32_t t = 0;
+                    if (chosen < 0) {                       // smallest type holding w
+                        t = tstar[item];
+                        cr = Bs[t];
+                        chosen = L;
+                        ++L;
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < 2 * q; ++x)
+                            if (x == chosen) t = typ[x];
+                    }
+                    const uint32_t Bt = Bs[t];
+                    const uint32_t r_new = cr - wj;
+                    const bool fire = (static_cast<uint64_t>(Bt) < 2ull * cr) &&
+                                      (2ull * r_new <= static_cast<uint64_t>(Bt));   // Rule 5
+#pragma unroll
+                    for (int x = 0; x < 2 * q + 2 && x < kBins; ++x) {
+                        if (x == chosen) { res[x] = r_new; typ[x] = t; }
+                        if (fire && x == L) { res[x] = Bt; typ[x] = t; }
+                    }
+                    if (fire) ++L;
+                    raw[q] = chosen;
+                }
+            }
+            unsigned long long tot = 0;
+#pragma unroll
+            for (int x = 0; x < kBins; ++x) {
+                const uint32_t cap = Bs[typ[x]];
+                if (x < L && res[x] < cap) tot += cap;
+            }
+            key = (tot << 10) | static_cast<unsigned long long>(tid);
+        }
+        key = warp_min_u64(key);
+        if (lane == 0) wbest[warp] = key;
+        __syncthreads();
+        unsigned long long best = ~0ull;
+        for (int x = 0; x < nwarps; ++x) best = wbest[x] < best ? wbest[x] : best;
+        if (active && tid == static_cast<int>(best & 1023ull)) {
+            // the winning permutation's result, in sublist-local form
+            bool used[kBins];
+            int cnt = 0;
+#pragma unroll
+            for (int x = 0; x < kBins; ++x) {
+                used[x] = x < L && res[x] < Bs[typ[x]];
+                if (used[x]) {
+                    p.out.local_types[wb + a + cnt] = static_cast<int32_t>(typ[x]);
+                    ++cnt;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                if (q < k) {
+                    int d = 0;
+#pragma unroll
+                    for (int x = 0; x < kBins; ++x)
+                        if (x < raw[q] && used[x]) ++d;
+                    p.out.bin_of_item[wb + a + perm[q]] = d;
+                }
+            }
+            p.out.unit_count[uid] = cnt;
+            p.out.unit_total[uid] = static_cast<int64_t>(best >> 10);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace vsbpp

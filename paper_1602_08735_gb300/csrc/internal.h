@@ -31,10 +31,11 @@ int kc_blocks_per_sm(int smem);
 
 cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaStream_t st);
 int h2_blocks_per_sm(int threads, int smem);
+int h2_blocks_per_sm_reg(int threads, int sublist);   // register kernel (no preopen)
 
 cudaError_t validate_launch(const PrepParams& p, int grid, cudaStream_t st);
 cudaError_t order_launch(uint32_t* hist, int64_t* cursor, int64_t* seg, unsigned long long* queue,
-                         cudaStream_t st);
+                         int64_t* spill_seg, cudaStream_t st);
 cudaError_t scatter_launch(const BatchView& in, const int32_t* cls, int64_t* cursor, int32_t* order,
                            int grid, cudaStream_t st);
 cudaError_t unit_scan_launch(int64_t N, const int64_t* nu, int64_t* unit_base, int64_t* seg_units,

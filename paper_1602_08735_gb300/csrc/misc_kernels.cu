@@ -45,10 +45,38 @@ int h1_blocks_per_sm(bool wide, int G, int groups, int smem) {
 }
 
 cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaStream_t st) {
+    if (!p.preopen) {
+        // bins in registers, sublist size fixed at compile time
+        switch (p.sublist) {
+            case 1: h2_pack_kernel_reg<1><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
+            case 2: h2_pack_kernel_reg<2><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
+            case 3: h2_pack_kernel_reg<3><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
+            case 4: h2_pack_kernel_reg<4><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
+            case 5: h2_pack_kernel_reg<5><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
+            case 6: h2_pack_kernel_reg<6><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
+            default: break;
+        }
+    }
     cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(h2_pack_kernel), smem);
     if (e != cudaSuccess) return e;
     h2_pack_kernel<<<grid, threads, smem, st>>>(p);
     return cudaGetLastError();
+}
+
+int h2_blocks_per_sm_reg(int threads, int sublist) {
+    const void* k = nullptr;
+    switch (sublist) {
+        case 1: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<1>); break;
+        case 2: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<2>); break;
+        case 3: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<3>); break;
+        case 4: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<4>); break;
+        case 5: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<5>); break;
+        case 6: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<6>); break;
+        default: return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, 0) != cudaSuccess) return 0;
+    return nb;
 }
 
 int h2_blocks_per_sm(int threads, int smem) {
@@ -79,8 +107,8 @@ cudaError_t validate_launch(const PrepParams& p, int grid, cudaStream_t st) {
 }
 
 cudaError_t order_launch(uint32_t* hist, int64_t* cursor, int64_t* seg, unsigned long long* queue,
-                         cudaStream_t st) {
-    order_kernel<<<1, 32, 0, st>>>(hist, cursor, seg, queue);
+                         int64_t* spill_seg, cudaStream_t st) {
+    order_kernel<<<1, 32, 0, st>>>(hist, cursor, seg, queue, spill_seg);
     return cudaGetLastError();
 }
 

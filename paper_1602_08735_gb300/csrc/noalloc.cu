@@ -125,7 +125,7 @@ extern "C" int vsbpp_pack_batch_noalloc(int64_t N, const int32_t* w_all, const i
     pp.hist = hist;
     const int prep_grid = static_cast<int>(std::min<int64_t>(int64_t(sms) * 8, (N + 7) / 8));
     if (validate_launch(pp, prep_grid, st) != cudaSuccess) return VSBPP_ECUDA;
-    if (order_launch(hist, cursor, seg, queue, st) != cudaSuccess) return VSBPP_ECUDA;
+    if (order_launch(hist, cursor, seg, queue, nullptr, st) != cudaSuccess) return VSBPP_ECUDA;
     if (scatter_launch(in, cls, cursor, order, prep_grid, st) != cudaSuccess) return VSBPP_ECUDA;
     H1Params hp;
     std::memset(&hp, 0, sizeof(hp));

@@ -86,22 +86,38 @@ __global__ void validate_kernel(const PrepParams p) {
     }
 }
 
-// Single thread: histogram -> segment bounds and per-bucket cursors.  The
-// histogram is cleared for the next call; queue counters restart at zero.
+// One warp: histogram -> segment bounds and per-bucket cursors (largest
+// bucket first inside each class).  The histogram is cleared for the next
+// call; queue counters and the spill segment restart at zero.
 __global__ void order_kernel(uint32_t* hist, int64_t* cursor, int64_t* seg,
-                             unsigned long long* queue) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+                             unsigned long long* queue, int64_t* spill_seg) {
+    __shared__ uint32_t h[kClasses * kBuckets];
+    __shared__ int64_t base[kClasses + 1];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+    for (int x = lane; x < kClasses * kBuckets; x += 32) {
+        h[x] = hist[x];
+        hist[x] = 0;
+    }
+    __syncwarp();
+    // per class: descending-bucket exclusive scan, two buckets per lane
     int64_t run = 0;
     for (int c = 0; c < kClasses; ++c) {
-        seg[c] = run;
-        for (int b = kBuckets - 1; b >= 0; --b) {
-            cursor[c * kBuckets + b] = run;
-            run += hist[c * kBuckets + b];
-            hist[c * kBuckets + b] = 0;
-        }
+        const int b_hi = kBuckets - 1 - 2 * lane, b_lo = b_hi - 1;    // lane 0: buckets 63, 62
+        const uint32_t v_hi = h[c * kBuckets + b_hi], v_lo = h[c * kBuckets + b_lo];
+        const uint32_t pair = v_hi + v_lo;
+        const uint32_t ex = warp_exclusive_scan(pair, lane);
+        cursor[c * kBuckets + b_hi] = run + ex;
+        cursor[c * kBuckets + b_lo] = run + ex + v_hi;
+        if (lane == 0) base[c] = run;
+        run += __shfl_sync(kFull, ex + pair, 31);
     }
-    seg[kClasses] = run;
-    for (int q = 0; q < kClasses; ++q) queue[q] = 0ull;
+    if (lane == 0) {
+        for (int c = 0; c < kClasses; ++c) seg[c] = base[c];
+        seg[kClasses] = run;
+    }
+    if (lane <= kClasses) queue[lane] = 0ull;
+    if (spill_seg && lane < 2) spill_seg[lane] = 0;
 }
 
 __global__ void scatter_kernel(BatchView in, const int32_t* cls, int64_t* cursor, int32_t* order) {

@@ -95,7 +95,12 @@ def mixture_weights(rng, p_first: float, first: tuple, second: tuple, m: int) ->
 
 def distinct_capacities(rng, n: int, lo: int, hi: int) -> np.ndarray:
     """n distinct integers in [lo, hi], sorted descending."""
-    return np.sort(rng.choice(np.arange(lo, hi + 1), size=n, replace=False))[::-1].astype(np.int32)
+    if hi - lo + 1 <= 1_000_000:
+        return np.sort(rng.choice(np.arange(lo, hi + 1), size=n, replace=False))[::-1].astype(np.int32)
+    picked = set()
+    while len(picked) < n:           # wide range: draw until n distinct values
+        picked.add(int(rng.integers(lo, hi + 1)))
+    return np.array(sorted(picked, reverse=True), dtype=np.int32)
 
 
 CFG1_B = np.array([100, 70, 40], dtype=np.int32)

@@ -191,3 +191,22 @@ def test_errors():
     assert got.status.tolist() == [0, native.EINVAL, native.ETOOBIG, 0, native.EINVAL]
     ref = run_oracle(b, 1, native.BF)
     assert_same(b, got, ref, "mixed")
+
+
+@pytest.mark.parametrize("pct", [50, 100])
+def test_spill_and_rerun(pct):
+    """Systems that outgrow their shared-memory slots are repacked at full
+    size; the result must not change."""
+    native.set_config(slot_pct=pct)
+    try:
+        rng = np.random.default_rng(77)
+        inst = [(rng.integers(51, 101, size=m).astype(np.int32), np.array([100, 60], dtype=np.int32))
+                for m in (300, 2000, 19000)]            # ~2 bins per item: always spills
+        inst += [I.config3(N=20, m_hi=5000, seed=78).instance(i) for i in range(20)]
+        b = I.from_instances(inst)
+        for crit in H1_CRITERIA:
+            assert_same(b, run_batch(b, 1, crit, seed=3), run_oracle(b, 1, crit, seed=3), f"spill {pct} c{crit}")
+            assert_same(b, run_batch(b, 1, crit, seed=3, plain=True), run_oracle(b, 1, crit, seed=3),
+                        f"spill plain {pct} c{crit}")
+    finally:
+        native.set_config(slot_pct=100)
