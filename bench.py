@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1024, help="instances in the oracle sample")
+    ap.add_argument("--no-side", action="store_true", help="skip configs 1, 2, 4 and 5 side numbers")
+    ap.add_argument("--config4-instances", type=int, default=64)
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="config 5 arrivals per second")
+    ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -155,6 +159,82 @@ class ClockSampler:
             out.update(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), samples=len(sm),
                        reasons=sorted(reasons))
         return out
+
+
+# ----------------------------------------------------------- side numbers
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def single_instance_latency(native, I, dev, stream):
+    """Configs 1 and 2: one instance per call, device-resident, per pass."""
+    import torch
+    out = {}
+    for name, batch in (("config1", I.config1()), ("config2u", I.config2("u")), ("config2m", I.config2("m"))):
+        db = native.DeviceBatch.from_host(batch, device=dev)
+        res = native.DeviceResult.empty(db.N, db.total_items, device=dev)
+        row = {}
+        for (pname, h, c, s_) in PASSES:
+            plan = native.Plan(db.N, db.total_items, db.max_m, h, c, s_)
+            for _ in range(3):
+                plan.run(db, res, stream)
+            e0, e1 = _events(torch)
+            reps = 5
+            e0.record(stream)
+            for _ in range(reps):
+                plan.run(db, res, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[pname] = {"ms": ms, "items_per_s": db.total_items / (ms / 1e3)}
+            plan.close()
+        out[name] = row
+    return out
+
+
+def config4_pass(native, I, dev, stream, N):
+    """Config 4: N instances of 10^6 items (global-memory kernel), one BF pass."""
+    import torch
+    batch = I.config4(N=N)
+    db = native.DeviceBatch.from_host(batch, device=dev)
+    res = native.DeviceResult.empty(db.N, db.total_items, device=dev)
+    plan = native.Plan(db.N, db.total_items, db.max_m, 1, 1, 0)
+    plan.run(db, res, stream)                       # warm-up (records the graph)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record(stream)
+    plan.run(db, res, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ok = int((res.status[:db.N] == 0).sum().item())
+    plan.close()
+    return {"instances": db.N, "items": db.total_items, "pass": "H1-BF", "ms": ms,
+            "items_per_s": db.total_items / (ms / 1e3), "instances_ok": ok}
+
+
+def serving_run(native, I, rate, n_req):
+    """Config 5: Poisson arrivals through the continuous-batching server."""
+    reqs = I.config5(seed=5, num_requests=n_req, rate_per_s=rate)
+    items = sum(len(w) for (_, w, _) in reqs)
+    with native.Server(device_mem_budget=8 << 30, max_slots=64, lanes=8) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for (t_arr, w, B) in reqs:
+            now = time.perf_counter() - t0
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            tickets.append(srv.submit(w, B, 1, 1))
+        bad = 0
+        for t in tickets:
+            rc, _ = srv.poll(t)
+            bad += rc != 0
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    return {"rate_per_s": rate, "requests": n_req, "items": items, "failed": bad,
+            "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
+            "items_per_s": items / wall, "wall_s": wall,
+            "pass": "H1-BF per request", "m": "log-uniform [100, 1e5]"}
 
 
 # ------------------------------------------------------------------ oracle
@@ -347,6 +427,12 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(batch, args.cpu_sample)
 
+    side = {}
+    if not args.no_side:
+        side["single_instance"] = single_instance_latency(native, I, dev, stream)
+        side["config4"] = config4_pass(native, I, dev, stream, args.config4_instances)
+        side["serving"] = serving_run(native, I, args.serve_rate, args.serve_requests)
+
     if rank == 0:
         line = {
             "metric": "items packed/s", "value": value, "unit": "items/s", "n_gpus": ws,
@@ -365,6 +451,7 @@ def run_ours(args, ws, rank, local):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "fit_tests": fit_tests,
+            "side": side,
         }
         print(json.dumps(line), flush=True)
     for pl in plans:
