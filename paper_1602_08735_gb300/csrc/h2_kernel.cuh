@@ -209,125 +209,144 @@ __global__ void __launch_bounds__(768) h2_pack_kernel_reg(const H2Params p) {
         u_begin = p.units.unit_base[p.only_instance];
         u_end = p.units.unit_base[p.only_instance + 1];
     }
-    for (int64_t uid = u_begin + blockIdx.x; uid < u_end; uid += gridDim.x) {
-        const int64_t i = p.units.instance_of(uid, p.in.N);
-        if (p.out.status[i] != VSBPP_OK) continue;
-        const int64_t m = p.in.m(i);
-        const int64_t g = uid - p.units.unit_base[i];
-        const int64_t a = g * S;
-        const int k = static_cast<int>((m - a) < S ? (m - a) : S);
-        const int nperm = h2_fact_small(k);
-        const int64_t wb = p.in.w_begin(i);
-        const int32_t* w = p.in.w_all + wb + a;
-        const int32_t n = p.in.n(i);
+    // Each block takes runs of kRun consecutive sublists, so the instance is
+    // found once per run and its metadata reloaded only when the run crosses
+    // into the next instance (sublists are numbered instance by instance).
+    constexpr int kRun = 16;
+    for (int64_t r0 = u_begin + static_cast<int64_t>(blockIdx.x) * kRun; r0 < u_end;
+         r0 += static_cast<int64_t>(gridDim.x) * kRun) {
+        const int64_t r1 = (r0 + kRun) < u_end ? (r0 + kRun) : u_end;
+        int64_t i = p.units.instance_of(r0, p.in.N);
+        int64_t ub = p.units.unit_base[i], ub_next = p.units.unit_base[i + 1];
+        int32_t st = p.out.status[i];
+        int64_t m = p.in.m(i), wb = p.in.w_begin(i);
+        int32_t n = p.in.n(i);
         const int32_t* B = p.in.B_all + p.in.B_begin(i);
-        if (tid < kMaxTypes) Bs[tid] = tid < n ? static_cast<uint32_t>(B[tid]) : 0u;
-        if (tid < k) {
-            const int32_t x = w[tid];
-            uint32_t t = 0;
-            for (int y = 0; y < n; ++y)
-                if (B[y] >= x) t = static_cast<uint32_t>(y);
-            wsub[tid] = static_cast<uint32_t>(x);
-            tstar[tid] = t;
-        }
-        __syncthreads();
+        for (int64_t uid = r0; uid < r1; ++uid) {
+            while (uid >= ub_next) {                 // next instance with sublists
+                ++i;
+                ub = ub_next;
+                ub_next = p.units.unit_base[i + 1];
+                st = p.out.status[i];
+                m = p.in.m(i);
+                wb = p.in.w_begin(i);
+                n = p.in.n(i);
+                B = p.in.B_all + p.in.B_begin(i);
+            }
+            if (st != VSBPP_OK) continue;
+            const int64_t g = uid - ub;
+            const int64_t a = g * S;
+            const int k = static_cast<int>((m - a) < S ? (m - a) : S);
+            const int nperm = h2_fact_small(k);
+            const int32_t* w = p.in.w_all + wb + a;
+            if (tid < kMaxTypes) Bs[tid] = tid < n ? static_cast<uint32_t>(B[tid]) : 0u;
+            if (tid < k) {
+                const int32_t x = w[tid];
+                uint32_t t = 0;
+                for (int y = 0; y < n; ++y)
+                    if (B[y] >= x) t = static_cast<uint32_t>(y);
+                wsub[tid] = static_cast<uint32_t>(x);
+                tstar[tid] = t;
+            }
+            __syncthreads();
 
-        unsigned long long key = ~0ull;
-        int perm[S], raw[S];
-        uint32_t res[kBins], typ[kBins];
-#pragma unroll
-        for (int x = 0; x < kBins; ++x) { res[x] = 0; typ[x] = 0; }
-        int L = 0;
-        const bool active = tid < nperm;
-        if (active) {
-            if (k == S) {
-#pragma unroll
-                for (int q = 0; q < S; ++q) perm[q] = pfull[q];
-            } else {
-                h2_decode<S>(tid, k, perm);
-            }
-#pragma unroll
-            for (int q = 0; q < S; ++q) {
-                raw[q] = 0;
-                if (q < k) {
-                    const int item = perm[q];
-                    const uint32_t wj = wsub[item];
-                    const int c = pick_criterion(p.criterion, p.seed,
-                                                 static_cast<uint64_t>((g * 720 + tid) * 8 + q));
-                    int chosen = -1;
-                    uint32_t cr = 0;
-#pragma unroll
-                    for (int x = 0; x < 2 * q; ++x) {        // Rule 4 over the live bins
-                        const uint32_t r = res[x];
-                        if (x < L && r >= wj &&
-                            (chosen < 0 || (c == kBF && r < cr) || (c == kWF && r > cr))) {
-                            chosen = x;
-                            cr = r;
+            unsigned long long key = ~0ull;
+            int perm[S], raw[S];
+            uint32_t res[kBins], typ[kBins];
+    #pragma unroll
+            for (int x = 0; x < kBins; ++x) { res[x] = 0; typ[x] = 0; }
+            int L = 0;
+            const bool active = tid < nperm;
+            if (active) {
+                if (k == S) {
+    #pragma unroll
+                    for (int q = 0; q < S; ++q) perm[q] = pfull[q];
+                } else {
+                    h2_decode<S>(tid, k, perm);
+                }
+    #pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    raw[q] = 0;
+                    if (q < k) {
+                        const int item = perm[q];
+                        const uint32_t wj = wsub[item];
+                        const int c = pick_criterion(p.criterion, p.seed,
+                                                     static_cast<uint64_t>((g * 720 + tid) * 8 + q));
+                        int chosen = -1;
+                        uint32_t cr = 0;
+    #pragma unroll
+                        for (int x = 0; x < 2 * q; ++x) {        // Rule 4 over the live bins
+                            const uint32_t r = res[x];
+                            if (x < L && r >= wj &&
+                                (chosen < 0 || (c == kBF && r < cr) || (c == kWF && r > cr))) {
+                                chosen = x;
+                                cr = r;
+                            }
                         }
+                        uint32_t t = 0;
+                        if (chosen < 0) {                       // smallest type holding w
+                            t = tstar[item];
+                            cr = Bs[t];
+                            chosen = L;
+                            ++L;
+                        } else {
+    #pragma unroll
+                            for (int x = 0; x < 2 * q; ++x)
+                                if (x == chosen) t = typ[x];
+                        }
+                        const uint32_t Bt = Bs[t];
+                        const uint32_t r_new = cr - wj;
+                        const bool fire = (static_cast<uint64_t>(Bt) < 2ull * cr) &&
+                                          (2ull * r_new <= static_cast<uint64_t>(Bt));   // Rule 5
+    #pragma unroll
+                        for (int x = 0; x < 2 * q + 2 && x < kBins; ++x) {
+                            if (x == chosen) { res[x] = r_new; typ[x] = t; }
+                            if (fire && x == L) { res[x] = Bt; typ[x] = t; }
+                        }
+                        if (fire) ++L;
+                        raw[q] = chosen;
                     }
-                    uint32_t t = 0;
-                    if (chosen < 0) {                       // smallest type holding w
-                        t = tstar[item];
-                        cr = Bs[t];
-                        chosen = L;
-                        ++L;
-                    } else {
-#pragma unroll
-                        for (int x = 0; x < 2 * q; ++x)
-                            if (x == chosen) t = typ[x];
-                    }
-                    const uint32_t Bt = Bs[t];
-                    const uint32_t r_new = cr - wj;
-                    const bool fire = (static_cast<uint64_t>(Bt) < 2ull * cr) &&
-                                      (2ull * r_new <= static_cast<uint64_t>(Bt));   // Rule 5
-#pragma unroll
-                    for (int x = 0; x < 2 * q + 2 && x < kBins; ++x) {
-                        if (x == chosen) { res[x] = r_new; typ[x] = t; }
-                        if (fire && x == L) { res[x] = Bt; typ[x] = t; }
-                    }
-                    if (fire) ++L;
-                    raw[q] = chosen;
                 }
+                unsigned long long tot = 0;
+    #pragma unroll
+                for (int x = 0; x < kBins; ++x) {
+                    const uint32_t cap = Bs[typ[x]];
+                    if (x < L && res[x] < cap) tot += cap;
+                }
+                key = (tot << 10) | static_cast<unsigned long long>(tid);
             }
-            unsigned long long tot = 0;
-#pragma unroll
-            for (int x = 0; x < kBins; ++x) {
-                const uint32_t cap = Bs[typ[x]];
-                if (x < L && res[x] < cap) tot += cap;
+            key = warp_min_u64(key);
+            if (lane == 0) wbest[warp] = key;
+            __syncthreads();
+            unsigned long long best = ~0ull;
+            for (int x = 0; x < nwarps; ++x) best = wbest[x] < best ? wbest[x] : best;
+            if (active && tid == static_cast<int>(best & 1023ull)) {
+                // the winning permutation's result, in sublist-local form
+                bool used[kBins];
+                int cnt = 0;
+    #pragma unroll
+                for (int x = 0; x < kBins; ++x) {
+                    used[x] = x < L && res[x] < Bs[typ[x]];
+                    if (used[x]) {
+                        p.out.local_types[wb + a + cnt] = static_cast<int32_t>(typ[x]);
+                        ++cnt;
+                    }
+                }
+    #pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    if (q < k) {
+                        int d = 0;
+    #pragma unroll
+                        for (int x = 0; x < kBins; ++x)
+                            if (x < raw[q] && used[x]) ++d;
+                        p.out.bin_of_item[wb + a + perm[q]] = d;
+                    }
+                }
+                p.out.unit_count[uid] = cnt;
+                p.out.unit_total[uid] = static_cast<int64_t>(best >> 10);
             }
-            key = (tot << 10) | static_cast<unsigned long long>(tid);
+            __syncthreads();
         }
-        key = warp_min_u64(key);
-        if (lane == 0) wbest[warp] = key;
-        __syncthreads();
-        unsigned long long best = ~0ull;
-        for (int x = 0; x < nwarps; ++x) best = wbest[x] < best ? wbest[x] : best;
-        if (active && tid == static_cast<int>(best & 1023ull)) {
-            // the winning permutation's result, in sublist-local form
-            bool used[kBins];
-            int cnt = 0;
-#pragma unroll
-            for (int x = 0; x < kBins; ++x) {
-                used[x] = x < L && res[x] < Bs[typ[x]];
-                if (used[x]) {
-                    p.out.local_types[wb + a + cnt] = static_cast<int32_t>(typ[x]);
-                    ++cnt;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < S; ++q) {
-                if (q < k) {
-                    int d = 0;
-#pragma unroll
-                    for (int x = 0; x < kBins; ++x)
-                        if (x < raw[q] && used[x]) ++d;
-                    p.out.bin_of_item[wb + a + perm[q]] = d;
-                }
-            }
-            p.out.unit_count[uid] = cnt;
-            p.out.unit_total[uid] = static_cast<int64_t>(best >> 10);
-        }
-        __syncthreads();
     }
 }
 
