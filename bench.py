@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-side", action="store_true", help="skip configs 1, 2, 4 and 5 side numbers")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default launch config")
     ap.add_argument("--config4-instances", type=int, default=64)
+    ap.add_argument("--config4-m", type=int, default=1_000_000)
+    ap.add_argument("--only", choices=["all", "config4"], default="all",
+                    help="config4: run only the config-4 pass (a small case for profiling)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="config 5 arrivals per second")
     ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
@@ -193,10 +196,10 @@ def single_instance_latency(native, I, dev, stream):
     return out
 
 
-def config4_pass(native, I, dev, stream, N):
+def config4_pass(native, I, dev, stream, N, m=1_000_000):
     """Config 4: N instances of 10^6 items (global-memory kernel), one BF pass."""
     import torch
-    batch = I.config4(N=N)
+    batch = I.config4(N=N, m=m)
     db = native.DeviceBatch.from_host(batch, device=dev)
     res = native.DeviceResult.empty(db.N, db.total_items, device=dev)
     plan = native.Plan(db.N, db.total_items, db.max_m, 1, 1, 0)
@@ -439,7 +442,7 @@ def run_ours(args, ws, rank, local):
     side = {}
     if not args.no_side:
         side["single_instance"] = single_instance_latency(native, I, dev, stream)
-        side["config4"] = config4_pass(native, I, dev, stream, args.config4_instances)
+        side["config4"] = config4_pass(native, I, dev, stream, args.config4_instances, args.config4_m)
         side["serving"] = serving_run(native, I, args.serve_rate, args.serve_requests)
 
     if rank == 0:
@@ -473,6 +476,18 @@ def run_ours(args, ws, rank, local):
 def main():
     args = parse()
     ws, rank, local = dist_setup()
+    if args.only == "config4":
+        import torch
+        from paper_1602_08735_gb300 import build as B
+        from paper_1602_08735_gb300 import instances as I
+        from paper_1602_08735_gb300 import native
+        B.build()
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        r = config4_pass(native, I, dev, torch.cuda.current_stream(dev), args.config4_instances,
+                         args.config4_m)
+        print(json.dumps({"config4": r}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
     else:

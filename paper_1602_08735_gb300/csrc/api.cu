@@ -46,12 +46,13 @@ DeviceInfo& device_info() {
     return di;
 }
 
+// Defaults: the autotuner's choice on the 4096-instance benchmark batch.
 vsbpp_config g_cfg = {
-    /*large_warps=*/8,
-    /*small_m=*/1024,
-    /*small_warps_per_block=*/8,
-    /*chunk=*/1024,
-    /*slot_pct=*/100,
+    /*large_warps=*/4,
+    /*small_m=*/0,
+    /*small_warps_per_block=*/16,
+    /*chunk=*/512,
+    /*slot_pct=*/80,
 };
 
 int record(cudaError_t e) {
@@ -177,13 +178,15 @@ struct LaunchPlan {
 };
 
 int round4(int64_t x) { return static_cast<int>((x + 3) & ~int64_t(3)); }
+// Shared-memory kernels read whole 128-bin segments.
+int round128(int64_t x) { return static_cast<int>((x + 127) & ~int64_t(127)); }
 
 // Largest m whose group footprint fits `budget` bytes (slot_cap = 2m + 32).
 int64_t cap_for_budget(int budget, int chunk, int slot_size) {
     int64_t lo = 0, hi = 1 << 22;
     while (hi - lo > 1) {
         const int64_t mid = (lo + hi) / 2;
-        const int64_t sc = round4(2 * mid + kMaxTypes);
+        const int64_t sc = round128(2 * mid + kMaxTypes);
         const int64_t bytes = h1_group_bytes(static_cast<int>(std::min<int64_t>(sc, 1 << 26)), chunk, slot_size);
         if (bytes <= budget) lo = mid; else hi = mid;
     }
@@ -202,7 +205,7 @@ int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int ch
     sh.G = G;
     sh.groups = groups;
     sh.cap_m = cap;
-    sh.slot_cap = std::min(round4(2 * cap + kMaxTypes), round4(cap * pct / 100 + 64));
+    sh.slot_cap = std::min(round128(2 * cap + kMaxTypes), round128(cap * pct / 100 + 64));
     sh.smem = h1_group_bytes(sh.slot_cap, chunk, slot_size) * groups;
     if (sh.smem > smem_max) return VSBPP_ECAPACITY;
     const int occ = h1_blocks_per_sm(wide, G, groups, sh.smem);
@@ -254,7 +257,7 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         lp.h2_max_bins = 2 * s + (prm.preopen ? kMaxTypes : 0);
         lp.h2_smem = h2_smem_bytes(lp.h2_threads, lp.h2_max_bins);
         const int occ = prm.preopen ? h2_blocks_per_sm(lp.h2_threads, lp.h2_smem)
-                                    : h2_blocks_per_sm_reg(lp.h2_threads, s);
+                                    : h2_blocks_per_sm_reg(lp.h2_threads, s, prm.criterion);
         if (occ <= 0) return record(cudaErrorInvalidConfiguration);
         lp.h2_grid = occ * di.sms;
         const int64_t units = N * ((max_m + s - 1) / s);

@@ -104,7 +104,7 @@ struct H1Params {
     unsigned long long* counters;  // null, or {items, fit tests} to add to
     int32_t compose;        // 1: write sublist-local results (see OutView)
     int32_t chunk;          // items staged per step (multiple of 32)
-    int32_t slot_cap;       // bins per group (multiple of 4)
+    int32_t slot_cap;       // bins per group (multiple of 128: whole segments)
     int32_t group_bytes;    // shared memory per group
 };
 
@@ -113,6 +113,7 @@ __host__ __device__ inline int h1_align16(int x) { return (x + 15) & ~15; }
 __host__ __device__ inline int h1_group_bytes(int slot_cap, int chunk, int slot_size) {
     return h1_align16(slot_cap * slot_size)      // slots
          + h1_align16(slot_cap)                  // bin types (uint8)
+         + h1_align16(4 * ((slot_cap + 127) / 128))   // per-segment largest residual
          + 2 * chunk * 4                         // double-buffered weights
          + kMaxTypes * 4                         // capacities
          + 2 * 32 * slot_size                    // per-warp minima, two buffers
@@ -136,6 +137,7 @@ struct H1Group {
     int tid, lane, warp, gid;
     S* slots;
     uint8_t* typ;
+    uint32_t* segmax;    // largest residual of each 128-bin segment (FF/WF)
     int32_t* wst;
     uint32_t* Bs;
     S* red;
@@ -182,40 +184,68 @@ struct H1Group {
         return best;
     }
 
-    __device__ __forceinline__ S scan_wf(uint32_t nq) const {
-        S best = Tr::kNone;
-#pragma unroll 4
-        for (uint32_t q = tid; q < nq; q += T) {
-            S a, b, c, d;
-            Tr::load_quad(slots, q, a, b, c, d);
-            best = min(best, a ^ Tr::kHi);
-            best = min(best, b ^ Tr::kHi);
-            best = min(best, c ^ Tr::kHi);
-            best = min(best, d ^ Tr::kHi);
-        }
-        return best;
-    }
-
     __device__ __forceinline__ static S ff_key(S s) {
         return ((s & Tr::kLo) << kShift) | (s >> kShift);   // (idx, r)
     }
 
-    __device__ __forceinline__ S scan_ff(uint32_t nq, uint32_t w) const {
+    // --- segment summaries (FF, WF): segment s = bins [128s, 128s+128) is
+    // 32 consecutive quads, all owned by warp s mod G, which alone writes its
+    // bins and its entry of segmax; a warp reads only its own segments, so
+    // the summaries need no barrier.  Each warp returns its own best key.
+    __device__ __forceinline__ S seg_ff(uint32_t nseg, uint32_t w) const {
         const S W = static_cast<S>(w) << kShift;
-        for (uint32_t base = static_cast<uint32_t>(warp) * 32u; base < nq; base += T) {
-            const uint32_t q = base + static_cast<uint32_t>(lane);
-            S cand = Tr::kNone;
-            if (q < nq) {
+        for (uint32_t k0 = 0; static_cast<uint32_t>(warp) + G * k0 < nseg; k0 += 32) {
+            const uint32_t sl = static_cast<uint32_t>(warp) + G * (k0 + static_cast<uint32_t>(lane));
+            const uint32_t mx = sl < nseg ? segmax[sl] : 0u;
+            const unsigned bal = __ballot_sync(kFull, mx >= w);
+            if (bal) {
+                const uint32_t sf = static_cast<uint32_t>(warp) + G * (k0 + __ffs(bal) - 1);
                 S a, b, c, d;
-                Tr::load_quad(slots, q, a, b, c, d);
+                Tr::load_quad(slots, 32u * sf + static_cast<uint32_t>(lane), a, b, c, d);
+                S cand = Tr::kNone;
                 if (a >= W) cand = ff_key(a);
                 else if (b >= W) cand = ff_key(b);
                 else if (c >= W) cand = ff_key(c);
                 else if (d >= W) cand = ff_key(d);
+                return cand;
             }
-            if (__any_sync(kFull, cand != Tr::kNone)) return cand;
         }
         return Tr::kNone;
+    }
+
+    __device__ __forceinline__ S seg_wf(uint32_t nseg) const {
+        uint32_t mx = 0;
+        for (uint32_t k0 = 0; static_cast<uint32_t>(warp) + G * k0 < nseg; k0 += 32) {
+            const uint32_t sl = static_cast<uint32_t>(warp) + G * (k0 + static_cast<uint32_t>(lane));
+            if (sl < nseg) mx = max(mx, segmax[sl]);
+        }
+        mx = __reduce_max_sync(kFull, mx);
+        if (mx == 0u) return Tr::kNone;
+        for (uint32_t k0 = 0; static_cast<uint32_t>(warp) + G * k0 < nseg; k0 += 32) {
+            const uint32_t sl = static_cast<uint32_t>(warp) + G * (k0 + static_cast<uint32_t>(lane));
+            const unsigned bal = __ballot_sync(kFull, sl < nseg && segmax[sl] == mx);
+            if (bal) {
+                const uint32_t sf = static_cast<uint32_t>(warp) + G * (k0 + __ffs(bal) - 1);
+                S a, b, c, d;
+                Tr::load_quad(slots, 32u * sf + static_cast<uint32_t>(lane), a, b, c, d);
+                S best = min(a ^ Tr::kHi, b ^ Tr::kHi);
+                best = min(best, min(c ^ Tr::kHi, d ^ Tr::kHi));
+                return best;
+            }
+        }
+        return Tr::kNone;
+    }
+
+    // Owner warp of segment sg recomputes its largest residual.
+    __device__ __forceinline__ void seg_refresh(uint32_t sg) const {
+        if (static_cast<uint32_t>(warp) != sg % G) return;
+        __syncwarp();
+        S a, b, c, d;
+        Tr::load_quad(slots, 32u * sg + static_cast<uint32_t>(lane), a, b, c, d);
+        const S top = max(max(a, b), max(c, d));
+        const uint32_t r = __reduce_max_sync(kFull, static_cast<uint32_t>(top >> kShift));
+        if (lane == 0) segmax[sg] = r;
+        __syncwarp();
     }
 
     __device__ __forceinline__ void load_chunk(const int32_t* w, int64_t first, int64_t k,
@@ -258,10 +288,11 @@ struct H1Group {
             const uint32_t nq = (L + 3u) >> 2;
             fit_tests += L;
 
+            constexpr bool kSeg = CRIT != kBF;          // segment summaries kept up to date
             S key;
             if (c == kBF) key = scan_bf(nq, wj);
-            else if (c == kWF) key = scan_wf(nq);
-            else key = scan_ff(nq, wj);
+            else if (c == kWF) key = seg_wf((L + 127u) >> 7);
+            else key = seg_ff((L + 127u) >> 7, wj);
             key = Tr::warp_min(key);
             if constexpr (G > 1) {
                 if (lane == 0) red[par + warp] = key;
@@ -310,6 +341,10 @@ struct H1Group {
                 if (tid == static_cast<int>(owner(Ln))) put_new(Ln, Bt, t);
                 ++Ln;
             }
+            if constexpr (kSeg) {
+                seg_refresh(b >> 7);                   // the chosen (or new) bin's segment
+                if (fire && ((Ln - 1u) >> 7) != (b >> 7)) seg_refresh((Ln - 1u) >> 7);
+            }
             if (tid == 0) raw[j] = static_cast<int32_t>(b);
             L = Ln;
             if (++jc == chunk) {
@@ -343,6 +378,18 @@ struct H1Group {
         int32_t* types_out = p.compose ? (p.out.local_types + wb + a) : (p.out.bin_type + wb);
         const int chunk = p.chunk;
 
+        if (p.criterion != kBF) {
+            // Segment reads cover whole 128-bin segments, so every slot must
+            // read as empty until its bin exists: each thread clears its own
+            // quads, each warp its own segment summaries.
+            for (uint32_t q = static_cast<uint32_t>(tid); q < static_cast<uint32_t>(p.slot_cap) / 4u; q += T)
+                Tr::store_quad(slots, q, S(0), S(0), S(0), S(0));
+            const uint32_t nseg = static_cast<uint32_t>(p.slot_cap) / 128u;
+            for (uint32_t sg = static_cast<uint32_t>(warp) + G * static_cast<uint32_t>(lane); sg < nseg;
+                 sg += 32u * G)
+                segmax[sg] = 0u;
+            __syncwarp();
+        }
         uint32_t L = 0;
         if (p.preopen) {                     // literal Rule 2: one empty bin per type
             for (int t = 0; t < n; ++t) {
@@ -350,6 +397,7 @@ struct H1Group {
                     put_new(static_cast<uint32_t>(t), static_cast<uint32_t>(B[t]), static_cast<uint32_t>(t));
             }
             L = static_cast<uint32_t>(n);
+            if (p.criterion != kBF) seg_refresh(0);   // n <= 32 bins: all in segment 0
         }
         if (k > 0) load_chunk(w, 0, k, 0, chunk);
         unsigned long long fit_tests = 0;      // live bins summed over items (counters)
@@ -446,6 +494,8 @@ h1_pack_kernel(const H1Params p) {
     base += h1_align16(p.slot_cap * static_cast<int>(sizeof(S)));
     g.typ = base;
     base += h1_align16(p.slot_cap);
+    g.segmax = reinterpret_cast<uint32_t*>(base);
+    base += h1_align16(4 * ((p.slot_cap + 127) / 128));
     g.wst = reinterpret_cast<int32_t*>(base);
     base += 2 * p.chunk * 4;
     g.Bs = reinterpret_cast<uint32_t*>(base);

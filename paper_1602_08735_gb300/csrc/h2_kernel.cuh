@@ -191,7 +191,7 @@ __device__ __forceinline__ void h2_decode(int rank, int k, int (&perm)[S]) {
     }
 }
 
-template <int S>
+template <int S, int CRIT>
 __global__ void __launch_bounds__(768) h2_pack_kernel_reg(const H2Params p) {
     constexpr int kBins = 2 * S;
     __shared__ unsigned long long wbest[32];
@@ -270,8 +270,10 @@ __global__ void __launch_bounds__(768) h2_pack_kernel_reg(const H2Params p) {
                     if (q < k) {
                         const int item = perm[q];
                         const uint32_t wj = wsub[item];
-                        const int c = pick_criterion(p.criterion, p.seed,
-                                                     static_cast<uint64_t>((g * 720 + tid) * 8 + q));
+                        const int c = CRIT == kRandom
+                                          ? pick_criterion(kRandom, p.seed,
+                                                           static_cast<uint64_t>((g * 720 + tid) * 8 + q))
+                                          : CRIT;
                         int chosen = -1;
                         uint32_t cr = 0;
     #pragma unroll

@@ -31,7 +31,7 @@ int kc_blocks_per_sm(int smem);
 
 cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaStream_t st);
 int h2_blocks_per_sm(int threads, int smem);
-int h2_blocks_per_sm_reg(int threads, int sublist);   // register kernel (no preopen)
+int h2_blocks_per_sm_reg(int threads, int sublist, int criterion);   // register kernel (no preopen)
 
 cudaError_t validate_launch(const PrepParams& p, int grid, cudaStream_t st);
 cudaError_t order_launch(uint32_t* hist, int64_t* cursor, int64_t* seg, unsigned long long* queue,

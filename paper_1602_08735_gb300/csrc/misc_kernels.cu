@@ -44,17 +44,15 @@ int h1_blocks_per_sm(bool wide, int G, int groups, int smem) {
     return wide ? h1_occ_wide_entry(G, groups, smem) : h1_occ_narrow_entry(G, groups, smem);
 }
 
+static const void* h2_reg_kernel(int sublist, int criterion);
+
 cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaStream_t st) {
     if (!p.preopen) {
-        // bins in registers, sublist size fixed at compile time
-        switch (p.sublist) {
-            case 1: h2_pack_kernel_reg<1><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
-            case 2: h2_pack_kernel_reg<2><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
-            case 3: h2_pack_kernel_reg<3><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
-            case 4: h2_pack_kernel_reg<4><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
-            case 5: h2_pack_kernel_reg<5><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
-            case 6: h2_pack_kernel_reg<6><<<grid, threads, 0, st>>>(p); return cudaGetLastError();
-            default: break;
+        // bins in registers; sublist size and criterion fixed at compile time
+        const void* k = h2_reg_kernel(p.sublist, p.criterion);
+        if (k) {
+            void* args[] = {const_cast<H2Params*>(&p)};
+            return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, st);
         }
     }
     cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(h2_pack_kernel), smem);
@@ -63,17 +61,26 @@ cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaSt
     return cudaGetLastError();
 }
 
-int h2_blocks_per_sm_reg(int threads, int sublist) {
-    const void* k = nullptr;
+// Register second-heuristic kernel for (sublist size, criterion).
+static const void* h2_reg_kernel(int sublist, int criterion) {
+#define H2K(S)                                                                          \
+    case S:                                                                             \
+        switch (criterion) {                                                            \
+            case kFF: return reinterpret_cast<const void*>(h2_pack_kernel_reg<S, kFF>);      \
+            case kBF: return reinterpret_cast<const void*>(h2_pack_kernel_reg<S, kBF>);      \
+            case kWF: return reinterpret_cast<const void*>(h2_pack_kernel_reg<S, kWF>);      \
+            default: return reinterpret_cast<const void*>(h2_pack_kernel_reg<S, kRandom>);   \
+        }
     switch (sublist) {
-        case 1: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<1>); break;
-        case 2: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<2>); break;
-        case 3: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<3>); break;
-        case 4: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<4>); break;
-        case 5: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<5>); break;
-        case 6: k = reinterpret_cast<const void*>(h2_pack_kernel_reg<6>); break;
-        default: return 0;
+        H2K(1) H2K(2) H2K(3) H2K(4) H2K(5) H2K(6)
+        default: return nullptr;
     }
+#undef H2K
+}
+
+int h2_blocks_per_sm_reg(int threads, int sublist, int criterion) {
+    const void* k = h2_reg_kernel(sublist, criterion);
+    if (!k) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, 0) != cudaSuccess) return 0;
     return nb;

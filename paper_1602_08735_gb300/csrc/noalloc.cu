@@ -97,7 +97,7 @@ extern "C" int vsbpp_pack_batch_noalloc(int64_t N, const int32_t* w_all, const i
         cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return VSBPP_ECUDA;
     const int64_t cap_m = std::max<int64_t>(max_m, 1);
-    const int slot_cap = static_cast<int>((2 * cap_m + kMaxTypes + 3) & ~int64_t(3));
+    const int slot_cap = static_cast<int>((2 * cap_m + kMaxTypes + 127) & ~int64_t(127));
     const int smem = h1_group_bytes(slot_cap, cfg.chunk, 4);
     if (smem > smax) return VSBPP_ECAPACITY;
     const int occ = h1_blocks_per_sm(false, cfg.large_warps, 1, smem);

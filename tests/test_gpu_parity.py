@@ -140,23 +140,39 @@ def test_batch_equals_single_calls():
 
 @pytest.mark.parametrize("chunk", [32, 96, 4096])
 def test_chunk_boundaries(chunk):
+    saved = native.get_config()
     native.set_config(chunk=chunk)
     try:
         b = I.config3(N=40, m_hi=5000, seed=8)
-        assert_same(b, run_batch(b, 1, native.FF), run_oracle(b, 1, native.FF), f"chunk {chunk}")
+        for crit in (native.FF, native.BF, native.WF):
+            assert_same(b, run_batch(b, 1, crit), run_oracle(b, 1, crit), f"chunk {chunk} c{crit}")
     finally:
-        native.set_config(chunk=1024)
+        native.set_config(**saved)
 
 
-@pytest.mark.parametrize("warps", [2, 4, 16, 32])
+@pytest.mark.parametrize("warps", [2, 4, 8, 16, 32])
 def test_group_sizes(warps):
+    saved = native.get_config()
     native.set_config(large_warps=warps, small_m=64)
     try:
         b = I.config3(N=40, m_hi=4000, seed=9)
-        for crit in (native.BF, native.FF, native.WF):
-            assert_same(b, run_batch(b, 1, crit), run_oracle(b, 1, crit), f"G={warps} c{crit}")
+        for crit in (native.BF, native.FF, native.WF, native.RANDOM):
+            assert_same(b, run_batch(b, 1, crit, seed=1), run_oracle(b, 1, crit, seed=1), f"G={warps} c{crit}")
     finally:
-        native.set_config(large_warps=8, small_m=1024)
+        native.set_config(**saved)
+
+
+@pytest.mark.parametrize("small_m", [0, 300, 3000])
+def test_single_warp_class(small_m):
+    saved = native.get_config()
+    native.set_config(small_m=small_m)
+    try:
+        b = I.config3(N=60, m_hi=4000, seed=10)
+        for crit in (native.BF, native.FF, native.WF, native.RANDOM):
+            assert_same(b, run_batch(b, 1, crit, seed=2), run_oracle(b, 1, crit, seed=2),
+                        f"small_m={small_m} c{crit}")
+    finally:
+        native.set_config(**saved)
 
 
 def test_edge_cases():
@@ -197,6 +213,7 @@ def test_errors():
 def test_spill_and_rerun(pct):
     """Systems that outgrow their shared-memory slots are repacked at full
     size; the result must not change."""
+    saved = native.get_config()
     native.set_config(slot_pct=pct)
     try:
         rng = np.random.default_rng(77)
@@ -209,4 +226,4 @@ def test_spill_and_rerun(pct):
             assert_same(b, run_batch(b, 1, crit, seed=3, plain=True), run_oracle(b, 1, crit, seed=3),
                         f"spill plain {pct} c{crit}")
     finally:
-        native.set_config(slot_pct=100)
+        native.set_config(**saved)
