@@ -150,6 +150,7 @@ struct Mode {
 struct H1Shape {
     int G, groups;
     int chunk;
+    int bf_index;         // BF residual index laid out in shared memory
     int slot_cap;
     int smem;
     int grid;
@@ -182,12 +183,13 @@ int round4(int64_t x) { return static_cast<int>((x + 3) & ~int64_t(3)); }
 int round128(int64_t x) { return static_cast<int>((x + 127) & ~int64_t(127)); }
 
 // Largest m whose group footprint fits `budget` bytes (slot_cap = 2m + 32).
-int64_t cap_for_budget(int budget, int chunk, int slot_size) {
+int64_t cap_for_budget(int budget, int chunk, int slot_size, int G, int bf_index) {
     int64_t lo = 0, hi = 1 << 22;
     while (hi - lo > 1) {
         const int64_t mid = (lo + hi) / 2;
         const int64_t sc = round128(2 * mid + kMaxTypes);
-        const int64_t bytes = h1_group_bytes(static_cast<int>(std::min<int64_t>(sc, 1 << 26)), chunk, slot_size);
+        const int64_t bytes = h1_group_bytes(static_cast<int>(std::min<int64_t>(sc, 1 << 26)), chunk,
+                                             slot_size, G, bf_index);
         if (bytes <= budget) lo = mid; else hi = mid;
     }
     return lo;
@@ -196,17 +198,18 @@ int64_t cap_for_budget(int budget, int chunk, int slot_size) {
 // cap_m = the largest system whose worst case (2m + 32 slots) the shape could
 // hold; slot_cap = pct% of that plus 64 (never above the worst case).
 int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int chunk, int smem_max,
-               int sms, int64_t hard_cap, int pct = 200) {
+               int sms, int64_t hard_cap, int pct, int bf_index) {
     const int slot_size = wide ? 8 : 4;
     sh.chunk = chunk;
-    int64_t cap = std::min<int64_t>(want_m, cap_for_budget(smem_max / groups, chunk, slot_size));
+    sh.bf_index = bf_index;
+    int64_t cap = std::min<int64_t>(want_m, cap_for_budget(smem_max / groups, chunk, slot_size, G, bf_index));
     cap = std::min<int64_t>(cap, hard_cap);
     cap = std::max<int64_t>(cap, 1);
     sh.G = G;
     sh.groups = groups;
     sh.cap_m = cap;
     sh.slot_cap = std::min(round128(2 * cap + kMaxTypes), round128(cap * pct / 100 + 64));
-    sh.smem = h1_group_bytes(sh.slot_cap, chunk, slot_size) * groups;
+    sh.smem = h1_group_bytes(sh.slot_cap, chunk, slot_size, G, bf_index) * groups;
     if (sh.smem > smem_max) return VSBPP_ECAPACITY;
     const int occ = h1_blocks_per_sm(wide, G, groups, sh.smem);
     if (occ <= 0) return record(cudaErrorInvalidConfiguration);
@@ -271,23 +274,26 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         const int G = one_warp ? 1 : lp.cfg.large_warps;
         const int groups = one_warp ? lp.cfg.small_warps_per_block : 1;
         const int sub_chunk = one_warp ? std::min(chunk, 256) : chunk;
-        int rc = make_shape(lp.sub, true, G, groups, s, sub_chunk, smax, di.sms, 1 << 30);
+        const int bfi = prm.criterion == VSBPP_BF || prm.criterion == VSBPP_RANDOM;
+        int rc = make_shape(lp.sub, true, G, groups, s, sub_chunk, smax, di.sms, 1 << 30, 200, bfi);
         if (rc != VSBPP_OK) return rc;
         if (lp.sub.cap_m < s) return VSBPP_ECAPACITY;
         cap_grid(lp.sub, N * ((max_m + s - 1) / s));
         return VSBPP_OK;
     }
     lp.mode = {VSBPP_H1, 0, 0};
-    int rc = make_shape(lp.full, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752);
+    // the BF residual index is laid out when BF items can occur
+    const int bfi = prm.criterion == VSBPP_BF || prm.criterion == VSBPP_RANDOM;
+    int rc = make_shape(lp.full, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752, 200, bfi);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.large, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752,
-                    lp.cfg.slot_pct);
+                    lp.cfg.slot_pct, bfi);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.small, false, 1, lp.cfg.small_warps_per_block,
                     std::min<int64_t>(max_m, std::max(1, lp.cfg.small_m)), std::min(chunk, 256), smax,
-                    di.sms, 32752, lp.cfg.slot_pct);
+                    di.sms, 32752, lp.cfg.slot_pct, bfi);
     if (rc != VSBPP_OK) return rc;
-    rc = make_shape(lp.wide, true, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30);
+    rc = make_shape(lp.wide, true, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30, 200, bfi);
     if (rc != VSBPP_OK) return rc;
     cap_grid(lp.large, N);
     cap_grid(lp.small, N);
@@ -351,6 +357,7 @@ H1Params h1_params(const BatchView& in, const OutView& out, const vsbpp_params& 
     p.cls = nullptr;
     p.want_cls = 0;
     p.counters = g_counters;
+    p.bf_index = sh.bf_index;
     return p;
 }
 
@@ -829,7 +836,7 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
                           st, 3, &cur_ms)))
         return rc;
     const int warps[] = {2, 4, 8, 16, 32};
-    const int smalls[] = {0, 128, 512, 1024, 2048, 4096};
+    const int smalls[] = {0, 128, 512, 1024, 2048, 4096, 8192, 16384};
     const int wpb[] = {2, 4, 8, 16};
     const int chunks[] = {256, 512, 1024, 2048};
     const int pcts[] = {80, 100, 130, 200};
@@ -837,7 +844,7 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
         for (int knob = 0; knob < 5; ++knob) {
             const int* vals = knob == 0 ? warps : knob == 1 ? smalls : knob == 2 ? wpb
                               : knob == 3 ? chunks : pcts;
-            const int nv = knob == 0 ? 5 : knob == 1 ? 6 : 4;
+            const int nv = knob == 0 ? 5 : knob == 1 ? 8 : 4;
             for (int v = 0; v < nv; ++v) {
                 vsbpp_config c = cur;
                 if (knob == 0) c.large_warps = vals[v];

@@ -1,25 +1,34 @@
 // h1_kernel.cuh -- the first heuristic of Section 6.3 on one GB300 SM.
 //
 // One thread group (G warps) runs one membrane system at a time: the items
-// of a unit are taken in list order (Rule 3); for each item every open bin
-// membrane tests whether the item fits (Rule 4, residual >= w) -- the scan
-// below touches every live bin -- and FF / BF / WF (Section 1) picks one,
-// the lowest creation index winning ties.  When nothing fits a bin of the
-// smallest type holding the item is opened; the chosen bin's residual drops
-// by w, and when its load first reaches half its capacity it divides off one
-// empty bin of its type (Rule 5).
+// of a unit are taken in list order (Rule 3); for each item the bin membranes
+// are tested for room (Rule 4, residual >= w) and FF / BF / WF (Section 1)
+// picks one, the lowest creation index winning ties.  When nothing fits a bin
+// of the smallest type holding the item is opened; the chosen bin's residual
+// drops by w, and when its load first reaches half its capacity it divides
+// off one empty bin of its type (Rule 5).
 //
 // GB300 layout.  Bin membranes live in shared memory as one packed word per
-// bin, slot = (residual << SHIFT) | creation index, so that each criterion
-// becomes one unsigned min-reduction over the slots:
+// bin, slot = (residual << SHIFT) | creation index, so each criterion is one
+// unsigned minimum over slots:
 //     BF:  min(slot - (w << SHIFT))  -> (r - w, idx); r < w wraps to the top
 //          half of the range, so a non-fitting bin never wins
 //     WF:  min(slot ^ HI)            -> (~r, idx): most room, lowest index
-//     FF:  first slot >= (w << SHIFT) in index order (early exit per warp)
+//     FF:  min over fitting slots of (idx, r)
 // Slots are read as 16-byte quads; quad q belongs to thread q mod T of the
-// group, and only that thread ever writes those four slots, so a bin update
-// needs no barrier before the next item's scan.  Each item costs one group
-// barrier (the exchange of per-warp minima through a double-buffered array).
+// group, the only writer of those four slots.  A segment (128 bins = 32
+// consecutive quads) therefore belongs to one warp (segment s to warp
+// s mod G), and each warp keeps exact summaries of its own segments:
+//     segmax[s]    the largest residual in segment s (FF, WF)
+//     segres[s]    bit r set iff segment s holds a bin with residual r
+//     wbits[warp]  bit r set iff any of the warp's segments does (BF)
+// so a warp answers the flat scan's question for its bins by scanning one
+// segment: FF its first segment whose maximum is >= w, WF its first segment
+// whose maximum equals its largest, BF -- with r* the least residual >= w in
+// wbits -- its first segment holding r*.  The group minimum of the warps'
+// keys is the flat scan's answer.  A warp reads only summaries it writes, so
+// the only barrier per item is the exchange of per-warp minima (none when
+// G = 1).  BF falls back to the full scan when B_1 > 1023 (no index).
 // Item weights are streamed into shared memory a chunk at a time with
 // cp.async, one chunk ahead of the one being packed.
 #pragma once
@@ -103,6 +112,7 @@ struct H1Params {
     int64_t* spill_seg;
     unsigned long long* counters;  // null, or {items, fit tests} to add to
     int32_t compose;        // 1: write sublist-local results (see OutView)
+    int32_t bf_index;       // 1: the BF residual index is laid out (used when B_1 <= 1023)
     int32_t chunk;          // items staged per step (multiple of 32)
     int32_t slot_cap;       // bins per group (multiple of 128: whole segments)
     int32_t group_bytes;    // shared memory per group
@@ -110,10 +120,15 @@ struct H1Params {
 
 // Shared-memory footprint of one group (host and device agree on this).
 __host__ __device__ inline int h1_align16(int x) { return (x + 15) & ~15; }
-__host__ __device__ inline int h1_group_bytes(int slot_cap, int chunk, int slot_size) {
+constexpr int kIndexMaxRes = 1023;       // residuals the BF index covers (32 words)
+
+__host__ __device__ inline int h1_group_bytes(int slot_cap, int chunk, int slot_size, int G = 1,
+                                              int bf_index = 0) {
+    const int nseg = (slot_cap + 127) / 128;
     return h1_align16(slot_cap * slot_size)      // slots
          + h1_align16(slot_cap)                  // bin types (uint8)
-         + h1_align16(4 * ((slot_cap + 127) / 128))   // per-segment largest residual
+         + h1_align16(4 * nseg)                  // per-segment largest residual
+         + (bf_index ? nseg * 128 + G * 128 : 0) // residual bitmaps: per segment, per warp
          + 2 * chunk * 4                         // double-buffered weights
          + kMaxTypes * 4                         // capacities
          + 2 * 32 * slot_size                    // per-warp minima, two buffers
@@ -138,6 +153,8 @@ struct H1Group {
     S* slots;
     uint8_t* typ;
     uint32_t* segmax;    // largest residual of each 128-bin segment (FF/WF)
+    uint32_t* segres;    // [segment][32 words]: residuals present in the segment (BF)
+    uint32_t* wbits;     // [warp][32 words]: residuals present in the warp's segments (BF)
     int32_t* wst;
     uint32_t* Bs;
     S* red;
@@ -236,15 +253,81 @@ struct H1Group {
         return Tr::kNone;
     }
 
-    // Owner warp of segment sg recomputes its largest residual.
-    __device__ __forceinline__ void seg_refresh(uint32_t sg) const {
+    // BF with the residual index: r* = least residual >= w present in this
+    // warp's segments, then the warp's first segment holding r*; in it the BF
+    // key minimum is r* at its lowest index (no bin of the warp has a
+    // residual in [w, r*)).
+    __device__ __forceinline__ S seg_bf(uint32_t nseg, uint32_t w) const {
+        const uint32_t* wb = wbits + warp * 32;
+        uint32_t word = wb[lane];
+        const uint32_t wi = w >> 5;
+        if (static_cast<uint32_t>(lane) < wi) word = 0u;
+        else if (static_cast<uint32_t>(lane) == wi) word &= ~((1u << (w & 31)) - 1u);
+        const unsigned bal = __ballot_sync(kFull, word != 0u);
+        if (!bal) return Tr::kNone;
+        const int src = __ffs(bal) - 1;
+        const uint32_t rs = static_cast<uint32_t>(src) * 32u +
+                            static_cast<uint32_t>(__ffs(__shfl_sync(kFull, word, src)) - 1);
+        const uint32_t rw = rs >> 5, rbit = 1u << (rs & 31);
+        for (uint32_t k0 = 0; static_cast<uint32_t>(warp) + G * k0 < nseg; k0 += 32) {
+            const uint32_t sl = static_cast<uint32_t>(warp) + G * (k0 + static_cast<uint32_t>(lane));
+            const bool has = sl < nseg && (segres[sl * 32 + rw] & rbit);
+            const unsigned b2 = __ballot_sync(kFull, has);
+            if (b2) {
+                const uint32_t sf = static_cast<uint32_t>(warp) + G * (k0 + __ffs(b2) - 1);
+                S a, b, c, d;
+                Tr::load_quad(slots, 32u * sf + static_cast<uint32_t>(lane), a, b, c, d);
+                const S W = static_cast<S>(w) << kShift;
+                S best = min(a - W, b - W);
+                best = min(best, min(c - W, d - W));
+                return best;
+            }
+        }
+        return Tr::kNone;
+    }
+
+    // Owner warp of segment sg brings its summaries up to date after the
+    // owners' slot writes of this item: the segment maximum (seg), and for the
+    // BF index (idx) the removal of r_removed if no bin of the segment holds it
+    // any more (and from the warp's bitmap if none of its segments does), and
+    // the addition of r_add1 / r_add2 (residual 0 never fits and is not kept).
+    __device__ __forceinline__ void seg_update(uint32_t sg, bool seg, bool idx, uint32_t nseg,
+                                               int64_t r_removed, uint32_t r_add1,
+                                               uint32_t r_add2) const {
         if (static_cast<uint32_t>(warp) != sg % G) return;
         __syncwarp();
         S a, b, c, d;
         Tr::load_quad(slots, 32u * sg + static_cast<uint32_t>(lane), a, b, c, d);
-        const S top = max(max(a, b), max(c, d));
-        const uint32_t r = __reduce_max_sync(kFull, static_cast<uint32_t>(top >> kShift));
-        if (lane == 0) segmax[sg] = r;
+        if (seg) {
+            const S top = max(max(a, b), max(c, d));
+            const uint32_t r = __reduce_max_sync(kFull, static_cast<uint32_t>(top >> kShift));
+            if (lane == 0) segmax[sg] = r;
+        }
+        if (idx) {
+            uint32_t* sr = segres + sg * 32;
+            uint32_t* wb = wbits + warp * 32;
+            if (r_removed > 0) {
+                const S R = static_cast<S>(r_removed);
+                const bool here = (a >> kShift) == R || (b >> kShift) == R || (c >> kShift) == R ||
+                                  (d >> kShift) == R;
+                if (!__any_sync(kFull, here)) {
+                    const uint32_t rw = static_cast<uint32_t>(r_removed) >> 5;
+                    const uint32_t rbit = 1u << (static_cast<uint32_t>(r_removed) & 31);
+                    if (lane == 0) sr[rw] &= ~rbit;
+                    __syncwarp();
+                    bool any = false;
+                    for (uint32_t k0 = 0; static_cast<uint32_t>(warp) + G * k0 < nseg; k0 += 32) {
+                        const uint32_t sl = static_cast<uint32_t>(warp) + G * (k0 + static_cast<uint32_t>(lane));
+                        any |= sl < nseg && (segres[sl * 32 + rw] & rbit);
+                    }
+                    if (!__any_sync(kFull, any) && lane == 0) wb[rw] &= ~rbit;
+                }
+            }
+            if (lane == 0) {
+                if (r_add1 > 0) { sr[r_add1 >> 5] |= 1u << (r_add1 & 31); wb[r_add1 >> 5] |= 1u << (r_add1 & 31); }
+                if (r_add2 > 0) { sr[r_add2 >> 5] |= 1u << (r_add2 & 31); wb[r_add2 >> 5] |= 1u << (r_add2 & 31); }
+            }
+        }
         __syncwarp();
     }
 
@@ -261,7 +344,8 @@ struct H1Group {
     template <int CRIT>
     __device__ __forceinline__ bool item_loop(const H1Params& p, int64_t i, const int32_t* w,
                                               int64_t a, int64_t k, int32_t* raw, uint32_t Bl,
-                                              uint32_t& L_io, unsigned long long& fit_tests) const {
+                                              bool use_idx, uint32_t& L_io,
+                                              unsigned long long& fit_tests) const {
         const int chunk = p.chunk;
         uint32_t L = L_io;
         int jc = 0, buf = 0, par = 0;
@@ -288,11 +372,12 @@ struct H1Group {
             const uint32_t nq = (L + 3u) >> 2;
             fit_tests += L;
 
-            constexpr bool kSeg = CRIT != kBF;          // segment summaries kept up to date
+            constexpr bool kSeg = CRIT != kBF;          // segment maxima kept up to date
+            const uint32_t nseg = (L + 127u) >> 7;
             S key;
-            if (c == kBF) key = scan_bf(nq, wj);
-            else if (c == kWF) key = seg_wf((L + 127u) >> 7);
-            else key = seg_ff((L + 127u) >> 7, wj);
+            if (c == kBF) key = use_idx ? seg_bf(nseg, wj) : scan_bf(nq, wj);
+            else if (c == kWF) key = seg_wf(nseg);
+            else key = seg_ff(nseg, wj);
             key = Tr::warp_min(key);
             if constexpr (G > 1) {
                 if (lane == 0) red[par + warp] = key;
@@ -341,9 +426,14 @@ struct H1Group {
                 if (tid == static_cast<int>(owner(Ln))) put_new(Ln, Bt, t);
                 ++Ln;
             }
-            if constexpr (kSeg) {
-                seg_refresh(b >> 7);                   // the chosen (or new) bin's segment
-                if (fire && ((Ln - 1u) >> 7) != (b >> 7)) seg_refresh((Ln - 1u) >> 7);
+            if (kSeg || use_idx) {                     // summaries of the touched segments
+                const uint32_t sb = b >> 7, sf = (Ln - 1u) >> 7;
+                const uint32_t nseg_after = (Ln + 127u) >> 7;
+                const bool same = fire && sf == sb;
+                seg_update(sb, kSeg, use_idx, nseg_after, hit ? static_cast<int64_t>(r_old) : -1,
+                           static_cast<uint32_t>(r_new), same ? static_cast<uint32_t>(Bt) : 0u);
+                if (fire && !same)
+                    seg_update(sf, kSeg, use_idx, nseg_after, -1, static_cast<uint32_t>(Bt), 0u);
             }
             if (tid == 0) raw[j] = static_cast<int32_t>(b);
             L = Ln;
@@ -378,16 +468,21 @@ struct H1Group {
         int32_t* types_out = p.compose ? (p.out.local_types + wb + a) : (p.out.bin_type + wb);
         const int chunk = p.chunk;
 
-        if (p.criterion != kBF) {
+        const bool use_seg = p.criterion != kBF;
+        const bool use_idx = p.bf_index && (p.criterion == kBF || p.criterion == kRandom) &&
+                             __shfl_sync(kFull, Bl, 0) <= static_cast<uint32_t>(kIndexMaxRes);
+        if (use_seg || use_idx) {
             // Segment reads cover whole 128-bin segments, so every slot must
             // read as empty until its bin exists: each thread clears its own
             // quads, each warp its own segment summaries.
             for (uint32_t q = static_cast<uint32_t>(tid); q < static_cast<uint32_t>(p.slot_cap) / 4u; q += T)
                 Tr::store_quad(slots, q, S(0), S(0), S(0), S(0));
             const uint32_t nseg = static_cast<uint32_t>(p.slot_cap) / 128u;
-            for (uint32_t sg = static_cast<uint32_t>(warp) + G * static_cast<uint32_t>(lane); sg < nseg;
-                 sg += 32u * G)
-                segmax[sg] = 0u;
+            for (uint32_t sg = static_cast<uint32_t>(warp); sg < nseg; sg += G) {
+                if (use_seg && lane == 0) segmax[sg] = 0u;
+                if (use_idx) segres[sg * 32 + lane] = 0u;
+            }
+            if (use_idx) wbits[warp * 32 + lane] = 0u;
             __syncwarp();
         }
         uint32_t L = 0;
@@ -397,16 +492,28 @@ struct H1Group {
                     put_new(static_cast<uint32_t>(t), static_cast<uint32_t>(B[t]), static_cast<uint32_t>(t));
             }
             L = static_cast<uint32_t>(n);
-            if (p.criterion != kBF) seg_refresh(0);   // n <= 32 bins: all in segment 0
+            // n <= 32 bins, all in segment 0 (warp 0's): enter them in its summaries
+            if (warp == 0 && (use_seg || use_idx)) {
+                __syncwarp();
+                if (use_seg && lane == 0) segmax[0] = static_cast<uint32_t>(B[0]);
+                if (use_idx) {
+                    const uint32_t r = lane < n ? static_cast<uint32_t>(B[lane]) : 0u;
+                    if (r > 0u) {
+                        atomicOr(&segres[r >> 5], 1u << (r & 31));
+                        atomicOr(&wbits[r >> 5], 1u << (r & 31));
+                    }
+                }
+                __syncwarp();
+            }
         }
         if (k > 0) load_chunk(w, 0, k, 0, chunk);
         unsigned long long fit_tests = 0;      // live bins summed over items (counters)
         bool done;
         switch (p.criterion) {                 // the item loop, specialised per criterion
-            case kFF: done = item_loop<kFF>(p, i, w, a, k, raw, Bl, L, fit_tests); break;
-            case kBF: done = item_loop<kBF>(p, i, w, a, k, raw, Bl, L, fit_tests); break;
-            case kWF: done = item_loop<kWF>(p, i, w, a, k, raw, Bl, L, fit_tests); break;
-            default: done = item_loop<kRandom>(p, i, w, a, k, raw, Bl, L, fit_tests); break;
+            case kFF: done = item_loop<kFF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
+            case kBF: done = item_loop<kBF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
+            case kWF: done = item_loop<kWF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
+            default: done = item_loop<kRandom>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
         }
         if (!done) return;                     // spilled: a full-size launch repacks it
 
@@ -496,6 +603,9 @@ h1_pack_kernel(const H1Params p) {
     base += h1_align16(p.slot_cap);
     g.segmax = reinterpret_cast<uint32_t*>(base);
     base += h1_align16(4 * ((p.slot_cap + 127) / 128));
+    g.segres = reinterpret_cast<uint32_t*>(base);
+    g.wbits = g.segres + ((p.slot_cap + 127) / 128) * 32;
+    if (p.bf_index) base += ((p.slot_cap + 127) / 128) * 128 + G * 128;
     g.wst = reinterpret_cast<int32_t*>(base);
     base += 2 * p.chunk * 4;
     g.Bs = reinterpret_cast<uint32_t*>(base);

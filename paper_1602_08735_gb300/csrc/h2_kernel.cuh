@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(768) h2_pack_kernel_reg(const H2Params p) {
                                                            static_cast<uint64_t>((g * 720 + tid) * 8 + q))
                                           : CRIT;
                         int chosen = -1;
-                        uint32_t cr = 0;
+                        uint32_t cr = 0, ct = 0;             // residual and type of the choice
     #pragma unroll
                         for (int x = 0; x < 2 * q; ++x) {        // Rule 4 over the live bins
                             const uint32_t r = res[x];
@@ -283,27 +283,25 @@ __global__ void __launch_bounds__(768) h2_pack_kernel_reg(const H2Params p) {
                                 (chosen < 0 || (c == kBF && r < cr) || (c == kWF && r > cr))) {
                                 chosen = x;
                                 cr = r;
+                                ct = typ[x];
                             }
                         }
-                        uint32_t t = 0;
-                        if (chosen < 0) {                       // smallest type holding w
-                            t = tstar[item];
-                            cr = Bs[t];
+                        const bool opened = chosen < 0;
+                        if (opened) {                           // smallest type holding w
+                            ct = tstar[item];
+                            cr = Bs[ct];
                             chosen = L;
                             ++L;
-                        } else {
-    #pragma unroll
-                            for (int x = 0; x < 2 * q; ++x)
-                                if (x == chosen) t = typ[x];
                         }
-                        const uint32_t Bt = Bs[t];
+                        const uint32_t Bt = Bs[ct];
                         const uint32_t r_new = cr - wj;
                         const bool fire = (static_cast<uint64_t>(Bt) < 2ull * cr) &&
                                           (2ull * r_new <= static_cast<uint64_t>(Bt));   // Rule 5
     #pragma unroll
                         for (int x = 0; x < 2 * q + 2 && x < kBins; ++x) {
-                            if (x == chosen) { res[x] = r_new; typ[x] = t; }
-                            if (fire && x == L) { res[x] = Bt; typ[x] = t; }
+                            if (x == chosen) res[x] = r_new;
+                            if ((opened && x == chosen) || (fire && x == L)) typ[x] = ct;
+                            if (fire && x == L) res[x] = Bt;
                         }
                         if (fire) ++L;
                         raw[q] = chosen;

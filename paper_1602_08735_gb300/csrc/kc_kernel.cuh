@@ -233,26 +233,37 @@ __global__ void __launch_bounds__(32) kc_pack_kernel(const KCParams p) {
                 t = low & 31u;
                 b = static_cast<uint32_t>(tile) * kTileBins + idx;
                 const uint32_t r_new = r_old - wj;
-                // tile maximum and presence of r_old after the update, from registers
-                uint32_t mx = 0;
-                bool other = false;
+                // Tile maximum and presence of r_old after the update, from the
+                // registers.  The updated slot sits in lane (idx/4)%32, register
+                // 4*(idx/128) + idx%4.
+                const int own_lane = static_cast<int>((idx >> 2) & 31u);
+                const int own_reg = static_cast<int>(((idx >> 7) << 2) | (idx & 3u));
+                const uint32_t new_slot = (r_new << 16) | low;
+                const uint32_t old_max = W.tile_max[tile];
+                uint32_t mx = old_max;
+                if (r_old == old_max) {            // the chosen bin held the maximum
+                    uint32_t top = 0;
 #pragma unroll
-                for (int x = 0; x < 4 * kTileQuadsPerLane; ++x) {
-                    const uint32_t sl = s[x];
-                    // register x of this lane holds tile position 128*(x/4) + 4*lane + x%4
-                    const bool me = ((x & 3) + 4 * lane + 128 * (x >> 2)) == static_cast<int>(idx);
-                    const uint32_t r = me ? r_new : (sl >> 16);
-                    mx = max(mx, r);
-                    other |= (!me && (sl >> 16) == r_old);
+                    for (int x = 0; x < 4 * kTileQuadsPerLane; ++x) {
+                        const uint32_t sl = (lane == own_lane && x == own_reg) ? new_slot : s[x];
+                        top = max(top, sl);
+                    }
+                    mx = __reduce_max_sync(kFull, top) >> 16;
                 }
-                mx = __reduce_max_sync(kFull, mx);
-                const bool still = __any_sync(kFull, other);
+                bool still = true;
+                if (W.track) {                      // does the tile still hold r_old?
+                    bool other = false;
+#pragma unroll
+                    for (int x = 0; x < 4 * kTileQuadsPerLane; ++x)
+                        other |= (s[x] >> 16) == r_old && !(lane == own_lane && x == own_reg);
+                    still = __any_sync(kFull, other);
+                }
                 if (lane == 0) {
-                    W.slots[b] = (r_new << 16) | low;
+                    W.slots[b] = new_slot;
                     W.tile_max[tile] = static_cast<uint16_t>(mx);
                 }
                 __syncwarp();
-                W.refresh_sup(static_cast<uint32_t>(tile));
+                if (mx != old_max) W.refresh_sup(static_cast<uint32_t>(tile));
                 if (W.track) {
                     W.pres_drop(r_old, static_cast<uint32_t>(tile), still);
                     W.pres_set(r_new, static_cast<uint32_t>(tile));

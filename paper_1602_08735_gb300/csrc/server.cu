@@ -5,8 +5,9 @@
 // requests in arrival order whenever a slot is free and the request's device
 // memory fits in the remaining budget; an admitted request gets its own
 // device buffers (stream-ordered allocator) and is packed by the same kernels
-// as vsbpp_pack_device on one of several streams ("lanes"), so requests that
-// arrive while others run are packed concurrently with them.  A host callback
+// as vsbpp_pack_device on one of several streams ("lanes", the one with the
+// fewest items in flight), so requests that arrive while others run are
+// packed concurrently with them.  A host callback
 // at the end of each request's stream work time-stamps completion and returns
 // its slot and memory, which lets the next waiting request in.
 #include <algorithm>
@@ -90,7 +91,7 @@ struct vsbpp_server {
     std::unordered_map<uint64_t, Req*> tickets;
     size_t in_use = 0;
     int in_flight = 0;
-    int next_lane = 0;
+    std::vector<int64_t> lane_items;   // items in flight per lane
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread worker;
@@ -115,6 +116,7 @@ struct Req {
     int32_t* h_out = nullptr;    // pinned: bin_of_item[m], bin_type[m], 3 x int64
     void* d_buf = nullptr;
     int status = VSBPP_OK;
+    int lane = 0;
     bool done = false;
     Clock::time_point t_submit, t_done;
 
@@ -133,6 +135,7 @@ void finish(Req* r, int status) {
     r->done = true;
     s->in_flight -= 1;
     s->in_use -= r->need;
+    s->lane_items[r->lane] -= std::max<int64_t>(r->m, 1);
     s->completed += 1;
     s->items += r->m;
     s->t_last = now;
@@ -204,8 +207,13 @@ void worker_main(vsbpp_server* s) {
             s->waiting.pop_front();
             s->in_flight += 1;
             s->in_use += r->need;
-            st = s->lanes[s->next_lane];
-            s->next_lane = (s->next_lane + 1) % s->nlanes;
+            // the lane with the fewest items in flight
+            int best = 0;
+            for (int l = 1; l < s->nlanes; ++l)
+                if (s->lane_items[l] < s->lane_items[best]) best = l;
+            r->lane = best;
+            s->lane_items[best] += std::max<int64_t>(r->m, 1);
+            st = s->lanes[best];
             if (!s->any) {
                 s->any = true;
                 s->t_first = Clock::now();
@@ -248,6 +256,7 @@ int vsbpp_server_create(size_t device_mem_budget, int32_t max_slots, int32_t lan
         }
         s->lanes.push_back(st);
     }
+    s->lane_items.assign(static_cast<size_t>(lanes), 0);
     s->worker = std::thread(worker_main, s);
     *out = s;
     return VSBPP_OK;
