@@ -153,7 +153,9 @@ struct H1Group {
     S* slots;
     uint8_t* typ;
     uint32_t* segmax;    // largest residual of each 128-bin segment (FF/WF)
-    uint32_t* segres;    // [segment][32 words]: residuals present in the segment (BF)
+    uint32_t* segres;    // [32 words][segment]: residuals present in the segment (BF);
+                         // word-major so a warp's lanes read consecutive segments
+    uint32_t nsegcap;    // segments in the slot array (the segres row length)
     uint32_t* wbits;     // [warp][32 words]: residuals present in the warp's segments (BF)
     int32_t* wst;
     uint32_t* Bs;
@@ -271,7 +273,7 @@ struct H1Group {
         const uint32_t rw = rs >> 5, rbit = 1u << (rs & 31);
         for (uint32_t k0 = 0; static_cast<uint32_t>(warp) + G * k0 < nseg; k0 += 32) {
             const uint32_t sl = static_cast<uint32_t>(warp) + G * (k0 + static_cast<uint32_t>(lane));
-            const bool has = sl < nseg && (segres[sl * 32 + rw] & rbit);
+            const bool has = sl < nseg && (segres[rw * nsegcap + sl] & rbit);
             const unsigned b2 = __ballot_sync(kFull, has);
             if (b2) {
                 const uint32_t sf = static_cast<uint32_t>(warp) + G * (k0 + __ffs(b2) - 1);
@@ -304,7 +306,6 @@ struct H1Group {
             if (lane == 0) segmax[sg] = r;
         }
         if (idx) {
-            uint32_t* sr = segres + sg * 32;
             uint32_t* wb = wbits + warp * 32;
             if (r_removed > 0) {
                 const S R = static_cast<S>(r_removed);
@@ -313,19 +314,25 @@ struct H1Group {
                 if (!__any_sync(kFull, here)) {
                     const uint32_t rw = static_cast<uint32_t>(r_removed) >> 5;
                     const uint32_t rbit = 1u << (static_cast<uint32_t>(r_removed) & 31);
-                    if (lane == 0) sr[rw] &= ~rbit;
+                    if (lane == 0) segres[rw * nsegcap + sg] &= ~rbit;
                     __syncwarp();
                     bool any = false;
                     for (uint32_t k0 = 0; static_cast<uint32_t>(warp) + G * k0 < nseg; k0 += 32) {
                         const uint32_t sl = static_cast<uint32_t>(warp) + G * (k0 + static_cast<uint32_t>(lane));
-                        any |= sl < nseg && (segres[sl * 32 + rw] & rbit);
+                        any |= sl < nseg && (segres[rw * nsegcap + sl] & rbit);
                     }
                     if (!__any_sync(kFull, any) && lane == 0) wb[rw] &= ~rbit;
                 }
             }
             if (lane == 0) {
-                if (r_add1 > 0) { sr[r_add1 >> 5] |= 1u << (r_add1 & 31); wb[r_add1 >> 5] |= 1u << (r_add1 & 31); }
-                if (r_add2 > 0) { sr[r_add2 >> 5] |= 1u << (r_add2 & 31); wb[r_add2 >> 5] |= 1u << (r_add2 & 31); }
+                if (r_add1 > 0) {
+                    segres[(r_add1 >> 5) * nsegcap + sg] |= 1u << (r_add1 & 31);
+                    wb[r_add1 >> 5] |= 1u << (r_add1 & 31);
+                }
+                if (r_add2 > 0) {
+                    segres[(r_add2 >> 5) * nsegcap + sg] |= 1u << (r_add2 & 31);
+                    wb[r_add2 >> 5] |= 1u << (r_add2 & 31);
+                }
             }
         }
         __syncwarp();
@@ -446,6 +453,207 @@ struct H1Group {
         return true;
     }
 
+    // One-warp item loop (G == 1) driven entirely by the summaries: segment
+    // maxima for FF/WF items and the residual index for BF items.  The chain
+    // per item is short: each lane prepares its candidate's commit data (type,
+    // capacity) while the warp reduction runs, the winning lane -- the one that
+    // scanned the chosen bin -- writes, and the chosen segment's summaries are
+    // updated from the quad already in registers.  With one warp the owner rule
+    // is not needed; __syncwarp orders the writes before the next item.
+    template <int CRIT>
+    __device__ __forceinline__ bool item_loop_warp(const H1Params& p, int64_t i, const int32_t* w,
+                                                   int64_t a, int64_t k, int32_t* raw, uint32_t Bl,
+                                                   bool B1_indexed, uint32_t& L_io,
+                                                   unsigned long long& fit_tests) const {
+        constexpr bool kSeg = CRIT != kBF;                        // FF or WF items occur
+        constexpr bool kIdx = CRIT == kBF || CRIT == kRandom;     // BF items occur
+        const int chunk = p.chunk;
+        const uint32_t* wb = wbits;
+        uint32_t L = L_io;
+        int jc = 0, buf = 0;
+        for (int64_t j = 0; j < k; ++j) {
+            if (jc == 0) {
+                cp_async_wait_all();
+                __syncwarp();
+                if (j + chunk < k) load_chunk(w, j + chunk, k, buf ^ 1, chunk);
+            }
+            if (p.spill_list && L + 2u > static_cast<uint32_t>(p.slot_cap)) {
+                cp_async_wait_all();
+                if (lane == 0) {
+                    const unsigned long long pos = atomicAdd(
+                        reinterpret_cast<unsigned long long*>(p.spill_seg + 1), 1ull);
+                    p.spill_list[pos] = static_cast<int32_t>(i);
+                }
+                __syncwarp();
+                return false;
+            }
+            const uint32_t wj = static_cast<uint32_t>(wst[buf * chunk + jc]);
+            const int c = CRIT == kRandom ? pick_criterion(kRandom, p.seed, static_cast<uint64_t>(a + j))
+                                          : CRIT;
+            fit_tests += L;
+            const uint32_t nseg = (L + 127u) >> 7;
+
+            // 1. the segment that holds the answer (uniform), or none
+            int sf = -1;
+            if (c == kFF) {
+                for (uint32_t k0 = 0; k0 < nseg; k0 += 32) {
+                    const uint32_t sl = k0 + static_cast<uint32_t>(lane);
+                    const unsigned bal = __ballot_sync(kFull, sl < nseg && segmax[sl] >= wj);
+                    if (bal) { sf = static_cast<int>(k0) + __ffs(bal) - 1; break; }
+                }
+            } else if (c == kWF) {
+                uint32_t mx = 0;
+                for (uint32_t sl = static_cast<uint32_t>(lane); sl < nseg; sl += 32) mx = max(mx, segmax[sl]);
+                mx = __reduce_max_sync(kFull, mx);
+                if (mx >= wj) {
+                    for (uint32_t k0 = 0; k0 < nseg; k0 += 32) {
+                        const uint32_t sl = k0 + static_cast<uint32_t>(lane);
+                        const unsigned bal = __ballot_sync(kFull, sl < nseg && segmax[sl] == mx);
+                        if (bal) { sf = static_cast<int>(k0) + __ffs(bal) - 1; break; }
+                    }
+                }
+            } else {
+                uint32_t word = wb[lane];
+                const uint32_t wi = wj >> 5;
+                if (static_cast<uint32_t>(lane) < wi) word = 0u;
+                else if (static_cast<uint32_t>(lane) == wi) word &= ~((1u << (wj & 31)) - 1u);
+                const unsigned bal = __ballot_sync(kFull, word != 0u);
+                if (bal) {
+                    const int src = __ffs(bal) - 1;
+                    const uint32_t rs = static_cast<uint32_t>(src) * 32u +
+                                        static_cast<uint32_t>(__ffs(__shfl_sync(kFull, word, src)) - 1);
+                    const uint32_t* row = segres + (rs >> 5) * nsegcap;
+                    const uint32_t rbit = 1u << (rs & 31);
+                    for (uint32_t k0 = 0; k0 < nseg; k0 += 32) {
+                        const uint32_t sl = k0 + static_cast<uint32_t>(lane);
+                        const unsigned b2 = __ballot_sync(kFull, sl < nseg && (row[sl] & rbit));
+                        if (b2) { sf = static_cast<int>(k0) + __ffs(b2) - 1; break; }
+                    }
+                }
+            }
+
+            // 2. scan that segment; decode the winner
+            const bool hit = sf >= 0;
+            const S W = static_cast<S>(wj) << kShift;
+            S q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+            uint32_t b, r_old, t, Bt;
+            int winner = 0;
+            if (hit) {
+                Tr::load_quad(slots, 32u * static_cast<uint32_t>(sf) + static_cast<uint32_t>(lane), q0, q1, q2, q3);
+                S kl;
+                if (c == kFF) {
+                    kl = Tr::kNone;
+                    if (q3 >= W) kl = ff_key(q3);
+                    if (q2 >= W) kl = ff_key(q2);
+                    if (q1 >= W) kl = ff_key(q1);
+                    if (q0 >= W) kl = ff_key(q0);
+                } else if (c == kWF) {
+                    kl = min(min(q0 ^ Tr::kHi, q1 ^ Tr::kHi), min(q2 ^ Tr::kHi, q3 ^ Tr::kHi));
+                } else {
+                    kl = min(min(q0 - W, q1 - W), min(q2 - W, q3 - W));
+                }
+                // this lane's candidate bin: its type and capacity, fetched
+                // while the reduction runs
+                const uint32_t bl = c == kFF ? static_cast<uint32_t>(kl >> kShift)
+                                             : static_cast<uint32_t>(kl & Tr::kLo);
+                uint32_t tl = 0;
+                if (kl != Tr::kNone) tl = typ[bl];     // a lane without a candidate reads nothing
+                const uint32_t Btl = __shfl_sync(kFull, Bl, static_cast<int>(tl));
+                const S key = Tr::warp_min(kl);
+                if (c == kFF) {
+                    b = static_cast<uint32_t>(key >> kShift);
+                    r_old = static_cast<uint32_t>(key & Tr::kLo);
+                } else if (c == kBF) {
+                    b = static_cast<uint32_t>(key & Tr::kLo);
+                    r_old = static_cast<uint32_t>(key >> kShift) + wj;
+                } else {
+                    b = static_cast<uint32_t>(key & Tr::kLo);
+                    r_old = static_cast<uint32_t>(Tr::kLo - (key >> kShift));
+                }
+                winner = static_cast<int>((b >> 2) & 31u);
+                t = __shfl_sync(kFull, tl, winner);
+                Bt = __shfl_sync(kFull, Btl, winner);
+            } else {                                   // nothing fits: smallest type holding w
+                t = 31u - static_cast<uint32_t>(__clz(__ballot_sync(kFull, Bl >= wj)));
+                Bt = __shfl_sync(kFull, Bl, static_cast<int>(t));
+                b = L;
+                r_old = Bt;
+            }
+            const uint32_t r_new = r_old - wj;
+            const bool fire = (static_cast<uint64_t>(Bt) < 2ull * r_old) &&
+                              (2ull * r_new <= static_cast<uint64_t>(Bt));        // Rule 5
+            const uint32_t Lf = hit ? L : L + 1u;         // where a divided-off bin goes
+            if (lane == winner) {
+                slots[b] = (static_cast<S>(r_new) << kShift) | static_cast<S>(b);
+                if (!hit) typ[b] = static_cast<uint8_t>(t);
+                if (fire) {
+                    slots[Lf] = (static_cast<S>(Bt) << kShift) | static_cast<S>(Lf);
+                    typ[Lf] = static_cast<uint8_t>(t);
+                }
+                raw[j] = static_cast<int32_t>(b);
+            }
+
+            // 3. summaries of the touched segments
+            const uint32_t sb = b >> 7, sfire = Lf >> 7;
+            if constexpr (kSeg) {
+                if (hit) {
+                    // new maximum of segment sb from the quad in registers
+                    const S ns = (static_cast<S>(r_new) << kShift) | static_cast<S>(b);
+                    S x0 = q0, x1 = q1, x2 = q2, x3 = q3;
+                    if (lane == winner) {
+                        const uint32_t pos = b & 3u;
+                        x0 = pos == 0 ? ns : x0; x1 = pos == 1 ? ns : x1;
+                        x2 = pos == 2 ? ns : x2; x3 = pos == 3 ? ns : x3;
+                    }
+                    uint32_t top = static_cast<uint32_t>(max(max(x0, x1), max(x2, x3)) >> kShift);
+                    top = __reduce_max_sync(kFull, top);
+                    if (fire && sfire == sb) top = max(top, Bt);
+                    if (lane == 0) segmax[sb] = top;
+                } else if (lane == 0) {
+                    segmax[sb] = max(segmax[sb], r_new);
+                    if (fire && sfire == sb) segmax[sb] = max(segmax[sb], Bt);
+                }
+                if (fire && sfire != sb && lane == 0) segmax[sfire] = max(segmax[sfire], Bt);
+            }
+            if constexpr (kIdx) {
+                if (hit && B1_indexed) {
+                    // does segment sb still hold r_old after the update?
+                    const S Ro = static_cast<S>(r_old);
+                    const uint32_t pos = (lane == winner) ? (b & 3u) : 4u;
+                    const bool here = ((q0 >> kShift) == Ro && pos != 0) || ((q1 >> kShift) == Ro && pos != 1) ||
+                                      ((q2 >> kShift) == Ro && pos != 2) || ((q3 >> kShift) == Ro && pos != 3);
+                    if (!__any_sync(kFull, here)) {
+                        uint32_t* row = segres + (r_old >> 5) * nsegcap;
+                        const uint32_t rbit = 1u << (r_old & 31);
+                        if (lane == 0) row[sb] &= ~rbit;
+                        __syncwarp();
+                        bool any = false;
+                        for (uint32_t sl = static_cast<uint32_t>(lane); sl < nseg; sl += 32) any |= (row[sl] & rbit) != 0u;
+                        if (!__any_sync(kFull, any) && lane == 0) wbits[r_old >> 5] &= ~rbit;
+                    }
+                }
+                if (B1_indexed && lane == 0) {
+                    if (r_new > 0u) {
+                        segres[(r_new >> 5) * nsegcap + sb] |= 1u << (r_new & 31);
+                        wbits[r_new >> 5] |= 1u << (r_new & 31);
+                    }
+                    if (fire) {
+                        segres[(Bt >> 5) * nsegcap + sfire] |= 1u << (Bt & 31);
+                        wbits[Bt >> 5] |= 1u << (Bt & 31);
+                    }
+                }
+            }
+            __syncwarp();
+            L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
+            if (++jc == chunk) {
+                jc = 0;
+                buf ^= 1;
+            }
+        }
+        L_io = L;
+        return true;
+    }
+
     // Pack one unit; called by all T threads of the group with identical args.
     __device__ void pack_unit(const H1Params& p, int64_t uid) const {
         const int64_t i = p.units.instance_of(uid, p.in.N);
@@ -480,7 +688,7 @@ struct H1Group {
             const uint32_t nseg = static_cast<uint32_t>(p.slot_cap) / 128u;
             for (uint32_t sg = static_cast<uint32_t>(warp); sg < nseg; sg += G) {
                 if (use_seg && lane == 0) segmax[sg] = 0u;
-                if (use_idx) segres[sg * 32 + lane] = 0u;
+                if (use_idx) segres[lane * nsegcap + sg] = 0u;
             }
             if (use_idx) wbits[warp * 32 + lane] = 0u;
             __syncwarp();
@@ -499,7 +707,7 @@ struct H1Group {
                 if (use_idx) {
                     const uint32_t r = lane < n ? static_cast<uint32_t>(B[lane]) : 0u;
                     if (r > 0u) {
-                        atomicOr(&segres[r >> 5], 1u << (r & 31));
+                        atomicOr(&segres[(r >> 5) * nsegcap], 1u << (r & 31));   // segment 0
                         atomicOr(&wbits[r >> 5], 1u << (r & 31));
                     }
                 }
@@ -509,12 +717,27 @@ struct H1Group {
         if (k > 0) load_chunk(w, 0, k, 0, chunk);
         unsigned long long fit_tests = 0;      // live bins summed over items (counters)
         bool done;
+        if constexpr (G == 1) {
+            // one warp: the summary-driven loop whenever every criterion it
+            // meets has its summaries (BF needs the residual index)
+            if (p.criterion != kBF && p.criterion != kRandom) {
+                done = p.criterion == kFF ? item_loop_warp<kFF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests)
+                                          : item_loop_warp<kWF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests);
+                goto packed;
+            }
+            if (use_idx) {
+                done = p.criterion == kBF ? item_loop_warp<kBF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests)
+                                          : item_loop_warp<kRandom>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests);
+                goto packed;
+            }
+        }
         switch (p.criterion) {                 // the item loop, specialised per criterion
             case kFF: done = item_loop<kFF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
             case kBF: done = item_loop<kBF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
             case kWF: done = item_loop<kWF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
             default: done = item_loop<kRandom>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
         }
+    packed:
         if (!done) return;                     // spilled: a full-size launch repacks it
 
         // --- objective (Section 1) and dense ids: used bins in creation order ---
@@ -604,7 +827,8 @@ h1_pack_kernel(const H1Params p) {
     g.segmax = reinterpret_cast<uint32_t*>(base);
     base += h1_align16(4 * ((p.slot_cap + 127) / 128));
     g.segres = reinterpret_cast<uint32_t*>(base);
-    g.wbits = g.segres + ((p.slot_cap + 127) / 128) * 32;
+    g.nsegcap = static_cast<uint32_t>((p.slot_cap + 127) / 128);
+    g.wbits = g.segres + g.nsegcap * 32;
     if (p.bf_index) base += ((p.slot_cap + 127) / 128) * 128 + G * 128;
     g.wst = reinterpret_cast<int32_t*>(base);
     base += 2 * p.chunk * 4;
