@@ -155,6 +155,7 @@ struct H1Shape {
     int smem;
     int grid;
     int64_t cap_m;        // largest membrane system (items) the shape holds
+    bool warp_kernel;     // the one-warp kernel (G = 1, narrow, <= 32768 bins)
 };
 
 // Global-memory kernel for membrane systems beyond shared memory.
@@ -182,14 +183,20 @@ int round4(int64_t x) { return static_cast<int>((x + 3) & ~int64_t(3)); }
 // Shared-memory kernels read whole 128-bin segments.
 int round128(int64_t x) { return static_cast<int>((x + 127) & ~int64_t(127)); }
 
+// Shared memory of one group: the one-warp kernel's layout where it applies.
+int group_bytes(bool wide, int G, int slot_cap, int chunk, int bf_index) {
+    if (!wide && G == 1 && h1w_supported(slot_cap)) return h1w_bytes(slot_cap, bf_index);
+    return h1_group_bytes(slot_cap, chunk, wide ? 8 : 4, G, bf_index);
+}
+
 // Largest m whose group footprint fits `budget` bytes (slot_cap = 2m + 32).
-int64_t cap_for_budget(int budget, int chunk, int slot_size, int G, int bf_index) {
+int64_t cap_for_budget(int budget, bool wide, int chunk, int G, int bf_index) {
     int64_t lo = 0, hi = 1 << 22;
     while (hi - lo > 1) {
         const int64_t mid = (lo + hi) / 2;
         const int64_t sc = round128(2 * mid + kMaxTypes);
-        const int64_t bytes = h1_group_bytes(static_cast<int>(std::min<int64_t>(sc, 1 << 26)), chunk,
-                                             slot_size, G, bf_index);
+        const int64_t bytes = group_bytes(wide, G, static_cast<int>(std::min<int64_t>(sc, 1 << 26)), chunk,
+                                          bf_index);
         if (bytes <= budget) lo = mid; else hi = mid;
     }
     return lo;
@@ -198,23 +205,31 @@ int64_t cap_for_budget(int budget, int chunk, int slot_size, int G, int bf_index
 // cap_m = the largest system whose worst case (2m + 32 slots) the shape could
 // hold; slot_cap = pct% of that plus 64 (never above the worst case).
 int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int chunk, int smem_max,
-               int sms, int64_t hard_cap, int pct, int bf_index) {
-    const int slot_size = wide ? 8 : 4;
+               int sms, int64_t hard_cap, int pct, int bf_index, int criterion) {
     sh.chunk = chunk;
     sh.bf_index = bf_index;
-    int64_t cap = std::min<int64_t>(want_m, cap_for_budget(smem_max / groups, chunk, slot_size, G, bf_index));
+    int64_t cap = std::min<int64_t>(want_m, cap_for_budget(smem_max / groups, wide, chunk, G, bf_index));
     cap = std::min<int64_t>(cap, hard_cap);
     cap = std::max<int64_t>(cap, 1);
     sh.G = G;
     sh.groups = groups;
     sh.cap_m = cap;
     sh.slot_cap = std::min(round128(2 * cap + kMaxTypes), round128(cap * pct / 100 + 64));
-    sh.smem = h1_group_bytes(sh.slot_cap, chunk, slot_size, G, bf_index) * groups;
+    sh.warp_kernel = !wide && G == 1 && h1w_supported(sh.slot_cap);
+    sh.smem = group_bytes(wide, G, sh.slot_cap, chunk, bf_index) * groups;
     if (sh.smem > smem_max) return VSBPP_ECAPACITY;
-    const int occ = h1_blocks_per_sm(wide, G, groups, sh.smem);
+    const int occ = sh.warp_kernel ? h1w_blocks_per_sm(sh.slot_cap, criterion, groups, sh.smem)
+                                   : h1_blocks_per_sm(wide, G, groups, sh.smem);
     if (occ <= 0) return record(cudaErrorInvalidConfiguration);
     sh.grid = occ * sms;
     return VSBPP_OK;
+}
+
+// Launch one shape's kernel.
+cudaError_t launch_shape(const H1Shape& sh, bool wide, const H1Params& p, int groups, int grid,
+                         cudaStream_t st) {
+    if (sh.warp_kernel && !wide) return h1w_launch(p, groups, grid, sh.smem, st);
+    return h1_launch(wide, p, sh.G, groups, grid, sh.smem, st);
 }
 
 int check_params(const vsbpp_params* p) {
@@ -275,7 +290,8 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         const int groups = one_warp ? lp.cfg.small_warps_per_block : 1;
         const int sub_chunk = one_warp ? std::min(chunk, 256) : chunk;
         const int bfi = prm.criterion == VSBPP_BF || prm.criterion == VSBPP_RANDOM;
-        int rc = make_shape(lp.sub, true, G, groups, s, sub_chunk, smax, di.sms, 1 << 30, 200, bfi);
+        int rc = make_shape(lp.sub, true, G, groups, s, sub_chunk, smax, di.sms, 1 << 30, 200, bfi,
+                            prm.criterion);
         if (rc != VSBPP_OK) return rc;
         if (lp.sub.cap_m < s) return VSBPP_ECAPACITY;
         cap_grid(lp.sub, N * ((max_m + s - 1) / s));
@@ -284,16 +300,18 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
     lp.mode = {VSBPP_H1, 0, 0};
     // the BF residual index is laid out when BF items can occur
     const int bfi = prm.criterion == VSBPP_BF || prm.criterion == VSBPP_RANDOM;
-    int rc = make_shape(lp.full, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752, 200, bfi);
+    int rc = make_shape(lp.full, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752, 200, bfi,
+                        prm.criterion);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.large, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752,
-                    lp.cfg.slot_pct, bfi);
+                    lp.cfg.slot_pct, bfi, prm.criterion);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.small, false, 1, lp.cfg.small_warps_per_block,
                     std::min<int64_t>(max_m, std::max(1, lp.cfg.small_m)), std::min(chunk, 256), smax,
-                    di.sms, 32752, lp.cfg.slot_pct, bfi);
+                    di.sms, 32752, lp.cfg.slot_pct, bfi, prm.criterion);
     if (rc != VSBPP_OK) return rc;
-    rc = make_shape(lp.wide, true, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30, 200, bfi);
+    rc = make_shape(lp.wide, true, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30, 200, bfi,
+                    prm.criterion);
     if (rc != VSBPP_OK) return rc;
     cap_grid(lp.large, N);
     cap_grid(lp.small, N);
@@ -400,7 +418,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
                     p.want_cls = kClassLarge;
                     p.spill_list = sc.spill_list;
                     p.spill_seg = sc.spill_seg();
-                    VS_TRY(h1_launch(false, p, sh.G, 1, 1, sh.smem, st));
+                    VS_TRY(launch_shape(sh, false, p, 1, 1, st));
                 }
                 continue;
             }
@@ -415,7 +433,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
                 p.spill_list = sc.spill_list;
                 p.spill_seg = sc.spill_seg();
             }
-            VS_TRY(h1_launch(c == kClassWide, p, sh.G, sh.groups, sh.grid, sh.smem, st));
+            VS_TRY(launch_shape(sh, c == kClassWide, p, sh.groups, sh.grid, st));
         }
         {
             // systems that outgrew their slots, repacked from the start at full size
@@ -424,7 +442,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
             p.seg = sc.spill_seg();
             p.segment = 0;
             p.queue = sc.queue() + kClasses;
-            VS_TRY(h1_launch(false, p, lp.full.G, 1, lp.full.grid, lp.full.smem, st));
+            VS_TRY(launch_shape(lp.full, false, p, 1, lp.full.grid, st));
         }
         if (lp.kc.enabled) {
             KCParams kp;
@@ -727,7 +745,7 @@ int vsbpp_get_config(vsbpp_config* out) {
 
 int vsbpp_set_config(const vsbpp_config* cfg) {
     if (!cfg) return VSBPP_EINVAL;
-    if (!h1_shape_supported(cfg->large_warps, 1) || cfg->large_warps < 2) return VSBPP_EINVAL;
+    if (!h1_shape_supported(cfg->large_warps, 1)) return VSBPP_EINVAL;
     if (!h1_shape_supported(1, cfg->small_warps_per_block)) return VSBPP_EINVAL;
     if (cfg->small_m < 0 || cfg->chunk < 32 || cfg->chunk % 32 != 0 || cfg->chunk > 8192)
         return VSBPP_EINVAL;
@@ -835,7 +853,7 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
     if ((rc = time_config(cur, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb, tot, status,
                           st, 3, &cur_ms)))
         return rc;
-    const int warps[] = {2, 4, 8, 16, 32};
+    const int warps[] = {1, 2, 4, 8, 16, 32};
     const int smalls[] = {0, 128, 512, 1024, 2048, 4096, 8192, 16384};
     const int wpb[] = {2, 4, 8, 16};
     const int chunks[] = {256, 512, 1024, 2048};
@@ -844,7 +862,7 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
         for (int knob = 0; knob < 5; ++knob) {
             const int* vals = knob == 0 ? warps : knob == 1 ? smalls : knob == 2 ? wpb
                               : knob == 3 ? chunks : pcts;
-            const int nv = knob == 0 ? 5 : knob == 1 ? 8 : 4;
+            const int nv = knob == 0 ? 6 : knob == 1 ? 8 : 4;
             for (int v = 0; v < nv; ++v) {
                 vsbpp_config c = cur;
                 if (knob == 0) c.large_warps = vals[v];

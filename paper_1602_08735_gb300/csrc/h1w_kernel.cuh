@@ -1,0 +1,464 @@
+// h1w_kernel.cuh -- the first heuristic of Section 6.3, one warp per membrane
+// system, for systems of at most 32768 bins with B_1 <= 32767.
+//
+// Same method as h1_kernel.cuh (Rules 2-6: items in list order, fit test
+// residual >= w, FF / BF / WF with the lowest creation index winning ties,
+// the smallest type holding the item when nothing fits, the Rule 5 division
+// when a bin's load first reaches half its capacity), with the per-item work
+// arranged so that its dependent chain is as short as one warp can make it:
+//
+//   slot    one 32-bit word per bin, (residual << 16) | capacity.  The bin's
+//           index is its position, so a lane knows the index of every slot it
+//           reads, and its capacity (hence its type and its Rule 5 threshold)
+//           travels with the residual: no second lookup per item.
+//   segmax  the largest residual of each 128-bin segment, kept in registers:
+//           lane l holds segments l, l+32, ... (NS per lane).  FF finds its
+//           segment with one warp minimum over (segment, max) keys, WF with
+//           one warp maximum over (max, segment) keys.
+//   index   (BF, B_1 <= 1023) row[r] = bitmap of the segments holding a bin
+//           of residual r (NS words), and the bitmap of residuals present
+//           (32 words, word l in lane l's register).  BF takes the least
+//           residual >= w present (one warp minimum), then the first segment
+//           in its row.
+//
+// Within the chosen segment each lane reads one 16-byte quad; one warp
+// minimum over (index, residual or capacity) keys names the bin, and the
+// segment's new maximum comes from the same read (count of bins at the old
+// maximum and the largest other residual, reduced alongside).  All smem
+// writes of an item are made by lane 0 in program order; one __syncwarp()
+// orders them before the next item's reads.  Item weights are read from
+// global memory a 32-item block ahead, each lane holding one item's weight
+// together with the capacity of the smallest type that holds it.
+#pragma once
+
+#include "h1_kernel.cuh"
+
+namespace vsbpp {
+
+constexpr int kWarpMaxSlots = 32768;      // 8 segment words per lane at most
+
+// Segment words per lane for a system of slot_cap bins (0: too large).
+__host__ __device__ inline int h1w_ns(int slot_cap) {
+    return slot_cap <= 4096 ? 1 : slot_cap <= 8192 ? 2 : slot_cap <= 16384 ? 4
+         : slot_cap <= kWarpMaxSlots ? 8 : 0;
+}
+
+// Shared memory of one warp: slots, the BF rows (1024 residuals x NS words)
+// when laid out, capacities.
+__host__ __device__ inline int h1w_group_bytes(int slot_cap, int bf_index) {
+    const int ns = h1w_ns(slot_cap);
+    return 4 * slot_cap + (bf_index ? 4 * (kIndexMaxRes + 1) * ns : 0) + 4 * kMaxTypes;
+}
+
+template <int NS, int CRIT>
+struct H1Warp {
+    static constexpr bool kSeg = CRIT != kBF;                      // FF or WF items occur
+    static constexpr bool kBFItems = CRIT == kBF || CRIT == kRandom;
+    static constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+
+    uint32_t* slots;
+    uint32_t* rows;      // BF index rows (null when not laid out)
+    uint32_t* Bs;        // capacities, descending
+    int lane;
+
+    // Item weight j (0 past the end of the list).
+    __device__ __forceinline__ uint32_t weight(const int32_t* w, int64_t j, int64_t k) const {
+        return j < k ? static_cast<uint32_t>(__ldg(w + j)) : 0u;
+    }
+
+    // Item descriptor of weight x (item j): x | capacity of the smallest type
+    // holding it << 16, criterion bits at 15 and 31 (RANDOM).  0 for x = 0.
+    __device__ __forceinline__ uint32_t descriptor(uint32_t x, int64_t j, int n, uint64_t seed,
+                                                   int64_t key0) const {
+        if (x == 0u) return 0u;
+        uint32_t bn = 0;
+        for (int t = 0; t < n; ++t) {
+            const uint32_t c = Bs[t];
+            bn = c >= x ? c : bn;
+        }
+        uint32_t d = x | (bn << 16);
+        if (CRIT == kRandom) {
+            const uint32_t c = static_cast<uint32_t>(pick_criterion(kRandom, seed, static_cast<uint64_t>(key0 + j)));
+            d |= ((c & 1u) << 15) | ((c >> 1) << 31);
+        }
+        return d;
+    }
+
+    // Type of a capacity (capacities are distinct and descending).
+    __device__ __forceinline__ uint32_t type_of(uint32_t cap, int n) const {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (Bs[mid] > cap) lo = mid + 1; else hi = mid;
+        }
+        return static_cast<uint32_t>(lo);
+    }
+
+    // BF without the index (B_1 > 1023): the full scan over the live segments.
+    // key = (r - w) << 15 | index; returns kNoKey when nothing fits.
+    __device__ __forceinline__ uint32_t bf_scan(uint32_t wj, uint32_t L) const {
+        uint32_t key = kNoKey;
+        const uint32_t nseg = (L + 127u) >> 7;
+        for (uint32_t s = 0; s < nseg; ++s) {
+            const uint4 Q = reinterpret_cast<const uint4*>(slots)[32u * s + static_cast<uint32_t>(lane)];
+            const uint32_t base = 128u * s + 4u * static_cast<uint32_t>(lane);
+            const uint32_t r0 = Q.x >> 16, r1 = Q.y >> 16, r2 = Q.z >> 16, r3 = Q.w >> 16;
+            if (r3 >= wj) key = min(key, ((r3 - wj) << 15) | (base + 3u));
+            if (r2 >= wj) key = min(key, ((r2 - wj) << 15) | (base + 2u));
+            if (r1 >= wj) key = min(key, ((r1 - wj) << 15) | (base + 1u));
+            if (r0 >= wj) key = min(key, ((r0 - wj) << 15) | base);
+        }
+        return __reduce_min_sync(kFull, key);
+    }
+
+    // Pack items [0, k) of one system.  Returns false when the system would
+    // outgrow slot_cap bins (spill).
+    __device__ __forceinline__ bool run(const H1Params& p, int64_t i, const int32_t* w, int64_t key0,
+                                        int64_t k, int32_t* raw, int n, bool use_idx, uint32_t& L_io,
+                                        unsigned long long& fit_tests) const {
+        uint32_t L = L_io;
+        const uint32_t cap_bins = static_cast<uint32_t>(p.slot_cap);
+        const uint32_t ulane = static_cast<uint32_t>(lane);
+
+        uint32_t sm[NS];                 // segment maxima, segment 32q + lane
+        uint32_t wb = 0;                 // residuals 32*lane .. 32*lane+31 present
+#pragma unroll
+        for (int q = 0; q < NS; ++q) sm[q] = 0;
+        // start state (preopened bins: all in segment 0)
+        if (kSeg && L > 0 && lane == 0) sm[0] = Bs[0];
+        if (kBFItems && use_idx) {
+            for (uint32_t t = 0; t < L; ++t) {
+                const uint32_t r = Bs[t];
+                if ((r >> 5) == ulane) wb |= 1u << (r & 31);
+            }
+        }
+
+        // weights a 32-item block ahead: lane l holds item (block + l)
+        uint32_t dcur = descriptor(weight(w, ulane, k), ulane, n, p.seed, key0);
+        uint32_t wpre = weight(w, 32 + ulane, k);
+        uint32_t d = __shfl_sync(kFull, dcur, 0);
+        uint32_t bout = 0;
+        for (int64_t j = 0; j < k; ++j) {
+            const int jj = static_cast<int>(j & 31);
+            // the next item's descriptor (independent of the packing state)
+            uint32_t dn;
+            if (jj == 31) {
+                dcur = descriptor(wpre, j + 1 + ulane, n, p.seed, key0);
+                wpre = weight(w, j + 33 + ulane, k);
+                dn = __shfl_sync(kFull, dcur, 0);
+            } else {
+                dn = __shfl_sync(kFull, dcur, jj + 1);
+            }
+            if (p.spill_list && L + 2u > cap_bins) {
+                if (lane == 0) {
+                    const unsigned long long pos = atomicAdd(
+                        reinterpret_cast<unsigned long long*>(p.spill_seg + 1), 1ull);
+                    p.spill_list[pos] = static_cast<int32_t>(i);
+                }
+                __syncwarp();
+                return false;
+            }
+            const uint32_t wj = d & 0x7FFFu;
+            const uint32_t Bn = (d >> 16) & 0x7FFFu;
+            const int c = CRIT == kRandom ? static_cast<int>(((d >> 15) & 1u) | ((d >> 30) & 2u)) : CRIT;
+            fit_tests += L;
+
+            // 1. the segment holding the answer
+            bool hit;
+            uint32_t sf = 0, Mseg = 0, R = 0;
+            uint32_t rw[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) rw[q] = 0;
+            bool have_rows = false;
+            uint32_t bfkey = kNoKey;           // full-scan BF answer
+            if (kSeg && c == kFF) {
+                uint32_t key = kNoKey;
+#pragma unroll
+                for (int q = NS - 1; q >= 0; --q)
+                    if (sm[q] >= wj) key = ((32u * q + ulane) << 16) | sm[q];
+                key = __reduce_min_sync(kFull, key);
+                hit = key != kNoKey;
+                sf = key >> 16;
+                Mseg = key & 0xFFFFu;
+            } else if (kSeg && c == kWF) {
+                uint32_t key = 0;
+#pragma unroll
+                for (int q = 0; q < NS; ++q) key = max(key, (sm[q] << 8) | (255u - (32u * q + ulane)));
+                key = __reduce_max_sync(kFull, key);
+                Mseg = key >> 8;
+                sf = 255u - (key & 255u);
+                hit = Mseg >= wj;
+                R = Mseg;
+            } else if (use_idx) {
+                uint32_t x = wb;
+                const uint32_t wi = wj >> 5;
+                if (ulane < wi) x = 0;
+                else if (ulane == wi) x &= ~((1u << (wj & 31)) - 1u);
+                uint32_t key = x ? 32u * ulane + static_cast<uint32_t>(__ffs(x) - 1) : kNoKey;
+                key = __reduce_min_sync(kFull, key);
+                hit = key != kNoKey;
+                R = key;
+                if (hit) {
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) rw[q] = rows[R * NS + q];
+                    have_rows = true;
+#pragma unroll
+                    for (int q = NS - 1; q >= 0; --q)
+                        if (rw[q]) sf = 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1);
+                }
+            } else {
+                bfkey = bf_scan(wj, L);
+                hit = bfkey != kNoKey;
+                sf = (bfkey & 0x7FFFu) >> 7;
+                R = (bfkey >> 15) + wj;
+            }
+            if (kSeg && hit && c == kBF) {
+                // RANDOM: a BF item still keeps the segment maxima exact
+                uint32_t v = 0;
+#pragma unroll
+                for (int q = 0; q < NS; ++q) v = (sf >> 5) == static_cast<uint32_t>(q) ? sm[q] : v;
+                Mseg = __shfl_sync(kFull, v, static_cast<int>(sf & 31));
+            }
+
+            // 2. the chosen bin: index b, old residual, capacity; the segment's
+            //    count of bins at Mseg (cM) and largest other residual (M2)
+            uint32_t b, r_old, Bt, cM = 0, M2 = 0, cnt_old = 0;
+            if (hit) {
+                const uint4 Q = reinterpret_cast<const uint4*>(slots)[32u * sf + ulane];
+                const uint32_t r0 = Q.x >> 16, r1 = Q.y >> 16, r2 = Q.z >> 16, r3 = Q.w >> 16;
+                const uint32_t c0 = Q.x & 0xFFFFu, c1 = Q.y & 0xFFFFu, c2 = Q.z & 0xFFFFu, c3 = Q.w & 0xFFFFu;
+                const uint32_t i0 = 4u * ulane;
+                if (kSeg) {
+                    cM = (r0 == Mseg) + (r1 == Mseg) + (r2 == Mseg) + (r3 == Mseg);
+                    M2 = max(max(r0 != Mseg ? r0 : 0u, r1 != Mseg ? r1 : 0u),
+                             max(r2 != Mseg ? r2 : 0u, r3 != Mseg ? r3 : 0u));
+                }
+                if (c == kFF) {
+                    uint32_t k1 = kNoKey, k2 = kNoKey;
+                    if (r3 >= wj) { k1 = ((i0 + 3u) << 16) | r3; k2 = ((i0 + 3u) << 16) | c3; }
+                    if (r2 >= wj) { k1 = ((i0 + 2u) << 16) | r2; k2 = ((i0 + 2u) << 16) | c2; }
+                    if (r1 >= wj) { k1 = ((i0 + 1u) << 16) | r1; k2 = ((i0 + 1u) << 16) | c1; }
+                    if (r0 >= wj) { k1 = (i0 << 16) | r0; k2 = (i0 << 16) | c0; }
+                    k1 = __reduce_min_sync(kFull, k1);
+                    k2 = __reduce_min_sync(kFull, k2);
+                    cM = __reduce_add_sync(kFull, cM);
+                    M2 = __reduce_max_sync(kFull, M2);
+                    b = 128u * sf + (k1 >> 16);
+                    r_old = k1 & 0xFFFFu;
+                    Bt = k2 & 0xFFFFu;
+                    if (kBFItems && use_idx) {
+                        const uint32_t e = (r0 == r_old) + (r1 == r_old) + (r2 == r_old) + (r3 == r_old);
+                        cnt_old = __reduce_add_sync(kFull, e);
+                    }
+                } else if (bfkey != kNoKey) {
+                    // full-scan BF: the bin is known; its capacity from the slot
+                    b = bfkey & 0x7FFFu;
+                    r_old = R;
+                    Bt = slots[b] & 0xFFFFu;
+                    if (kSeg) {
+                        cM = __reduce_add_sync(kFull, cM);
+                        M2 = __reduce_max_sync(kFull, M2);
+                    }
+                } else {
+                    // WF (R = the largest residual) or indexed BF (R = least >= w)
+                    uint32_t k1 = kNoKey;
+                    if (r3 == R) k1 = ((i0 + 3u) << 16) | c3;
+                    if (r2 == R) k1 = ((i0 + 2u) << 16) | c2;
+                    if (r1 == R) k1 = ((i0 + 1u) << 16) | c1;
+                    if (r0 == R) k1 = (i0 << 16) | c0;
+                    const uint32_t e = (r0 == R) + (r1 == R) + (r2 == R) + (r3 == R);
+                    k1 = __reduce_min_sync(kFull, k1);
+                    cnt_old = __reduce_add_sync(kFull, e);
+                    if (kSeg) {
+                        cM = __reduce_add_sync(kFull, cM);
+                        M2 = __reduce_max_sync(kFull, M2);
+                    }
+                    b = 128u * sf + (k1 >> 16);
+                    r_old = R;
+                    Bt = k1 & 0xFFFFu;
+                }
+            } else {                                   // nothing fits: a new bin of the smallest type
+                b = L;
+                r_old = Bn;
+                Bt = Bn;
+            }
+            const uint32_t r_new = r_old - wj;
+            const bool fire = (Bt < 2u * r_old) && (2u * r_new <= Bt);     // Rule 5
+            const uint32_t Lf = hit ? L : L + 1u;      // where a divided-off bin goes
+            if (lane == 0) {
+                slots[b] = (r_new << 16) | Bt;
+                if (fire) slots[Lf] = (Bt << 16) | Bt;
+            }
+            const uint32_t sb = b >> 7, sfire = Lf >> 7;
+
+            // 3. segment maxima
+            if (kSeg) {
+                const uint32_t top = (r_old != Mseg || cM >= 2u) ? Mseg : max(M2, r_new);
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    const uint32_t s = 32u * q + ulane;
+                    uint32_t v = sm[q];
+                    if (s == sb) v = hit ? top : max(v, r_new);
+                    if (fire && s == sfire) v = max(v, Bt);
+                    sm[q] = v;
+                }
+            }
+            // 4. the BF index
+            if (kBFItems && use_idx) {
+                if (hit && cnt_old == 1u) {
+                    // r_old leaves segment sb
+                    if (!have_rows) {
+#pragma unroll
+                        for (int q = 0; q < NS; ++q) rw[q] = rows[r_old * NS + q];
+                    }
+                    uint32_t any = 0, word = 0;
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) {
+                        if ((sb >> 5) == static_cast<uint32_t>(q)) { rw[q] &= ~(1u << (sb & 31)); word = rw[q]; }
+                        any |= rw[q];
+                    }
+                    if (lane == 0) rows[r_old * NS + (sb >> 5)] = word;
+                    if (!any && (r_old >> 5) == ulane) wb &= ~(1u << (r_old & 31));
+                }
+                if (r_new > 0u) {
+                    if (lane == 0) atomicOr(&rows[r_new * NS + (sb >> 5)], 1u << (sb & 31));
+                    if ((r_new >> 5) == ulane) wb |= 1u << (r_new & 31);
+                }
+                if (fire) {
+                    if (lane == 0) atomicOr(&rows[Bt * NS + (sfire >> 5)], 1u << (sfire & 31));
+                    if ((Bt >> 5) == ulane) wb |= 1u << (Bt & 31);
+                }
+            }
+            L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
+            if (lane == jj) bout = b;
+            if (jj == 31 || j + 1 == k) {
+                if (lane <= jj) raw[j - jj + lane] = static_cast<int32_t>(bout);
+            }
+            d = dn;
+            __syncwarp();
+        }
+        L_io = L;
+        return true;
+    }
+};
+
+// One warp per membrane system; blockDim.x / 32 warps per block, each with
+// p.group_bytes of shared memory.  Direct mode only (no sublists).
+template <int NS, int CRIT>
+__global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = static_cast<int>(threadIdx.x) & 31;
+    const int wid = static_cast<int>(threadIdx.x) >> 5;
+    const int groups = static_cast<int>(blockDim.x) >> 5;
+    unsigned char* base = smem + static_cast<size_t>(wid) * static_cast<size_t>(p.group_bytes);
+    H1Warp<NS, CRIT> g;
+    g.lane = lane;
+    g.slots = reinterpret_cast<uint32_t*>(base);
+    base += 4 * p.slot_cap;
+    g.rows = nullptr;
+    if (p.bf_index) {
+        g.rows = reinterpret_cast<uint32_t*>(base);
+        base += 4 * (kIndexMaxRes + 1) * NS;
+    }
+    g.Bs = reinterpret_cast<uint32_t*>(base);
+
+    int64_t begin, end;
+    if (p.seg) {
+        begin = p.seg[p.segment];
+        end = p.seg[p.segment + 1];
+    } else {
+        begin = p.range_begin;
+        end = p.range_end;
+    }
+    const int64_t count = end - begin;
+    if (count <= 0) return;
+
+    int64_t u = 0;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * groups;
+    if (!p.queue) u = static_cast<int64_t>(blockIdx.x) * groups + wid;
+    for (;;) {
+        if (p.queue) {
+            unsigned long long v = 0;
+            if (lane == 0) v = atomicAdd(p.queue, 1ull);
+            u = static_cast<long long>(__shfl_sync(kFull, v, 0));
+        }
+        if (u >= count) break;
+        const int64_t i = p.order ? static_cast<int64_t>(p.order[begin + u]) : begin + u;
+        if (!p.queue) u += stride;
+
+        if (p.out.status[i] != VSBPP_OK) continue;        // rejected by validation
+        if (p.cls && p.cls[i] != p.want_cls) continue;
+        const int64_t k = p.in.m(i);
+        const int64_t wb = p.in.w_begin(i);
+        const int32_t* w = p.in.w_all + wb;
+        const int n = p.in.n(i);
+        const int32_t* B = p.in.B_all + p.in.B_begin(i);
+        const uint32_t Bl = lane < n ? static_cast<uint32_t>(B[lane]) : 0u;
+        g.Bs[lane] = Bl;
+        int32_t* raw = p.out.bin_of_item + wb;
+        int32_t* types_out = p.out.bin_type + wb;
+        const uint32_t B1 = __shfl_sync(kFull, Bl, 0);
+        const bool use_idx = g.rows != nullptr && H1Warp<NS, CRIT>::kBFItems &&
+                             B1 <= static_cast<uint32_t>(kIndexMaxRes);
+
+        // every slot reads as empty until its bin exists; index rows start clear
+        for (int q = lane; q < p.slot_cap / 4; q += 32)
+            reinterpret_cast<uint4*>(g.slots)[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (use_idx)
+            for (uint32_t x = static_cast<uint32_t>(lane); x < (B1 + 1u) * NS; x += 32u) g.rows[x] = 0u;
+        __syncwarp();
+        uint32_t L = 0;
+        if (p.preopen) {                     // literal Rule 2: one empty bin per type
+            if (lane < n) {
+                g.slots[lane] = (Bl << 16) | Bl;
+                if (use_idx) atomicOr(&g.rows[Bl * NS], 1u);     // segment 0
+            }
+            L = static_cast<uint32_t>(n);
+            __syncwarp();
+        }
+        unsigned long long fit_tests = 0;
+        const bool done = g.run(p, i, w, 0, k, raw, n, use_idx, L, fit_tests);
+        if (!done) continue;                 // spilled: a full-size launch repacks it
+
+        // --- objective (Section 1) and dense ids: used bins in creation order ---
+        __syncwarp();
+        const uint32_t per = (L + 31u) / 32u;
+        uint32_t b0 = static_cast<uint32_t>(lane) * per;
+        if (b0 > L) b0 = L;
+        const uint32_t b1 = (b0 + per) < L ? (b0 + per) : L;
+        uint32_t cnt = 0;
+        for (uint32_t b = b0; b < b1; ++b) {
+            const uint32_t s = g.slots[b];
+            cnt += static_cast<uint32_t>((s >> 16) < (s & 0xFFFFu));
+        }
+        const uint32_t excl = warp_exclusive_scan(cnt, lane);
+        const uint32_t used_total = __shfl_sync(kFull, excl + cnt, 31);
+        uint32_t dd = excl;
+        uint64_t tot = 0;
+        for (uint32_t b = b0; b < b1; ++b) {
+            const uint32_t s = g.slots[b];
+            const uint32_t cap = s & 0xFFFFu;
+            if ((s >> 16) < cap) {
+                types_out[dd] = static_cast<int32_t>(g.type_of(cap, n));
+                g.slots[b] = dd;
+                tot += cap;
+                ++dd;
+            }
+        }
+        __syncwarp();
+        for (int64_t j = lane; j < k; j += 32)
+            raw[j] = static_cast<int32_t>(g.slots[static_cast<uint32_t>(raw[j])]);
+        tot = warp_sum_u64(tot);
+        if (lane == 0) {
+            if (p.counters) {
+                atomicAdd(p.counters, static_cast<unsigned long long>(k));
+                atomicAdd(p.counters + 1, fit_tests);
+            }
+            p.out.num_bins[i] = static_cast<int64_t>(used_total);
+            p.out.total[i] = static_cast<int64_t>(tot);
+        }
+        __syncwarp();                        // shared memory is reused by the next system
+    }
+}
+
+}  // namespace vsbpp

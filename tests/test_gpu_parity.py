@@ -150,7 +150,7 @@ def test_chunk_boundaries(chunk):
         native.set_config(**saved)
 
 
-@pytest.mark.parametrize("warps", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("warps", [1, 2, 4, 8, 16, 32])
 def test_group_sizes(warps):
     saved = native.get_config()
     native.set_config(large_warps=warps, small_m=64)
