@@ -43,11 +43,12 @@ __host__ __device__ inline int h1w_ns(int slot_cap) {
          : slot_cap <= kWarpMaxSlots ? 8 : 0;
 }
 
-// Shared memory of one warp: slots, the BF rows (1024 residuals x NS words)
-// when laid out, capacities.
+// Shared memory of one warp: slots, a 16-byte pad (the write target of a bin
+// that does not divide), the BF rows (1024 residuals x NS words) when laid
+// out, capacities.
 __host__ __device__ inline int h1w_group_bytes(int slot_cap, int bf_index) {
     const int ns = h1w_ns(slot_cap);
-    return 4 * slot_cap + (bf_index ? 4 * (kIndexMaxRes + 1) * ns : 0) + 4 * kMaxTypes;
+    return 4 * slot_cap + 16 + (bf_index ? 4 * (kIndexMaxRes + 1) * ns : 0) + 4 * kMaxTypes;
 }
 
 template <int NS, int CRIT>
@@ -112,9 +113,13 @@ struct H1Warp {
     }
 
     // Pack items [0, k) of one system.  Returns false when the system would
-    // outgrow slot_cap bins (spill).
+    // outgrow slot_cap bins (spill).  IDX: BF items use the residual index
+    // (B_1 <= 1023), else the full scan.  The item step is straight-line code:
+    // the chosen segment's quad is read whether or not a bin fits, and the
+    // fitting / new-bin cases are merged by selects.
+    template <bool IDX>
     __device__ __forceinline__ bool run(const H1Params& p, int64_t i, const int32_t* w, int64_t key0,
-                                        int64_t k, int32_t* raw, int n, bool use_idx, uint32_t& L_io,
+                                        uint32_t k, int32_t* raw, int n, uint32_t& L_io,
                                         unsigned long long& fit_tests) const {
         uint32_t L = L_io;
         const uint32_t cap_bins = static_cast<uint32_t>(p.slot_cap);
@@ -126,7 +131,7 @@ struct H1Warp {
         for (int q = 0; q < NS; ++q) sm[q] = 0;
         // start state (preopened bins: all in segment 0)
         if (kSeg && L > 0 && lane == 0) sm[0] = Bs[0];
-        if (kBFItems && use_idx) {
+        if (IDX) {
             for (uint32_t t = 0; t < L; ++t) {
                 const uint32_t r = Bs[t];
                 if ((r >> 5) == ulane) wb |= 1u << (r & 31);
@@ -138,16 +143,16 @@ struct H1Warp {
         uint32_t wpre = weight(w, 32 + ulane, k);
         uint32_t d = __shfl_sync(kFull, dcur, 0);
         uint32_t bout = 0;
-        for (int64_t j = 0; j < k; ++j) {
-            const int jj = static_cast<int>(j & 31);
+        for (uint32_t j = 0; j < k; ++j) {
+            const uint32_t jj = j & 31u;
             // the next item's descriptor (independent of the packing state)
             uint32_t dn;
-            if (jj == 31) {
-                dcur = descriptor(wpre, j + 1 + ulane, n, p.seed, key0);
-                wpre = weight(w, j + 33 + ulane, k);
+            if (jj == 31u) {
+                dcur = descriptor(wpre, static_cast<int64_t>(j) + 1 + ulane, n, p.seed, key0);
+                wpre = weight(w, static_cast<int64_t>(j) + 33 + ulane, k);
                 dn = __shfl_sync(kFull, dcur, 0);
             } else {
-                dn = __shfl_sync(kFull, dcur, jj + 1);
+                dn = __shfl_sync(kFull, dcur, static_cast<int>(jj + 1u));
             }
             if (p.spill_list && L + 2u > cap_bins) {
                 if (lane == 0) {
@@ -163,14 +168,13 @@ struct H1Warp {
             const int c = CRIT == kRandom ? static_cast<int>(((d >> 15) & 1u) | ((d >> 30) & 2u)) : CRIT;
             fit_tests += L;
 
-            // 1. the segment holding the answer
+            // 1. the segment holding the answer: sf; Mseg = its largest
+            //    residual; R = the residual sought (BF, WF)
             bool hit;
             uint32_t sf = 0, Mseg = 0, R = 0;
             uint32_t rw[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) rw[q] = 0;
-            bool have_rows = false;
-            uint32_t bfkey = kNoKey;           // full-scan BF answer
             if (kSeg && c == kFF) {
                 uint32_t key = kNoKey;
 #pragma unroll
@@ -178,7 +182,7 @@ struct H1Warp {
                     if (sm[q] >= wj) key = ((32u * q + ulane) << 16) | sm[q];
                 key = __reduce_min_sync(kFull, key);
                 hit = key != kNoKey;
-                sf = key >> 16;
+                sf = hit ? key >> 16 : 0u;
                 Mseg = key & 0xFFFFu;
             } else if (kSeg && c == kWF) {
                 uint32_t key = 0;
@@ -189,7 +193,7 @@ struct H1Warp {
                 sf = 255u - (key & 255u);
                 hit = Mseg >= wj;
                 R = Mseg;
-            } else if (use_idx) {
+            } else if (IDX) {
                 uint32_t x = wb;
                 const uint32_t wi = wj >> 5;
                 if (ulane < wi) x = 0;
@@ -197,22 +201,19 @@ struct H1Warp {
                 uint32_t key = x ? 32u * ulane + static_cast<uint32_t>(__ffs(x) - 1) : kNoKey;
                 key = __reduce_min_sync(kFull, key);
                 hit = key != kNoKey;
-                R = key;
-                if (hit) {
+                R = hit ? key : 0u;
 #pragma unroll
-                    for (int q = 0; q < NS; ++q) rw[q] = rows[R * NS + q];
-                    have_rows = true;
+                for (int q = 0; q < NS; ++q) rw[q] = rows[R * NS + q];
 #pragma unroll
-                    for (int q = NS - 1; q >= 0; --q)
-                        if (rw[q]) sf = 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1);
-                }
+                for (int q = NS - 1; q >= 0; --q)
+                    if (rw[q]) sf = 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1);
             } else {
-                bfkey = bf_scan(wj, L);
-                hit = bfkey != kNoKey;
-                sf = (bfkey & 0x7FFFu) >> 7;
-                R = (bfkey >> 15) + wj;
+                const uint32_t key = bf_scan(wj, L);
+                hit = key != kNoKey;
+                sf = hit ? (key & 0x7FFFu) >> 7 : 0u;
+                R = (key >> 15) + wj;
             }
-            if (kSeg && hit && c == kBF) {
+            if (kSeg && c == kBF) {
                 // RANDOM: a BF item still keeps the segment maxima exact
                 uint32_t v = 0;
 #pragma unroll
@@ -220,75 +221,44 @@ struct H1Warp {
                 Mseg = __shfl_sync(kFull, v, static_cast<int>(sf & 31));
             }
 
-            // 2. the chosen bin: index b, old residual, capacity; the segment's
-            //    count of bins at Mseg (cM) and largest other residual (M2)
-            uint32_t b, r_old, Bt, cM = 0, M2 = 0, cnt_old = 0;
-            if (hit) {
-                const uint4 Q = reinterpret_cast<const uint4*>(slots)[32u * sf + ulane];
-                const uint32_t r0 = Q.x >> 16, r1 = Q.y >> 16, r2 = Q.z >> 16, r3 = Q.w >> 16;
-                const uint32_t c0 = Q.x & 0xFFFFu, c1 = Q.y & 0xFFFFu, c2 = Q.z & 0xFFFFu, c3 = Q.w & 0xFFFFu;
-                const uint32_t i0 = 4u * ulane;
-                if (kSeg) {
-                    cM = (r0 == Mseg) + (r1 == Mseg) + (r2 == Mseg) + (r3 == Mseg);
-                    M2 = max(max(r0 != Mseg ? r0 : 0u, r1 != Mseg ? r1 : 0u),
-                             max(r2 != Mseg ? r2 : 0u, r3 != Mseg ? r3 : 0u));
-                }
-                if (c == kFF) {
-                    uint32_t k1 = kNoKey, k2 = kNoKey;
-                    if (r3 >= wj) { k1 = ((i0 + 3u) << 16) | r3; k2 = ((i0 + 3u) << 16) | c3; }
-                    if (r2 >= wj) { k1 = ((i0 + 2u) << 16) | r2; k2 = ((i0 + 2u) << 16) | c2; }
-                    if (r1 >= wj) { k1 = ((i0 + 1u) << 16) | r1; k2 = ((i0 + 1u) << 16) | c1; }
-                    if (r0 >= wj) { k1 = (i0 << 16) | r0; k2 = (i0 << 16) | c0; }
-                    k1 = __reduce_min_sync(kFull, k1);
-                    k2 = __reduce_min_sync(kFull, k2);
-                    cM = __reduce_add_sync(kFull, cM);
-                    M2 = __reduce_max_sync(kFull, M2);
-                    b = 128u * sf + (k1 >> 16);
-                    r_old = k1 & 0xFFFFu;
-                    Bt = k2 & 0xFFFFu;
-                    if (kBFItems && use_idx) {
-                        const uint32_t e = (r0 == r_old) + (r1 == r_old) + (r2 == r_old) + (r3 == r_old);
-                        cnt_old = __reduce_add_sync(kFull, e);
-                    }
-                } else if (bfkey != kNoKey) {
-                    // full-scan BF: the bin is known; its capacity from the slot
-                    b = bfkey & 0x7FFFu;
-                    r_old = R;
-                    Bt = slots[b] & 0xFFFFu;
-                    if (kSeg) {
-                        cM = __reduce_add_sync(kFull, cM);
-                        M2 = __reduce_max_sync(kFull, M2);
-                    }
-                } else {
-                    // WF (R = the largest residual) or indexed BF (R = least >= w)
-                    uint32_t k1 = kNoKey;
-                    if (r3 == R) k1 = ((i0 + 3u) << 16) | c3;
-                    if (r2 == R) k1 = ((i0 + 2u) << 16) | c2;
-                    if (r1 == R) k1 = ((i0 + 1u) << 16) | c1;
-                    if (r0 == R) k1 = (i0 << 16) | c0;
-                    const uint32_t e = (r0 == R) + (r1 == R) + (r2 == R) + (r3 == R);
-                    k1 = __reduce_min_sync(kFull, k1);
-                    cnt_old = __reduce_add_sync(kFull, e);
-                    if (kSeg) {
-                        cM = __reduce_add_sync(kFull, cM);
-                        M2 = __reduce_max_sync(kFull, M2);
-                    }
-                    b = 128u * sf + (k1 >> 16);
-                    r_old = R;
-                    Bt = k1 & 0xFFFFu;
-                }
-            } else {                                   // nothing fits: a new bin of the smallest type
-                b = L;
-                r_old = Bn;
-                Bt = Bn;
+            // 2. in segment sf: the chosen bin (FF: first fitting; BF / WF:
+            //    first at residual R) as (index, residual) and (index,
+            //    capacity) keys; cR = bins at R, cM = bins at Mseg, M2 = the
+            //    largest residual other than Mseg
+            const uint4 Q = reinterpret_cast<const uint4*>(slots)[32u * sf + ulane];
+            const uint32_t r0 = Q.x >> 16, r1 = Q.y >> 16, r2 = Q.z >> 16, r3 = Q.w >> 16;
+            const uint32_t c0 = Q.x & 0xFFFFu, c1 = Q.y & 0xFFFFu, c2 = Q.z & 0xFFFFu, c3 = Q.w & 0xFFFFu;
+            const uint32_t i0 = (4u * ulane) << 16;
+            uint32_t k1 = kNoKey, k2 = kNoKey, cR = 0, cM = 0, M2 = 0;
+            if (c == kFF) {
+                if (r3 >= wj) { k1 = (i0 + (3u << 16)) | r3; k2 = (i0 + (3u << 16)) | c3; }
+                if (r2 >= wj) { k1 = (i0 + (2u << 16)) | r2; k2 = (i0 + (2u << 16)) | c2; }
+                if (r1 >= wj) { k1 = (i0 + (1u << 16)) | r1; k2 = (i0 + (1u << 16)) | c1; }
+                if (r0 >= wj) { k1 = i0 | r0; k2 = i0 | c0; }
+                k2 = __reduce_min_sync(kFull, k2);
+            } else {
+                if (r3 == R) k1 = (i0 + (3u << 16)) | c3;
+                if (r2 == R) k1 = (i0 + (2u << 16)) | c2;
+                if (r1 == R) k1 = (i0 + (1u << 16)) | c1;
+                if (r0 == R) k1 = i0 | c0;
+                if (IDX) cR = __reduce_add_sync(kFull, (r0 == R) + (r1 == R) + (r2 == R) + (r3 == R));
             }
+            k1 = __reduce_min_sync(kFull, k1);
+            if (kSeg) {
+                cM = __reduce_add_sync(kFull, (r0 == Mseg) + (r1 == Mseg) + (r2 == Mseg) + (r3 == Mseg));
+                M2 = __reduce_max_sync(kFull, max(max(r0 != Mseg ? r0 : 0u, r1 != Mseg ? r1 : 0u),
+                                                  max(r2 != Mseg ? r2 : 0u, r3 != Mseg ? r3 : 0u)));
+            }
+            const uint32_t b = hit ? 128u * sf + (k1 >> 16) : L;
+            const uint32_t r_old = hit ? (c == kFF ? (k1 & 0xFFFFu) : R) : Bn;
+            const uint32_t Bt = hit ? ((c == kFF ? k2 : k1) & 0xFFFFu) : Bn;
             const uint32_t r_new = r_old - wj;
             const bool fire = (Bt < 2u * r_old) && (2u * r_new <= Bt);     // Rule 5
             const uint32_t Lf = hit ? L : L + 1u;      // where a divided-off bin goes
-            if (lane == 0) {
-                slots[b] = (r_new << 16) | Bt;
-                if (fire) slots[Lf] = (Bt << 16) | Bt;
-            }
+            // every lane writes the same words; a bin that does not divide
+            // writes the pad word past the slots
+            slots[b] = (r_new << 16) | Bt;
+            slots[fire ? Lf : cap_bins] = (Bt << 16) | Bt;
             const uint32_t sb = b >> 7, sfire = Lf >> 7;
 
             // 3. segment maxima
@@ -298,41 +268,49 @@ struct H1Warp {
                 for (int q = 0; q < NS; ++q) {
                     const uint32_t s = 32u * q + ulane;
                     uint32_t v = sm[q];
-                    if (s == sb) v = hit ? top : max(v, r_new);
-                    if (fire && s == sfire) v = max(v, Bt);
+                    v = s == sb ? (hit ? top : max(v, r_new)) : v;
+                    v = (fire && s == sfire) ? max(v, Bt) : v;
                     sm[q] = v;
                 }
             }
-            // 4. the BF index
-            if (kBFItems && use_idx) {
-                if (hit && cnt_old == 1u) {
-                    // r_old leaves segment sb
-                    if (!have_rows) {
+            // 4. the BF index: r_old leaves segment sb when the chosen bin was
+            //    its only bin at r_old; r_new and a divided-off bin's
+            //    capacity enter
+            if (IDX) {
+                if (hit) {
+                    if (c == kFF) {
+                        cR = __reduce_add_sync(kFull, (r0 == r_old) + (r1 == r_old) + (r2 == r_old) + (r3 == r_old));
+#pragma unroll
+                        for (int q = 0; q < NS; ++q) rw[q] = rows[r_old * NS + q];
+                    } else if (c == kWF) {
+                        cR = cM;
 #pragma unroll
                         for (int q = 0; q < NS; ++q) rw[q] = rows[r_old * NS + q];
                     }
-                    uint32_t any = 0, word = 0;
+                    if (cR == 1u) {
+                        uint32_t any = 0, word = 0;
 #pragma unroll
-                    for (int q = 0; q < NS; ++q) {
-                        if ((sb >> 5) == static_cast<uint32_t>(q)) { rw[q] &= ~(1u << (sb & 31)); word = rw[q]; }
-                        any |= rw[q];
+                        for (int q = 0; q < NS; ++q) {
+                            if ((sb >> 5) == static_cast<uint32_t>(q)) { rw[q] &= ~(1u << (sb & 31)); word = rw[q]; }
+                            any |= rw[q];
+                        }
+                        rows[r_old * NS + (sb >> 5)] = word;
+                        if (!any && (r_old >> 5) == ulane) wb &= ~(1u << (r_old & 31));
                     }
-                    if (lane == 0) rows[r_old * NS + (sb >> 5)] = word;
-                    if (!any && (r_old >> 5) == ulane) wb &= ~(1u << (r_old & 31));
                 }
                 if (r_new > 0u) {
-                    if (lane == 0) atomicOr(&rows[r_new * NS + (sb >> 5)], 1u << (sb & 31));
+                    atomicOr(&rows[r_new * NS + (sb >> 5)], 1u << (sb & 31));
                     if ((r_new >> 5) == ulane) wb |= 1u << (r_new & 31);
                 }
                 if (fire) {
-                    if (lane == 0) atomicOr(&rows[Bt * NS + (sfire >> 5)], 1u << (sfire & 31));
+                    atomicOr(&rows[Bt * NS + (sfire >> 5)], 1u << (sfire & 31));
                     if ((Bt >> 5) == ulane) wb |= 1u << (Bt & 31);
                 }
             }
             L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
-            if (lane == jj) bout = b;
-            if (jj == 31 || j + 1 == k) {
-                if (lane <= jj) raw[j - jj + lane] = static_cast<int32_t>(bout);
+            bout = ulane == jj ? b : bout;
+            if (jj == 31u || j + 1u == k) {
+                if (ulane <= jj) raw[j - jj + ulane] = static_cast<int32_t>(bout);
             }
             d = dn;
             __syncwarp();
@@ -354,7 +332,7 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
     H1Warp<NS, CRIT> g;
     g.lane = lane;
     g.slots = reinterpret_cast<uint32_t*>(base);
-    base += 4 * p.slot_cap;
+    base += 4 * p.slot_cap + 16;
     g.rows = nullptr;
     if (p.bf_index) {
         g.rows = reinterpret_cast<uint32_t*>(base);
@@ -417,7 +395,13 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
             __syncwarp();
         }
         unsigned long long fit_tests = 0;
-        const bool done = g.run(p, i, w, 0, k, raw, n, use_idx, L, fit_tests);
+        bool done;
+        if constexpr (H1Warp<NS, CRIT>::kBFItems) {
+            done = use_idx ? g.template run<true>(p, i, w, 0, static_cast<uint32_t>(k), raw, n, L, fit_tests)
+                           : g.template run<false>(p, i, w, 0, static_cast<uint32_t>(k), raw, n, L, fit_tests);
+        } else {
+            done = g.template run<false>(p, i, w, 0, static_cast<uint32_t>(k), raw, n, L, fit_tests);
+        }
         if (!done) continue;                 // spilled: a full-size launch repacks it
 
         // --- objective (Section 1) and dense ids: used bins in creation order ---
