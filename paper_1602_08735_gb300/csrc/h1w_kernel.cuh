@@ -138,23 +138,16 @@ struct H1Warp {
             }
         }
 
-        // weights a 32-item block ahead: lane l holds item (block + l)
-        uint32_t dcur = descriptor(weight(w, ulane, k), ulane, n, p.seed, key0);
+        // Items go in blocks of 32: lane l holds the descriptor of item
+        // (block + l), and the weights of the next block are loaded a block
+        // ahead.
+        uint32_t dnext = descriptor(weight(w, ulane, k), ulane, n, p.seed, key0);
         uint32_t wpre = weight(w, 32 + ulane, k);
-        uint32_t d = __shfl_sync(kFull, dcur, 0);
-        uint32_t bout = 0;
-        for (uint32_t j = 0; j < k; ++j) {
-            const uint32_t jj = j & 31u;
-            // the next item's descriptor (independent of the packing state)
-            uint32_t dn;
-            if (jj == 31u) {
-                dcur = descriptor(wpre, static_cast<int64_t>(j) + 1 + ulane, n, p.seed, key0);
-                wpre = weight(w, static_cast<int64_t>(j) + 33 + ulane, k);
-                dn = __shfl_sync(kFull, dcur, 0);
-            } else {
-                dn = __shfl_sync(kFull, dcur, static_cast<int>(jj + 1u));
-            }
-            if (p.spill_list && L + 2u > cap_bins) {
+        for (uint32_t j0 = 0; j0 < k; j0 += 32u) {
+            const uint32_t cnt = min(32u, k - j0);
+            // an item adds at most two bins: stop before the block could
+            // outgrow the slots (a worst-case-sized launch repacks the system)
+            if (p.spill_list && L + 2u * cnt > cap_bins) {
                 if (lane == 0) {
                     const unsigned long long pos = atomicAdd(
                         reinterpret_cast<unsigned long long*>(p.spill_seg + 1), 1ull);
@@ -163,6 +156,14 @@ struct H1Warp {
                 __syncwarp();
                 return false;
             }
+            const uint32_t dblk = dnext;
+            dnext = descriptor(wpre, static_cast<int64_t>(j0) + 32 + ulane, n, p.seed, key0);
+            wpre = weight(w, static_cast<int64_t>(j0) + 64 + ulane, k);
+            uint32_t d = __shfl_sync(kFull, dblk, 0);
+            uint32_t bout = 0;
+        for (uint32_t jj = 0; jj < cnt; ++jj) {
+            // the next item's descriptor (independent of the packing state)
+            const uint32_t dn = __shfl_sync(kFull, dblk, static_cast<int>((jj + 1u) & 31u));
             const uint32_t wj = d & 0x7FFFu;
             const uint32_t Bn = (d >> 16) & 0x7FFFu;
             const int c = CRIT == kRandom ? static_cast<int>(((d >> 15) & 1u) | ((d >> 30) & 2u)) : CRIT;
@@ -172,9 +173,9 @@ struct H1Warp {
             //    residual; R = the residual sought (BF, WF)
             bool hit;
             uint32_t sf = 0, Mseg = 0, R = 0;
-            uint32_t rw[NS];
+            uint32_t rw[NS], rn[NS];          // index rows of r_old and of r_new
 #pragma unroll
-            for (int q = 0; q < NS; ++q) rw[q] = 0;
+            for (int q = 0; q < NS; ++q) rw[q] = rn[q] = 0;
             if (kSeg && c == kFF) {
                 uint32_t key = kNoKey;
 #pragma unroll
@@ -202,8 +203,13 @@ struct H1Warp {
                 key = __reduce_min_sync(kFull, key);
                 hit = key != kNoKey;
                 R = hit ? key : 0u;
+                // the row the chosen bin leaves and the row it enters, read together
+                const uint32_t Rn = (hit ? R : Bn) - wj;
 #pragma unroll
-                for (int q = 0; q < NS; ++q) rw[q] = rows[R * NS + q];
+                for (int q = 0; q < NS; ++q) {
+                    rw[q] = rows[R * NS + q];
+                    rn[q] = rows[Rn * NS + q];
+                }
 #pragma unroll
                 for (int q = NS - 1; q >= 0; --q)
                     if (rw[q]) sf = 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1);
@@ -230,6 +236,11 @@ struct H1Warp {
             const uint32_t c0 = Q.x & 0xFFFFu, c1 = Q.y & 0xFFFFu, c2 = Q.z & 0xFFFFu, c3 = Q.w & 0xFFFFu;
             const uint32_t i0 = (4u * ulane) << 16;
             uint32_t k1 = kNoKey, k2 = kNoKey, cR = 0, cM = 0, M2 = 0;
+            if (kSeg) {                     // these need only the quad: issued first
+                cM = __reduce_add_sync(kFull, (r0 == Mseg) + (r1 == Mseg) + (r2 == Mseg) + (r3 == Mseg));
+                M2 = __reduce_max_sync(kFull, max(max(r0 != Mseg ? r0 : 0u, r1 != Mseg ? r1 : 0u),
+                                                  max(r2 != Mseg ? r2 : 0u, r3 != Mseg ? r3 : 0u)));
+            }
             if (c == kFF) {
                 if (r3 >= wj) { k1 = (i0 + (3u << 16)) | r3; k2 = (i0 + (3u << 16)) | c3; }
                 if (r2 >= wj) { k1 = (i0 + (2u << 16)) | r2; k2 = (i0 + (2u << 16)) | c2; }
@@ -244,11 +255,6 @@ struct H1Warp {
                 if (IDX) cR = __reduce_add_sync(kFull, (r0 == R) + (r1 == R) + (r2 == R) + (r3 == R));
             }
             k1 = __reduce_min_sync(kFull, k1);
-            if (kSeg) {
-                cM = __reduce_add_sync(kFull, (r0 == Mseg) + (r1 == Mseg) + (r2 == Mseg) + (r3 == Mseg));
-                M2 = __reduce_max_sync(kFull, max(max(r0 != Mseg ? r0 : 0u, r1 != Mseg ? r1 : 0u),
-                                                  max(r2 != Mseg ? r2 : 0u, r3 != Mseg ? r3 : 0u)));
-            }
             const uint32_t b = hit ? 128u * sf + (k1 >> 16) : L;
             const uint32_t r_old = hit ? (c == kFF ? (k1 & 0xFFFFu) : R) : Bn;
             const uint32_t Bt = hit ? ((c == kFF ? k2 : k1) & 0xFFFFu) : Bn;
@@ -277,43 +283,49 @@ struct H1Warp {
             //    its only bin at r_old; r_new and a divided-off bin's
             //    capacity enter
             if (IDX) {
-                if (hit) {
-                    if (c == kFF) {
+                if (c != kBF) {
+                    // (RANDOM) an FF or WF item: the rows are read now
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) {
+                        rw[q] = rows[r_old * NS + q];
+                        rn[q] = rows[r_new * NS + q];
+                    }
+                    if (c == kFF)
                         cR = __reduce_add_sync(kFull, (r0 == r_old) + (r1 == r_old) + (r2 == r_old) + (r3 == r_old));
-#pragma unroll
-                        for (int q = 0; q < NS; ++q) rw[q] = rows[r_old * NS + q];
-                    } else if (c == kWF) {
+                    else
                         cR = cM;
+                }
+                if (hit && cR == 1u) {
+                    uint32_t any = 0, word = 0;
 #pragma unroll
-                        for (int q = 0; q < NS; ++q) rw[q] = rows[r_old * NS + q];
+                    for (int q = 0; q < NS; ++q) {
+                        if ((sb >> 5) == static_cast<uint32_t>(q)) { rw[q] &= ~(1u << (sb & 31)); word = rw[q]; }
+                        any |= rw[q];
                     }
-                    if (cR == 1u) {
-                        uint32_t any = 0, word = 0;
-#pragma unroll
-                        for (int q = 0; q < NS; ++q) {
-                            if ((sb >> 5) == static_cast<uint32_t>(q)) { rw[q] &= ~(1u << (sb & 31)); word = rw[q]; }
-                            any |= rw[q];
-                        }
-                        rows[r_old * NS + (sb >> 5)] = word;
-                        if (!any && (r_old >> 5) == ulane) wb &= ~(1u << (r_old & 31));
-                    }
+                    rows[r_old * NS + (sb >> 5)] = word;
+                    if (!any && (r_old >> 5) == ulane) wb &= ~(1u << (r_old & 31));
                 }
                 if (r_new > 0u) {
-                    atomicOr(&rows[r_new * NS + (sb >> 5)], 1u << (sb & 31));
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) word = (sb >> 5) == static_cast<uint32_t>(q) ? rn[q] : word;
+                    rows[r_new * NS + (sb >> 5)] = word | (1u << (sb & 31));
                     if ((r_new >> 5) == ulane) wb |= 1u << (r_new & 31);
                 }
                 if (fire) {
-                    atomicOr(&rows[Bt * NS + (sfire >> 5)], 1u << (sfire & 31));
+                    // read after the stores above (same warp, program order)
+                    uint32_t* at = &rows[Bt * NS + (sfire >> 5)];
+                    const uint32_t word = *at;
+                    *at = word | (1u << (sfire & 31));
                     if ((Bt >> 5) == ulane) wb |= 1u << (Bt & 31);
                 }
             }
             L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
             bout = ulane == jj ? b : bout;
-            if (jj == 31u || j + 1u == k) {
-                if (ulane <= jj) raw[j - jj + ulane] = static_cast<int32_t>(bout);
-            }
             d = dn;
             __syncwarp();
+        }
+            if (ulane < cnt) raw[j0 + ulane] = static_cast<int32_t>(bout);
         }
         L_io = L;
         return true;
