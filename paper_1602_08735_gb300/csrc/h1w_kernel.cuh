@@ -180,7 +180,7 @@ struct H1Warp {
                 uint32_t key = kNoKey;
 #pragma unroll
                 for (int q = NS - 1; q >= 0; --q)
-                    if (sm[q] >= wj) key = ((32u * q + ulane) << 16) | sm[q];
+                    key = sm[q] >= wj ? ((32u * q + ulane) << 16) | sm[q] : key;
                 key = __reduce_min_sync(kFull, key);
                 hit = key != kNoKey;
                 sf = hit ? key >> 16 : 0u;
@@ -195,10 +195,9 @@ struct H1Warp {
                 hit = Mseg >= wj;
                 R = Mseg;
             } else if (IDX) {
-                uint32_t x = wb;
+                // residuals >= w present in this lane's word (selects, no branches)
                 const uint32_t wi = wj >> 5;
-                if (ulane < wi) x = 0;
-                else if (ulane == wi) x &= ~((1u << (wj & 31)) - 1u);
+                const uint32_t x = wb & (ulane < wi ? 0u : ulane == wi ? ~((1u << (wj & 31)) - 1u) : 0xFFFFFFFFu);
                 uint32_t key = x ? 32u * ulane + static_cast<uint32_t>(__ffs(x) - 1) : kNoKey;
                 key = __reduce_min_sync(kFull, key);
                 hit = key != kNoKey;
@@ -212,7 +211,7 @@ struct H1Warp {
                 }
 #pragma unroll
                 for (int q = NS - 1; q >= 0; --q)
-                    if (rw[q]) sf = 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1);
+                    sf = rw[q] ? 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1) : sf;
             } else {
                 const uint32_t key = bf_scan(wj, L);
                 hit = key != kNoKey;
@@ -242,16 +241,15 @@ struct H1Warp {
                                                   max(r2 != Mseg ? r2 : 0u, r3 != Mseg ? r3 : 0u)));
             }
             if (c == kFF) {
-                if (r3 >= wj) { k1 = (i0 + (3u << 16)) | r3; k2 = (i0 + (3u << 16)) | c3; }
-                if (r2 >= wj) { k1 = (i0 + (2u << 16)) | r2; k2 = (i0 + (2u << 16)) | c2; }
-                if (r1 >= wj) { k1 = (i0 + (1u << 16)) | r1; k2 = (i0 + (1u << 16)) | c1; }
-                if (r0 >= wj) { k1 = i0 | r0; k2 = i0 | c0; }
+                // keys grow with the index: the first fitting bin is the minimum
+                k1 = min(min(r0 >= wj ? i0 | r0 : kNoKey, r1 >= wj ? (i0 + (1u << 16)) | r1 : kNoKey),
+                         min(r2 >= wj ? (i0 + (2u << 16)) | r2 : kNoKey, r3 >= wj ? (i0 + (3u << 16)) | r3 : kNoKey));
+                k2 = min(min(r0 >= wj ? i0 | c0 : kNoKey, r1 >= wj ? (i0 + (1u << 16)) | c1 : kNoKey),
+                         min(r2 >= wj ? (i0 + (2u << 16)) | c2 : kNoKey, r3 >= wj ? (i0 + (3u << 16)) | c3 : kNoKey));
                 k2 = __reduce_min_sync(kFull, k2);
             } else {
-                if (r3 == R) k1 = (i0 + (3u << 16)) | c3;
-                if (r2 == R) k1 = (i0 + (2u << 16)) | c2;
-                if (r1 == R) k1 = (i0 + (1u << 16)) | c1;
-                if (r0 == R) k1 = i0 | c0;
+                k1 = min(min(r0 == R ? i0 | c0 : kNoKey, r1 == R ? (i0 + (1u << 16)) | c1 : kNoKey),
+                         min(r2 == R ? (i0 + (2u << 16)) | c2 : kNoKey, r3 == R ? (i0 + (3u << 16)) | c3 : kNoKey));
                 if (IDX) cR = __reduce_add_sync(kFull, (r0 == R) + (r1 == R) + (r2 == R) + (r3 == R));
             }
             k1 = __reduce_min_sync(kFull, k1);
@@ -299,25 +297,27 @@ struct H1Warp {
                     uint32_t any = 0, word = 0;
 #pragma unroll
                     for (int q = 0; q < NS; ++q) {
-                        if ((sb >> 5) == static_cast<uint32_t>(q)) { rw[q] &= ~(1u << (sb & 31)); word = rw[q]; }
+                        const bool here = (sb >> 5) == static_cast<uint32_t>(q);
+                        rw[q] = here ? rw[q] & ~(1u << (sb & 31)) : rw[q];
+                        word = here ? rw[q] : word;
                         any |= rw[q];
                     }
                     rows[r_old * NS + (sb >> 5)] = word;
-                    if (!any && (r_old >> 5) == ulane) wb &= ~(1u << (r_old & 31));
+                    wb = (!any && (r_old >> 5) == ulane) ? wb & ~(1u << (r_old & 31)) : wb;
                 }
                 if (r_new > 0u) {
                     uint32_t word = 0;
 #pragma unroll
                     for (int q = 0; q < NS; ++q) word = (sb >> 5) == static_cast<uint32_t>(q) ? rn[q] : word;
                     rows[r_new * NS + (sb >> 5)] = word | (1u << (sb & 31));
-                    if ((r_new >> 5) == ulane) wb |= 1u << (r_new & 31);
+                    wb = (r_new >> 5) == ulane ? wb | (1u << (r_new & 31)) : wb;
                 }
                 if (fire) {
                     // read after the stores above (same warp, program order)
                     uint32_t* at = &rows[Bt * NS + (sfire >> 5)];
                     const uint32_t word = *at;
                     *at = word | (1u << (sfire & 31));
-                    if ((Bt >> 5) == ulane) wb |= 1u << (Bt & 31);
+                    wb = (Bt >> 5) == ulane ? wb | (1u << (Bt & 31)) : wb;
                 }
             }
             L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
