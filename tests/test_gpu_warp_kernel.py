@@ -93,7 +93,7 @@ def test_spill_rerun_one_warp(pct):
             assert_same(b, run_batch(b, 1, c, seed=4, plain=True), run_oracle(b, 1, c, seed=4),
                         f"spill plain {pct} c{c}")
     finally:
-        native.set_config(large_warps=1, small_m=0)
+        native.set_config(**saved)
 
 
 @pytest.mark.parametrize("wpb", [2, 16])
@@ -106,4 +106,4 @@ def test_many_warps_per_block(wpb):
         for c in CRITS:
             assert_same(b, run_batch(b, 1, c, seed=6), run_oracle(b, 1, c, seed=6), f"wpb {wpb} c{c}")
     finally:
-        native.set_config(large_warps=1, small_m=0)
+        native.set_config(**saved)
