@@ -272,7 +272,9 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         lp.mode = {VSBPP_H2, 1, s};
         int f = 1;
         for (int x = 2; x <= s; ++x) f *= x;
-        lp.h2_threads = std::max(32, (f + 31) / 32 * 32);
+        // literal Rule 2 start: one thread per permutation (shared-memory
+        // bins); otherwise four warps per block, one sublist per warp
+        lp.h2_threads = prm.preopen ? std::max(32, (f + 31) / 32 * 32) : 128;
         lp.h2_max_bins = 2 * s + (prm.preopen ? kMaxTypes : 0);
         lp.h2_smem = h2_smem_bytes(lp.h2_threads, lp.h2_max_bins);
         const int occ = prm.preopen ? h2_blocks_per_sm(lp.h2_threads, lp.h2_smem)

@@ -191,161 +191,324 @@ __device__ __forceinline__ void h2_decode(int rank, int k, int (&perm)[S]) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register kernel (no pre-opened bins): one warp per sublist.
+//
+// Lane l of the warp packs the permutations of rank l, l+32, ... (rounds of
+// 32), keeping the best (least total, then least rank) it has seen; one warp
+// minimum names the winner, whose lane writes the sublist's result.  No block
+// barrier is taken per sublist.  A lane's bins are fixed slots: the bin
+// opened at item step q (nothing fits) is slot 2q and the bin divided off at
+// step q (Rule 5) is slot 2q+1, so slot order is creation order and a new
+// bin's slot is known at compile time; a slot never created reads as an
+// empty word that never fits and is never used.
+//
+// Capacities <= 4095 (narrow): one word per slot, v = (residual << 16) |
+// (slot << 12) | capacity, so each selection is one operation pair per slot
+//   FF  the lowest fitting slot (v >= w << 16),
+//   BF  min(v - (w << 16)): a slot that does not fit wraps above 2^31,
+//   WF  min(v ^ 0xFFFF0000): the largest residual, then the lowest slot,
+// and the chosen word carries the bin's residual, slot and capacity.
+// Larger capacities (wide): residual and capacity words per slot, 64-bit
+// selection keys.
+// Permutations are packed 3 bits per position, one table per sublist
+// length k <= S in shared memory (lexicographic rank order).
+
+__host__ __device__ constexpr int h2_fact_c(int v) { return v <= 1 ? 1 : v * h2_fact_c(v - 1); }
+__host__ __device__ constexpr int h2_table_size(int S) { return S < 0 ? 0 : h2_fact_c(S) + h2_table_size(S - 1); }
+__device__ __forceinline__ int h2_table_off(int k) {      // entries of lengths 0 .. k-1
+    return k <= 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 4 : k == 4 ? 10 : k == 5 ? 34 : 154;
+}
+
+// Minimum of t[0..cnt) (cnt a compile-time constant after unrolling) as a
+// balanced tree; all-ones when cnt = 0.
+template <int N>
+__device__ __forceinline__ uint32_t h2_min_tree(uint32_t (&t)[N], int cnt) {
+#pragma unroll
+    for (int x = 0; x < N; ++x) if (x >= cnt) t[x] = 0xFFFFFFFFu;
+#pragma unroll
+    for (int step = 1; step < N; step *= 2) {
+#pragma unroll
+        for (int x = 0; x + step < N; x += 2 * step) t[x] = min(t[x], t[x + step]);
+    }
+    return t[0];
+}
+
+// Pack one permutation, narrow slot words.  Returns the used capacity (a
+// bin's capacity counts from the item that finds it empty); rawp gets the
+// slot of the item at step q in bits 4q..4q+3.  K > 0: exactly K items
+// (compile time); K = 0: k items.
+template <int S, int CRIT, int K>
+__device__ __forceinline__ uint32_t h2_pack_narrow(uint32_t perm, int k, const uint32_t* wsub,
+                                                   const uint32_t* bnew, uint64_t seed, int64_t g, int rank,
+                                                   uint32_t (&v)[2 * S], uint32_t& rawp) {
+    constexpr int kSlots = 2 * S;
+    constexpr uint32_t kNo = 0xFFFFFFFFu;
+#pragma unroll
+    for (int x = 0; x < kSlots; ++x) v[x] = 0u;
+    rawp = 0;
+    uint32_t tot = 0;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        if (K > 0 ? q < K : q < k) {
+            const uint32_t it = (perm >> (3 * q)) & 7u;
+            const uint32_t wq = wsub[it], bn = bnew[it];
+            const uint32_t W = wq << 16;
+            const int c = CRIT == kRandom
+                              ? pick_criterion(kRandom, seed, static_cast<uint64_t>((g * 720 + rank) * 8 + q))
+                              : CRIT;
+            uint32_t best;
+            bool hit;
+            if (c == kFF) {
+                best = kNo;
+#pragma unroll
+                for (int x = 2 * q - 1; x >= 0; --x) best = v[x] >= W ? v[x] : best;
+                hit = best != kNo;
+            } else if (c == kBF) {
+                uint32_t t[kSlots];
+#pragma unroll
+                for (int x = 0; x < 2 * q; ++x) t[x] = v[x] - W;
+                const uint32_t m = h2_min_tree<kSlots>(t, 2 * q);
+                hit = m < 0x80000000u;
+                best = m + W;
+            } else {
+                uint32_t t[kSlots];
+#pragma unroll
+                for (int x = 0; x < 2 * q; ++x) t[x] = v[x] ^ 0xFFFF0000u;
+                best = h2_min_tree<kSlots>(t, 2 * q) ^ 0xFFFF0000u;
+                hit = (best >> 16) >= wq;
+            }
+            const uint32_t xs = hit ? (best >> 12) & 15u : static_cast<uint32_t>(2 * q);
+            const uint32_t r_old = hit ? best >> 16 : bn;
+            const uint32_t cap = hit ? best & 0xFFFu : bn;
+            const uint32_t r_new = r_old - wq;
+            const bool fire = (cap < 2u * r_old) && (2u * r_new <= cap);     // Rule 5
+            tot += r_old == cap ? cap : 0u;        // the bin's first item: it becomes used
+#pragma unroll
+            for (int x = 0; x < 2 * q; ++x) v[x] = xs == static_cast<uint32_t>(x) ? v[x] - W : v[x];
+            v[2 * q] = hit ? 0u : (r_new << 16) | (static_cast<uint32_t>(2 * q) << 12) | cap;
+            v[2 * q + 1] = fire ? (cap << 16) | (static_cast<uint32_t>(2 * q + 1) << 12) | cap : 0u;
+            rawp |= xs << (4 * q);
+        }
+    }
+    return tot;
+}
+
+// Pack one permutation, wide slots (residual r[x], capacity c[x]).
 template <int S, int CRIT>
-__global__ void __launch_bounds__(768) h2_pack_kernel_reg(const H2Params p) {
-    constexpr int kBins = 2 * S;
-    __shared__ unsigned long long wbest[32];
+__device__ __forceinline__ uint64_t h2_pack_wide(uint32_t perm, int k, const uint32_t* wsub, const uint32_t* bnew,
+                                                 uint64_t seed, int64_t g, int rank, uint32_t (&r)[2 * S],
+                                                 uint32_t (&cp)[2 * S], uint32_t& rawp) {
+    constexpr int kSlots = 2 * S;
+    constexpr uint64_t kNo = ~0ull;
+#pragma unroll
+    for (int x = 0; x < kSlots; ++x) { r[x] = 0u; cp[x] = 0u; }
+    rawp = 0;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        if (q < k) {
+            const uint32_t it = (perm >> (3 * q)) & 7u;
+            const uint32_t wq = wsub[it], bn = bnew[it];
+            const int c = CRIT == kRandom
+                              ? pick_criterion(kRandom, seed, static_cast<uint64_t>((g * 720 + rank) * 8 + q))
+                              : CRIT;
+            uint64_t key = kNo;                // (measure << 4) | slot, least wins
+#pragma unroll
+            for (int x = 0; x < 2 * q; ++x) {
+                const bool fit = r[x] >= wq;
+                const uint64_t m = c == kFF ? 0ull : c == kBF ? static_cast<uint64_t>(r[x] - wq)
+                                                              : static_cast<uint64_t>(~r[x]);
+                const uint64_t kx = (m << 4) | static_cast<uint64_t>(x);
+                key = fit && kx < key ? kx : key;
+            }
+            const bool hit = key != kNo;
+            const uint32_t xs = hit ? static_cast<uint32_t>(key & 15ull) : static_cast<uint32_t>(2 * q);
+            uint32_t r_old = bn, cap = bn;
+#pragma unroll
+            for (int x = 0; x < 2 * q; ++x) {
+                r_old = xs == static_cast<uint32_t>(x) ? r[x] : r_old;
+                cap = xs == static_cast<uint32_t>(x) ? cp[x] : cap;
+            }
+            const uint32_t r_new = r_old - wq;
+            const bool fire = (static_cast<uint64_t>(cap) < 2ull * r_old) &&
+                              (2ull * r_new <= static_cast<uint64_t>(cap));     // Rule 5
+#pragma unroll
+            for (int x = 0; x < 2 * q; ++x) r[x] = xs == static_cast<uint32_t>(x) ? r_new : r[x];
+            r[2 * q] = hit ? 0u : r_new;
+            cp[2 * q] = hit ? 0u : cap;
+            r[2 * q + 1] = fire ? cap : 0u;
+            cp[2 * q + 1] = fire ? cap : 0u;
+            rawp |= xs << (4 * q);
+        }
+    }
+    uint64_t tot = 0;
+#pragma unroll
+    for (int x = 0; x < kSlots; ++x) tot += r[x] < cp[x] ? cp[x] : 0u;
+    return tot;
+}
+
+// The winner's result in sublist-local form: used slots (load > 0) get
+// dense ids in slot order (= creation order).
+template <int S>
+__device__ __forceinline__ void h2_write_winner(const H2Params& p, const uint32_t (&cap)[2 * S],
+                                                uint32_t used, uint32_t rawp, uint32_t perm, int k,
+                                                const uint32_t* Bs, int n, int64_t uid, int64_t base,
+                                                uint64_t total) {
+    int cnt = 0;
+#pragma unroll
+    for (int x = 0; x < 2 * S; ++x) {
+        if ((used >> x) & 1u) {
+            int t = 0;
+            for (int y = 0; y < n; ++y) t = Bs[y] == cap[x] ? y : t;
+            p.out.local_types[base + cnt] = t;
+            ++cnt;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        if (q < k) {
+            const uint32_t slot = (rawp >> (4 * q)) & 15u;
+            p.out.bin_of_item[base + ((perm >> (3 * q)) & 7u)] = __popc(used & ((1u << slot) - 1u));
+        }
+    }
+    p.out.unit_count[uid] = cnt;
+    p.out.unit_total[uid] = static_cast<int64_t>(total);
+}
+
+template <int S, int CRIT>
+__global__ void __launch_bounds__(128) h2_pack_kernel_reg(const H2Params p) {
+    constexpr int kWarps = 4;
+    constexpr int kRun = 16;                 // sublists per run
+    constexpr int kSlots = 2 * S;
+    __shared__ uint32_t permtab[h2_table_size(S)];
     __shared__ uint32_t Bs[kMaxTypes];
-    __shared__ uint32_t wsub[8];
-    __shared__ uint32_t tstar[8];
-    const int T = static_cast<int>(blockDim.x);
+    __shared__ uint32_t wrun[kRun * S];
+    __shared__ uint32_t brun[kRun * S];
     const int tid = static_cast<int>(threadIdx.x);
-    const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
-    int pfull[S];
-    h2_decode<S>(tid, S, pfull);                     // this thread's permutation of S items
+    const int lane = tid & 31, warp = tid >> 5;
+
+    // permutation tables: entry off(k) + rank = rank's permutation of k items
+    for (int e = tid; e < h2_table_size(S); e += blockDim.x) {
+        int k = 0;
+        while (k < S && e >= h2_table_off(k + 1)) ++k;
+        int perm[S];
+        h2_decode<S>(e - h2_table_off(k), k, perm);
+        uint32_t packed = 0;
+        for (int q = 0; q < k; ++q) packed |= static_cast<uint32_t>(perm[q]) << (3 * q);
+        permtab[e] = packed;
+    }
+    __syncthreads();
 
     int64_t u_begin = 0, u_end = p.units.unit_base[p.in.N];
     if (p.only_instance >= 0) {
         u_begin = p.units.unit_base[p.only_instance];
         u_end = p.units.unit_base[p.only_instance + 1];
     }
-    // Each block takes runs of kRun consecutive sublists, so the instance is
-    // found once per run and its metadata reloaded only when the run crosses
-    // into the next instance (sublists are numbered instance by instance).
-    constexpr int kRun = 16;
+    // Each block takes runs of kRun consecutive sublists (numbered instance
+    // by instance), in segments, one per instance a run touches: a segment's
+    // items are consecutive in w_all and are staged in shared memory once,
+    // each with the capacity of the smallest type holding it; the warps then
+    // take the segment's sublists in turn.
     for (int64_t r0 = u_begin + static_cast<int64_t>(blockIdx.x) * kRun; r0 < u_end;
          r0 += static_cast<int64_t>(gridDim.x) * kRun) {
         const int64_t r1 = (r0 + kRun) < u_end ? (r0 + kRun) : u_end;
         int64_t i = p.units.instance_of(r0, p.in.N);
-        int64_t ub = p.units.unit_base[i], ub_next = p.units.unit_base[i + 1];
-        int32_t st = p.out.status[i];
-        int64_t m = p.in.m(i), wb = p.in.w_begin(i);
-        int32_t n = p.in.n(i);
-        const int32_t* B = p.in.B_all + p.in.B_begin(i);
-        for (int64_t uid = r0; uid < r1; ++uid) {
-            while (uid >= ub_next) {                 // next instance with sublists
-                ++i;
-                ub = ub_next;
-                ub_next = p.units.unit_base[i + 1];
-                st = p.out.status[i];
-                m = p.in.m(i);
-                wb = p.in.w_begin(i);
-                n = p.in.n(i);
-                B = p.in.B_all + p.in.B_begin(i);
-            }
-            if (st != VSBPP_OK) continue;
-            const int64_t g = uid - ub;
-            const int64_t a = g * S;
-            const int k = static_cast<int>((m - a) < S ? (m - a) : S);
-            const int nperm = h2_fact_small(k);
-            const int32_t* w = p.in.w_all + wb + a;
+        int64_t uid = r0;
+        while (uid < r1) {
+            while (uid >= p.units.unit_base[i + 1]) ++i;     // instance of this segment
+            const int64_t ub = p.units.unit_base[i];
+            const int64_t seg_end = p.units.unit_base[i + 1] < r1 ? p.units.unit_base[i + 1] : r1;
+            if (p.out.status[i] != VSBPP_OK) { uid = seg_end; continue; }
+            const int64_t m = p.in.m(i), wb = p.in.w_begin(i);
+            const int32_t n = p.in.n(i);
+            const int32_t* B = p.in.B_all + p.in.B_begin(i);
+            const int64_t a0 = (uid - ub) * S;
+            const int64_t a1 = (seg_end - ub) * S < m ? (seg_end - ub) * S : m;
+            const int cnt = static_cast<int>(a1 - a0);
             if (tid < kMaxTypes) Bs[tid] = tid < n ? static_cast<uint32_t>(B[tid]) : 0u;
-            if (tid < k) {
-                const int32_t x = w[tid];
-                uint32_t t = 0;
-                for (int y = 0; y < n; ++y)
-                    if (B[y] >= x) t = static_cast<uint32_t>(y);
-                wsub[tid] = static_cast<uint32_t>(x);
-                tstar[tid] = t;
+            for (int t = tid; t < cnt; t += blockDim.x) {
+                const uint32_t x = static_cast<uint32_t>(p.in.w_all[wb + a0 + t]);
+                uint32_t bn = 0;
+                for (int y = 0; y < n; ++y) {
+                    const uint32_t c = static_cast<uint32_t>(B[y]);
+                    bn = c >= x ? c : bn;
+                }
+                wrun[t] = x;
+                brun[t] = bn;
             }
             __syncthreads();
-
-            unsigned long long key = ~0ull;
-            int perm[S], raw[S];
-            uint32_t res[kBins], typ[kBins];
-    #pragma unroll
-            for (int x = 0; x < kBins; ++x) { res[x] = 0; typ[x] = 0; }
-            int L = 0;
-            const bool active = tid < nperm;
-            if (active) {
-                if (k == S) {
-    #pragma unroll
-                    for (int q = 0; q < S; ++q) perm[q] = pfull[q];
+            const bool narrow = static_cast<uint32_t>(B[0]) <= 4095u;
+            for (int64_t u = uid + warp; u < seg_end; u += kWarps) {
+                const int64_t g = u - ub;
+                const int64_t a = g * S;
+                const int k = static_cast<int>((m - a) < S ? (m - a) : S);
+                const int nperm = h2_fact_small(k);
+                const uint32_t* ws = wrun + (a - a0);
+                const uint32_t* bs = brun + (a - a0);
+                const uint32_t* tab = permtab + h2_table_off(k);
+                if (narrow) {
+                    uint32_t bestkey = 0xFFFFFFFFu, bv[kSlots], brawp = 0, bperm = 0;
+#pragma unroll
+                    for (int x = 0; x < kSlots; ++x) bv[x] = 0u;
+                    for (int rb = 0; rb < nperm; rb += 32) {
+                        const int rank = rb + lane;
+                        const bool active = rank < nperm;
+                        const uint32_t perm = tab[active ? rank : 0];
+                        uint32_t v[kSlots], rawp;
+                        const uint32_t tot = k == S
+                            ? h2_pack_narrow<S, CRIT, S>(perm, k, ws, bs, p.seed, g, rank, v, rawp)
+                            : h2_pack_narrow<S, CRIT, 0>(perm, k, ws, bs, p.seed, g, rank, v, rawp);
+                        const uint32_t key = active ? (tot << 10) | static_cast<uint32_t>(rank) : 0xFFFFFFFFu;
+                        const bool better = key < bestkey;
+                        bestkey = better ? key : bestkey;
+                        brawp = better ? rawp : brawp;
+                        bperm = better ? perm : bperm;
+#pragma unroll
+                        for (int x = 0; x < kSlots; ++x) bv[x] = better ? v[x] : bv[x];
+                    }
+                    const uint32_t wkey = __reduce_min_sync(kFull, bestkey);
+                    if (bestkey == wkey) {
+                        uint32_t used = 0, capx[kSlots];
+#pragma unroll
+                        for (int x = 0; x < kSlots; ++x) {
+                            capx[x] = bv[x] & 0xFFFu;
+                            used |= ((bv[x] >> 16) < capx[x] ? 1u : 0u) << x;
+                        }
+                        h2_write_winner<S>(p, capx, used, brawp, bperm, k, Bs, n, u, wb + a, wkey >> 10);
+                    }
                 } else {
-                    h2_decode<S>(tid, k, perm);
-                }
-    #pragma unroll
-                for (int q = 0; q < S; ++q) {
-                    raw[q] = 0;
-                    if (q < k) {
-                        const int item = perm[q];
-                        const uint32_t wj = wsub[item];
-                        const int c = CRIT == kRandom
-                                          ? pick_criterion(kRandom, p.seed,
-                                                           static_cast<uint64_t>((g * 720 + tid) * 8 + q))
-                                          : CRIT;
-                        int chosen = -1;
-                        uint32_t cr = 0, ct = 0;             // residual and type of the choice
-    #pragma unroll
-                        for (int x = 0; x < 2 * q; ++x) {        // Rule 4 over the live bins
-                            const uint32_t r = res[x];
-                            if (x < L && r >= wj &&
-                                (chosen < 0 || (c == kBF && r < cr) || (c == kWF && r > cr))) {
-                                chosen = x;
-                                cr = r;
-                                ct = typ[x];
-                            }
+                    uint64_t bestkey = ~0ull;
+                    uint32_t br[kSlots], bc[kSlots], brawp = 0, bperm = 0;
+#pragma unroll
+                    for (int x = 0; x < kSlots; ++x) { br[x] = 0u; bc[x] = 0u; }
+                    for (int rb = 0; rb < nperm; rb += 32) {
+                        const int rank = rb + lane;
+                        const bool active = rank < nperm;
+                        const uint32_t perm = tab[active ? rank : 0];
+                        uint32_t r[kSlots], c[kSlots], rawp;
+                        const uint64_t tot = h2_pack_wide<S, CRIT>(perm, k, ws, bs, p.seed, g, rank, r, c, rawp);
+                        const uint64_t key = active ? (tot << 10) | static_cast<uint64_t>(rank) : ~0ull;
+                        const bool better = key < bestkey;
+                        bestkey = better ? key : bestkey;
+                        brawp = better ? rawp : brawp;
+                        bperm = better ? perm : bperm;
+#pragma unroll
+                        for (int x = 0; x < kSlots; ++x) {
+                            br[x] = better ? r[x] : br[x];
+                            bc[x] = better ? c[x] : bc[x];
                         }
-                        const bool opened = chosen < 0;
-                        if (opened) {                           // smallest type holding w
-                            ct = tstar[item];
-                            cr = Bs[ct];
-                            chosen = L;
-                            ++L;
-                        }
-                        const uint32_t Bt = Bs[ct];
-                        const uint32_t r_new = cr - wj;
-                        const bool fire = (static_cast<uint64_t>(Bt) < 2ull * cr) &&
-                                          (2ull * r_new <= static_cast<uint64_t>(Bt));   // Rule 5
-    #pragma unroll
-                        for (int x = 0; x < 2 * q + 2 && x < kBins; ++x) {
-                            if (x == chosen) res[x] = r_new;
-                            if ((opened && x == chosen) || (fire && x == L)) typ[x] = ct;
-                            if (fire && x == L) res[x] = Bt;
-                        }
-                        if (fire) ++L;
-                        raw[q] = chosen;
+                    }
+                    const uint64_t wkey = warp_min_u64(bestkey);
+                    if (bestkey == wkey) {
+                        uint32_t used = 0;
+#pragma unroll
+                        for (int x = 0; x < kSlots; ++x) used |= (br[x] < bc[x] ? 1u : 0u) << x;
+                        h2_write_winner<S>(p, bc, used, brawp, bperm, k, Bs, n, u, wb + a, wkey >> 10);
                     }
                 }
-                unsigned long long tot = 0;
-    #pragma unroll
-                for (int x = 0; x < kBins; ++x) {
-                    const uint32_t cap = Bs[typ[x]];
-                    if (x < L && res[x] < cap) tot += cap;
-                }
-                key = (tot << 10) | static_cast<unsigned long long>(tid);
             }
-            key = warp_min_u64(key);
-            if (lane == 0) wbest[warp] = key;
-            __syncthreads();
-            unsigned long long best = ~0ull;
-            for (int x = 0; x < nwarps; ++x) best = wbest[x] < best ? wbest[x] : best;
-            if (active && tid == static_cast<int>(best & 1023ull)) {
-                // the winning permutation's result, in sublist-local form
-                bool used[kBins];
-                int cnt = 0;
-    #pragma unroll
-                for (int x = 0; x < kBins; ++x) {
-                    used[x] = x < L && res[x] < Bs[typ[x]];
-                    if (used[x]) {
-                        p.out.local_types[wb + a + cnt] = static_cast<int32_t>(typ[x]);
-                        ++cnt;
-                    }
-                }
-    #pragma unroll
-                for (int q = 0; q < S; ++q) {
-                    if (q < k) {
-                        int d = 0;
-    #pragma unroll
-                        for (int x = 0; x < kBins; ++x)
-                            if (x < raw[q] && used[x]) ++d;
-                        p.out.bin_of_item[wb + a + perm[q]] = d;
-                    }
-                }
-                p.out.unit_count[uid] = cnt;
-                p.out.unit_total[uid] = static_cast<int64_t>(best >> 10);
-            }
-            __syncthreads();
+            __syncthreads();                         // staged items are reused by the next segment
+            uid = seg_end;
         }
     }
 }
