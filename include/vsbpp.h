@@ -227,13 +227,15 @@ int vsbpp_pack_plain(int64_t N, const int32_t *w_all, const int64_t *w_off,
                      void *stream);
 
 /*
- * Work counters (tracing).  While enabled, the first-heuristic kernels add
- * to two device counters: the items they pack, and the fit tests the method
+ * Work counters (tracing).  While enabled, the first-heuristic kernels and
+ * the second heuristic's register kernel (no pre-opened bins) add to two
+ * device counters: the items they pack, and the fit tests the method
  * performs -- for every item, one per bin membrane alive when it arrives
  * (Rule 4 tests every open bin), whether or not a kernel stops a first-fit
- * scan early.  Enabling affects launches made (or plans recorded) afterwards.
- * vsbpp_counters_read synchronises the device, copies the counters and, if
- * reset != 0, sets them back to zero.
+ * scan early; for the second heuristic, summed over every permutation each
+ * sublist tries (Section 6.4).  Enabling affects launches made (or plans
+ * recorded) afterwards.  vsbpp_counters_read synchronises the device, copies
+ * the counters and, if reset != 0, sets them back to zero.
  */
 typedef struct {
     uint64_t items;
@@ -242,6 +244,20 @@ typedef struct {
 
 int vsbpp_counters_enable(int enable);
 int vsbpp_counters_read(vsbpp_counters *out, int reset);
+
+/*
+ * Kernel timing (measurement).  While enabled, every vsbpp_pack_batch call
+ * made on a stream that is not capturing records a CUDA event pair on that
+ * stream around its main packing kernel: the first-heuristic kernel of the
+ * instances held in shared memory (the large class), or the second-
+ * heuristic kernel.  Up to 256 pairs are kept (the oldest are overwritten).
+ * vsbpp_kernel_timing_read waits for the recorded pairs, writes up to `max`
+ * durations in milliseconds to ms[] (oldest first), their number to *count,
+ * and forgets them.  Enabling or disabling also forgets them.
+ * Errors: EINVAL for a null count or a null ms with max > 0; ECUDA.
+ */
+int vsbpp_kernel_timing_enable(int enable);
+int vsbpp_kernel_timing_read(float *ms, int32_t max, int32_t *count);
 
 /*
  * Plans: a batch shape recorded once into a CUDA graph and replayed.

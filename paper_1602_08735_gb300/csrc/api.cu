@@ -28,6 +28,44 @@ std::recursive_mutex g_mu;
 std::atomic<int> g_last_cuda{0};
 unsigned long long* g_counters = nullptr;   // device {items, fit tests} or null
 
+// Kernel timing: a ring of CUDA event pairs recorded around the main
+// packing launch of calls made outside stream capture.
+struct KernelTiming {
+    static constexpr int kRing = 256;
+    bool on = false;
+    int dev = -1;
+    cudaEvent_t ev[kRing][2] = {};
+    int head = 0, count = 0;       // pairs recorded since the last read (oldest at head - count)
+} g_timing;
+
+// Records the start event of the main launch on `st` when timing applies.
+bool timing_begin(cudaStream_t st) {
+    if (!g_timing.on) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_timing.dev != dev) {
+        for (auto& pr : g_timing.ev)
+            for (auto& e : pr)
+                if (e) { cudaEventDestroy(e); e = nullptr; }
+        g_timing.dev = dev;
+        g_timing.head = g_timing.count = 0;
+    }
+    auto& pr = g_timing.ev[g_timing.head];
+    for (auto& e : pr)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) return false;
+    return cudaEventRecord(pr[0], st) == cudaSuccess;
+}
+
+void timing_end(bool started, cudaStream_t st) {
+    if (!started) return;
+    auto& pr = g_timing.ev[g_timing.head];
+    if (cudaEventRecord(pr[1], st) != cudaSuccess) return;
+    g_timing.head = (g_timing.head + 1) % KernelTiming::kRing;
+    if (g_timing.count < KernelTiming::kRing) ++g_timing.count;
+}
+
 struct DeviceInfo {
     int dev = -1;
     int sms = 0;
@@ -436,7 +474,9 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
                 p.spill_list = sc.spill_list;
                 p.spill_seg = sc.spill_seg();
             }
+            const bool timed = c == kClassLarge && timing_begin(st);
             VS_TRY(launch_shape(sh, c == kClassWide, p, sh.groups, sh.grid, st));
+            timing_end(timed, st);
         }
         {
             // systems that outgrew their slots, repacked from the start at full size
@@ -502,7 +542,10 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
             hp.sublist = static_cast<int32_t>(lp.mode.s);
             hp.max_bins = lp.h2_max_bins;
             hp.only_instance = only;
+            hp.counters = g_counters;
+            const bool timed = !plain && timing_begin(st);
             VS_TRY(h2_launch(hp, lp.h2_threads, plain ? 1 : lp.h2_grid, lp.h2_smem, st));
+            timing_end(timed, st);
         } else {
             H1Params p = h1_params(in, out, prm, lp.sub);
             p.units.unit_base = sc.unit_base;
@@ -736,6 +779,31 @@ int vsbpp_counters_read(vsbpp_counters* out, int reset) {
     if (reset) VS_TRY(cudaMemset(g_counters, 0, sizeof(v)));
     out->items = v[0];
     out->fit_tests = v[1];
+    return VSBPP_OK;
+}
+
+int vsbpp_kernel_timing_enable(int enable) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    g_timing.on = enable != 0;
+    g_timing.count = 0;
+    return VSBPP_OK;
+}
+
+int vsbpp_kernel_timing_read(float* ms, int32_t max, int32_t* count) {
+    if (!count || max < 0 || (max > 0 && !ms)) return VSBPP_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    *count = 0;
+    const int have = g_timing.count;
+    const int first = (g_timing.head - have + KernelTiming::kRing) % KernelTiming::kRing;
+    for (int x = 0; x < have && x < max; ++x) {
+        auto& pr = g_timing.ev[(first + x) % KernelTiming::kRing];
+        VS_TRY(cudaEventSynchronize(pr[1]));
+        float t = 0.f;
+        VS_TRY(cudaEventElapsedTime(&t, pr[0], pr[1]));
+        ms[x] = t;
+        ++*count;
+    }
+    g_timing.count = 0;
     return VSBPP_OK;
 }
 

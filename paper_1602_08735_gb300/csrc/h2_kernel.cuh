@@ -237,17 +237,19 @@ __device__ __forceinline__ uint32_t h2_min_tree(uint32_t (&t)[N], int cnt) {
 // Pack one permutation, narrow slot words.  Returns the used capacity (a
 // bin's capacity counts from the item that finds it empty); rawp gets the
 // slot of the item at step q in bits 4q..4q+3.  K > 0: exactly K items
-// (compile time); K = 0: k items.
-template <int S, int CRIT, int K>
+// (compile time); K = 0: k items.  COUNT: fit gets the fit tests of the
+// method (bins alive when each item arrives).
+template <int S, int CRIT, int K, bool COUNT>
 __device__ __forceinline__ uint32_t h2_pack_narrow(uint32_t perm, int k, const uint32_t* wsub,
                                                    const uint32_t* bnew, uint64_t seed, int64_t g, int rank,
-                                                   uint32_t (&v)[2 * S], uint32_t& rawp) {
+                                                   uint32_t (&v)[2 * S], uint32_t& rawp, uint32_t& fit) {
     constexpr int kSlots = 2 * S;
     constexpr uint32_t kNo = 0xFFFFFFFFu;
 #pragma unroll
     for (int x = 0; x < kSlots; ++x) v[x] = 0u;
     rawp = 0;
-    uint32_t tot = 0;
+    uint32_t tot = 0, alive = 0;
+    fit = 0;
 #pragma unroll
     for (int q = 0; q < S; ++q) {
         if (K > 0 ? q < K : q < k) {
@@ -284,6 +286,10 @@ __device__ __forceinline__ uint32_t h2_pack_narrow(uint32_t perm, int k, const u
             const uint32_t r_new = r_old - wq;
             const bool fire = (cap < 2u * r_old) && (2u * r_new <= cap);     // Rule 5
             tot += r_old == cap ? cap : 0u;        // the bin's first item: it becomes used
+            if (COUNT) {
+                fit += alive;
+                alive += (hit ? 0u : 1u) + (fire ? 1u : 0u);
+            }
 #pragma unroll
             for (int x = 0; x < 2 * q; ++x) v[x] = xs == static_cast<uint32_t>(x) ? v[x] - W : v[x];
             v[2 * q] = hit ? 0u : (r_new << 16) | (static_cast<uint32_t>(2 * q) << 12) | cap;
@@ -454,10 +460,17 @@ __global__ void __launch_bounds__(128) h2_pack_kernel_reg(const H2Params p) {
                         const int rank = rb + lane;
                         const bool active = rank < nperm;
                         const uint32_t perm = tab[active ? rank : 0];
-                        uint32_t v[kSlots], rawp;
-                        const uint32_t tot = k == S
-                            ? h2_pack_narrow<S, CRIT, S>(perm, k, ws, bs, p.seed, g, rank, v, rawp)
-                            : h2_pack_narrow<S, CRIT, 0>(perm, k, ws, bs, p.seed, g, rank, v, rawp);
+                        uint32_t v[kSlots], rawp, fit = 0;
+                        uint32_t tot;
+                        if (p.counters) {
+                            tot = h2_pack_narrow<S, CRIT, 0, true>(perm, k, ws, bs, p.seed, g, rank, v, rawp, fit);
+                            fit = __reduce_add_sync(kFull, active ? fit : 0u);
+                            if (lane == 0) atomicAdd(p.counters + 1, static_cast<unsigned long long>(fit));
+                        } else if (k == S) {
+                            tot = h2_pack_narrow<S, CRIT, S, false>(perm, k, ws, bs, p.seed, g, rank, v, rawp, fit);
+                        } else {
+                            tot = h2_pack_narrow<S, CRIT, 0, false>(perm, k, ws, bs, p.seed, g, rank, v, rawp, fit);
+                        }
                         const uint32_t key = active ? (tot << 10) | static_cast<uint32_t>(rank) : 0xFFFFFFFFu;
                         const bool better = key < bestkey;
                         bestkey = better ? key : bestkey;
@@ -466,6 +479,7 @@ __global__ void __launch_bounds__(128) h2_pack_kernel_reg(const H2Params p) {
 #pragma unroll
                         for (int x = 0; x < kSlots; ++x) bv[x] = better ? v[x] : bv[x];
                     }
+                    if (p.counters && lane == 0) atomicAdd(p.counters, static_cast<unsigned long long>(k));
                     const uint32_t wkey = __reduce_min_sync(kFull, bestkey);
                     if (bestkey == wkey) {
                         uint32_t used = 0, capx[kSlots];

@@ -17,6 +17,7 @@ struct H2Params {
     int32_t perms;        // s!
     int32_t max_bins;     // 2*s + (preopen ? 32 : 0)
     int64_t only_instance;  // -1: every unit; else only that instance's sublists
+    unsigned long long* counters;   // null, or {items, fit tests} to add to (register kernel)
 };
 
 __host__ __device__ inline int h2_smem_bytes(int threads, int max_bins) {

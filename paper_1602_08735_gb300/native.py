@@ -27,6 +27,7 @@ EXPORTS = (
     "vsbpp_pack", "vsbpp_pack_device", "vsbpp_pack_batch", "vsbpp_pack_plain",
     "vsbpp_pack_batch_noalloc",
     "vsbpp_counters_enable", "vsbpp_counters_read",
+    "vsbpp_kernel_timing_enable", "vsbpp_kernel_timing_read",
     "vsbpp_plan_create", "vsbpp_plan_run", "vsbpp_plan_destroy",
     "vsbpp_get_config", "vsbpp_set_config", "vsbpp_autotune", "vsbpp_tune_save", "vsbpp_tune_load",
     "vsbpp_server_create", "vsbpp_server_submit", "vsbpp_server_poll", "vsbpp_server_stats",
@@ -105,6 +106,11 @@ def load(path: str = LIB_PATH):
         lib.vsbpp_counters_enable.argtypes = [ctypes.c_int]
         lib.vsbpp_counters_read.restype = ctypes.c_int
         lib.vsbpp_counters_read.argtypes = [ctypes.POINTER(Counters), ctypes.c_int]
+        lib.vsbpp_kernel_timing_enable.restype = ctypes.c_int
+        lib.vsbpp_kernel_timing_enable.argtypes = [ctypes.c_int]
+        lib.vsbpp_kernel_timing_read.restype = ctypes.c_int
+        lib.vsbpp_kernel_timing_read.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_int32)]
         lib.vsbpp_get_config.restype = ctypes.c_int
         lib.vsbpp_get_config.argtypes = [ctypes.POINTER(Config)]
         lib.vsbpp_set_config.restype = ctypes.c_int
@@ -301,6 +307,22 @@ def counters_enable(on: bool = True) -> None:
     rc = load().vsbpp_counters_enable(1 if on else 0)
     if rc != 0:
         raise VsbppError(rc, "vsbpp_counters_enable")
+
+
+def kernel_timing_enable(on: bool = True) -> None:
+    rc = load().vsbpp_kernel_timing_enable(1 if on else 0)
+    if rc != 0:
+        raise VsbppError(rc, "vsbpp_kernel_timing_enable")
+
+
+def kernel_timing_read(max_n: int = 256) -> list:
+    """Durations (ms) of the main packing kernel of each timed call, oldest first."""
+    buf = (ctypes.c_float * max_n)()
+    n = ctypes.c_int32(0)
+    rc = load().vsbpp_kernel_timing_read(buf, max_n, ctypes.byref(n))
+    if rc != 0:
+        raise VsbppError(rc, "vsbpp_kernel_timing_read")
+    return [float(buf[i]) for i in range(n.value)]
 
 
 def counters_read(reset: bool = True) -> dict:
