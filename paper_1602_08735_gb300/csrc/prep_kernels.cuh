@@ -43,22 +43,27 @@ __global__ void validate_kernel(const PrepParams p) {
             B1 = __shfl_sync(kFull, b, 0);
         }
         if (code == VSBPP_OK) {
+            // the first bad weight (in list order) decides the code; eight
+            // independent loads per lane per trip keep the loads in flight
             const int32_t* w = p.in.w_all + p.in.w_begin(i);
-            for (int64_t j0 = 0; j0 < m; j0 += 32) {
-                const int64_t j = j0 + lane;
-                int e = 0;
-                if (j < m) {
-                    const int32_t x = w[j];
-                    e = x < 1 ? 1 : (x > B1 ? 2 : 0);
+            unsigned long long first = ~0ull;          // (index << 2) | kind of this lane's first bad weight
+            for (int64_t j0 = 0; j0 < m; j0 += 256) {
+                int32_t x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int64_t j = j0 + 32 * u + lane;
+                    x[u] = j < m ? __ldg(w + j) : 1;
                 }
-                const unsigned badm = __ballot_sync(kFull, e != 0);
-                if (badm) {
-                    const int first = __ffs(badm) - 1;
-                    const int ef = __shfl_sync(kFull, e, first);
-                    code = ef == 1 ? VSBPP_EINVAL : VSBPP_ETOOBIG;
-                    break;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int64_t j = j0 + 32 * u + lane;
+                    const int e = x[u] < 1 ? 1 : (x[u] > B1 ? 2 : 0);
+                    const unsigned long long k = (static_cast<unsigned long long>(j) << 2) | static_cast<unsigned>(e);
+                    first = (e != 0 && k < first) ? k : first;
                 }
             }
+            first = warp_min_u64(first);
+            if (first != ~0ull) code = (first & 3ull) == 1ull ? VSBPP_EINVAL : VSBPP_ETOOBIG;
         }
         int c = kClassNone;
         if (code == VSBPP_OK && m > 0 && p.classify) {
@@ -188,15 +193,41 @@ __global__ void compose_kernel(const ComposeParams p) {
             const int64_t my_off = off + ex;
             const int64_t first = (u0 - ub) * s;
             const int64_t last = (first + 32 * s) < m ? (first + 32 * s) : m;
-            for (int64_t x0 = first; x0 < last; x0 += 32) {
-                const int64_t x = x0 + lane;
-                const int src = static_cast<int>(x < last ? (x - first) / s : 0);
-                const int64_t o = __shfl_sync(kFull, my_off, src);
-                if (x < last) p.out.bin_of_item[wb + x] += static_cast<int32_t>(o);
-            }
-            if (u < ue) {
+            if (s <= 6) {
+                // every load of the chunk is issued before its stores (at most
+                // 6 items and 12 bin types per lane)
+                int32_t item[6], typ[12];
+                int64_t item_off[6];
+#pragma unroll
+                for (int y = 0; y < 6; ++y) {
+                    const int64_t x = first + 32 * y + lane;
+                    const bool in = y < s && x < last;
+                    const int src = static_cast<int>(in ? (x - first) / s : 0);
+                    item_off[y] = __shfl_sync(kFull, my_off, src);
+                    item[y] = in ? p.out.bin_of_item[wb + x] : 0;
+                }
                 const int64_t la = wb + (u - ub) * s;
-                for (uint32_t d = 0; d < c; ++d) p.out.bin_type[wb + my_off + d] = p.out.local_types[la + d];
+#pragma unroll
+                for (int d = 0; d < 12; ++d) typ[d] = (u < ue && static_cast<uint32_t>(d) < c) ? p.out.local_types[la + d] : 0;
+#pragma unroll
+                for (int y = 0; y < 6; ++y) {
+                    const int64_t x = first + 32 * y + lane;
+                    if (y < s && x < last) p.out.bin_of_item[wb + x] = item[y] + static_cast<int32_t>(item_off[y]);
+                }
+#pragma unroll
+                for (int d = 0; d < 12; ++d)
+                    if (u < ue && static_cast<uint32_t>(d) < c) p.out.bin_type[wb + my_off + d] = typ[d];
+            } else {
+                for (int64_t x0 = first; x0 < last; x0 += 32) {
+                    const int64_t x = x0 + lane;
+                    const int src = static_cast<int>(x < last ? (x - first) / s : 0);
+                    const int64_t o = __shfl_sync(kFull, my_off, src);
+                    if (x < last) p.out.bin_of_item[wb + x] += static_cast<int32_t>(o);
+                }
+                if (u < ue) {
+                    const int64_t la = wb + (u - ub) * s;
+                    for (uint32_t d = 0; d < c; ++d) p.out.bin_type[wb + my_off + d] = p.out.local_types[la + d];
+                }
             }
             off += __shfl_sync(kFull, ex + c, 31);
             tot += warp_sum_u64(t);
