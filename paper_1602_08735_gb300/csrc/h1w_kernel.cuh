@@ -44,11 +44,12 @@ __host__ __device__ inline int h1w_ns(int slot_cap) {
 }
 
 // Shared memory of one warp: slots, a 16-byte pad (the write target of a bin
-// that does not divide), the BF rows (1024 residuals x NS words) when laid
-// out, capacities.
+// that does not divide), the BF rows (1024 residuals x NS words) and a
+// 16-byte pad (the target of index writes that do not apply) when laid out,
+// capacities.
 __host__ __device__ inline int h1w_group_bytes(int slot_cap, int bf_index) {
     const int ns = h1w_ns(slot_cap);
-    return 4 * slot_cap + 16 + (bf_index ? 4 * (kIndexMaxRes + 1) * ns : 0) + 4 * kMaxTypes;
+    return 4 * slot_cap + 16 + (bf_index ? 4 * (kIndexMaxRes + 1) * ns + 16 : 0) + 4 * kMaxTypes;
 }
 
 template <int NS, int CRIT>
@@ -56,6 +57,7 @@ struct H1Warp {
     static constexpr bool kSeg = CRIT != kBF;                      // FF or WF items occur
     static constexpr bool kBFItems = CRIT == kBF || CRIT == kRandom;
     static constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+    static constexpr uint32_t kRowsPad = (kIndexMaxRes + 1) * NS;   // index word past the rows
 
     uint32_t* slots;
     uint32_t* rows;      // BF index rows (null when not laid out)
@@ -138,6 +140,10 @@ struct H1Warp {
             }
         }
 
+        // The index entry of a divided-off bin is written during the next
+        // item (its row word read at that item's start, stored before the
+        // item reads any row), so the read-modify-write is off the chain.
+        uint32_t pend_at = kRowsPad, pend_bit = 0;
         // Items go in blocks of 32: lane l holds the descriptor of item
         // (block + l), and the weights of the next block are loaded a block
         // ahead.
@@ -168,6 +174,8 @@ struct H1Warp {
             const uint32_t Bn = (d >> 16) & 0x7FFFu;
             const int c = CRIT == kRandom ? static_cast<int>(((d >> 15) & 1u) | ((d >> 30) & 2u)) : CRIT;
             fit_tests += L;
+            uint32_t pend_word = 0;
+            if (IDX) pend_word = rows[pend_at];
 
             // 1. the segment holding the answer: sf; Mseg = its largest
             //    residual; R = the residual sought (BF, WF)
@@ -202,6 +210,9 @@ struct H1Warp {
                 key = __reduce_min_sync(kFull, key);
                 hit = key != kNoKey;
                 R = hit ? key : 0u;
+                rows[pend_at] = pend_word | pend_bit;        // the deferred entry, before any row read
+                pend_at = kRowsPad;
+                pend_bit = 0;
                 // the row the chosen bin leaves and the row it enters, read together
                 const uint32_t Rn = (hit ? R : Bn) - wj;
 #pragma unroll
@@ -282,7 +293,10 @@ struct H1Warp {
             //    capacity enter
             if (IDX) {
                 if (c != kBF) {
-                    // (RANDOM) an FF or WF item: the rows are read now
+                    // (RANDOM) an FF or WF item: the deferred entry, then the rows
+                    rows[pend_at] = pend_word | pend_bit;
+                    pend_at = kRowsPad;
+                    pend_bit = 0;
 #pragma unroll
                     for (int q = 0; q < NS; ++q) {
                         rw[q] = rows[r_old * NS + q];
@@ -293,32 +307,25 @@ struct H1Warp {
                     else
                         cR = cM;
                 }
-                if (hit && cR == 1u) {
-                    uint32_t any = 0, word = 0;
+                // selects and plain stores only: an update that does not
+                // apply writes the pad word
+                const bool clear = hit && cR == 1u;
+                uint32_t any = 0, word = 0, wnew = 0;
 #pragma unroll
-                    for (int q = 0; q < NS; ++q) {
-                        const bool here = (sb >> 5) == static_cast<uint32_t>(q);
-                        rw[q] = here ? rw[q] & ~(1u << (sb & 31)) : rw[q];
-                        word = here ? rw[q] : word;
-                        any |= rw[q];
-                    }
-                    rows[r_old * NS + (sb >> 5)] = word;
-                    wb = (!any && (r_old >> 5) == ulane) ? wb & ~(1u << (r_old & 31)) : wb;
+                for (int q = 0; q < NS; ++q) {
+                    const bool here = (sb >> 5) == static_cast<uint32_t>(q);
+                    const uint32_t cl = here ? rw[q] & ~(1u << (sb & 31)) : rw[q];
+                    word = here ? cl : word;
+                    any |= cl;
+                    wnew = here ? rn[q] : wnew;
                 }
-                if (r_new > 0u) {
-                    uint32_t word = 0;
-#pragma unroll
-                    for (int q = 0; q < NS; ++q) word = (sb >> 5) == static_cast<uint32_t>(q) ? rn[q] : word;
-                    rows[r_new * NS + (sb >> 5)] = word | (1u << (sb & 31));
-                    wb = (r_new >> 5) == ulane ? wb | (1u << (r_new & 31)) : wb;
-                }
-                if (fire) {
-                    // read after the stores above (same warp, program order)
-                    uint32_t* at = &rows[Bt * NS + (sfire >> 5)];
-                    const uint32_t word = *at;
-                    *at = word | (1u << (sfire & 31));
-                    wb = (Bt >> 5) == ulane ? wb | (1u << (Bt & 31)) : wb;
-                }
+                rows[clear ? r_old * NS + (sb >> 5) : kRowsPad] = word;
+                wb = (clear && !any && (r_old >> 5) == ulane) ? wb & ~(1u << (r_old & 31)) : wb;
+                rows[r_new > 0u ? r_new * NS + (sb >> 5) : kRowsPad] = wnew | (1u << (sb & 31));
+                wb = (r_new > 0u && (r_new >> 5) == ulane) ? wb | (1u << (r_new & 31)) : wb;
+                pend_at = fire ? Bt * NS + (sfire >> 5) : kRowsPad;
+                pend_bit = fire ? 1u << (sfire & 31) : 0u;
+                wb = (fire && (Bt >> 5) == ulane) ? wb | (1u << (Bt & 31)) : wb;
             }
             L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
             bout = ulane == jj ? b : bout;
@@ -348,7 +355,7 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
     g.rows = nullptr;
     if (p.bf_index) {
         g.rows = reinterpret_cast<uint32_t*>(base);
-        base += 4 * (kIndexMaxRes + 1) * NS;
+        base += 4 * (kIndexMaxRes + 1) * NS + 16;
     }
     g.Bs = reinterpret_cast<uint32_t*>(base);
 
