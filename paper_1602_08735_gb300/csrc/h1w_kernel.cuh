@@ -7,10 +7,13 @@
 // when a bin's load first reaches half its capacity), with the per-item work
 // arranged so that its dependent chain is as short as one warp can make it:
 //
-//   slot    one 32-bit word per bin, (residual << 16) | capacity.  The bin's
-//           index is its position, so a lane knows the index of every slot it
-//           reads, and its capacity (hence its type and its Rule 5 threshold)
-//           travels with the residual: no second lookup per item.
+//   slot    one 32-bit word per bin, (residual << 16) | capacity, or
+//           (residual << 10) | capacity when B_1 <= 1023.  The bin's index is
+//           its position, so a lane knows the index of every slot it reads,
+//           and its capacity (hence its type and its Rule 5 threshold)
+//           travels with the residual: no second lookup per item.  In the
+//           10-bit form a key (index << 20) | slot carries index, residual
+//           and capacity at once.
 //   segmax  the largest residual of each 128-bin segment, kept in registers:
 //           lane l holds segments l, l+32, ... (NS per lane).  FF finds its
 //           segment with one warp minimum over (segment, max) keys, WF with
@@ -99,13 +102,14 @@ struct H1Warp {
 
     // BF without the index (B_1 > 1023): the full scan over the live segments.
     // key = (r - w) << 15 | index; returns kNoKey when nothing fits.
+    template <int kR>
     __device__ __forceinline__ uint32_t bf_scan(uint32_t wj, uint32_t L) const {
         uint32_t key = kNoKey;
         const uint32_t nseg = (L + 127u) >> 7;
         for (uint32_t s = 0; s < nseg; ++s) {
             const uint4 Q = reinterpret_cast<const uint4*>(slots)[32u * s + static_cast<uint32_t>(lane)];
             const uint32_t base = 128u * s + 4u * static_cast<uint32_t>(lane);
-            const uint32_t r0 = Q.x >> 16, r1 = Q.y >> 16, r2 = Q.z >> 16, r3 = Q.w >> 16;
+            const uint32_t r0 = Q.x >> kR, r1 = Q.y >> kR, r2 = Q.z >> kR, r3 = Q.w >> kR;
             if (r3 >= wj) key = min(key, ((r3 - wj) << 15) | (base + 3u));
             if (r2 >= wj) key = min(key, ((r2 - wj) << 15) | (base + 2u));
             if (r1 >= wj) key = min(key, ((r1 - wj) << 15) | (base + 1u));
@@ -119,10 +123,12 @@ struct H1Warp {
     // (B_1 <= 1023), else the full scan.  The item step is straight-line code:
     // the chosen segment's quad is read whether or not a bin fits, and the
     // fitting / new-bin cases are merged by selects.
-    template <bool IDX>
+    template <bool IDX, bool W10>
     __device__ __forceinline__ bool run(const H1Params& p, int64_t i, const int32_t* w, int64_t key0,
                                         uint32_t k, int32_t* raw, int n, uint32_t& L_io,
                                         unsigned long long& fit_tests) const {
+        constexpr int kR = W10 ? 10 : 16;                 // residual shift in a slot
+        constexpr uint32_t kCap = W10 ? 0x3FFu : 0xFFFFu;   // capacity field
         uint32_t L = L_io;
         const uint32_t cap_bins = static_cast<uint32_t>(p.slot_cap);
         const uint32_t ulane = static_cast<uint32_t>(lane);
@@ -224,7 +230,7 @@ struct H1Warp {
                 for (int q = NS - 1; q >= 0; --q)
                     sf = rw[q] ? 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1) : sf;
             } else {
-                const uint32_t key = bf_scan(wj, L);
+                const uint32_t key = bf_scan<kR>(wj, L);
                 hit = key != kNoKey;
                 sf = hit ? (key & 0x7FFFu) >> 7 : 0u;
                 R = (key >> 15) + wj;
@@ -242,38 +248,53 @@ struct H1Warp {
             //    capacity) keys; cR = bins at R, cM = bins at Mseg, M2 = the
             //    largest residual other than Mseg
             const uint4 Q = reinterpret_cast<const uint4*>(slots)[32u * sf + ulane];
-            const uint32_t r0 = Q.x >> 16, r1 = Q.y >> 16, r2 = Q.z >> 16, r3 = Q.w >> 16;
-            const uint32_t c0 = Q.x & 0xFFFFu, c1 = Q.y & 0xFFFFu, c2 = Q.z & 0xFFFFu, c3 = Q.w & 0xFFFFu;
+            const uint32_t r0 = Q.x >> kR, r1 = Q.y >> kR, r2 = Q.z >> kR, r3 = Q.w >> kR;
+            const uint32_t c0 = Q.x & kCap, c1 = Q.y & kCap, c2 = Q.z & kCap, c3 = Q.w & kCap;
             const uint32_t i0 = (4u * ulane) << 16;
+            const uint32_t j0 = (4u * ulane) << 20;          // 10-bit form: index field of a key
             uint32_t k1 = kNoKey, k2 = kNoKey, cR = 0, cM = 0, M2 = 0;
             if (kSeg) {                     // these need only the quad: issued first
                 cM = __reduce_add_sync(kFull, (r0 == Mseg) + (r1 == Mseg) + (r2 == Mseg) + (r3 == Mseg));
                 M2 = __reduce_max_sync(kFull, max(max(r0 != Mseg ? r0 : 0u, r1 != Mseg ? r1 : 0u),
                                                   max(r2 != Mseg ? r2 : 0u, r3 != Mseg ? r3 : 0u)));
             }
-            if (c == kFF) {
+            if (c == kFF && W10) {
                 // keys grow with the index: the first fitting bin is the minimum
+                k1 = min(min(r0 >= wj ? j0 | Q.x : kNoKey, r1 >= wj ? (j0 + (1u << 20)) | Q.y : kNoKey),
+                         min(r2 >= wj ? (j0 + (2u << 20)) | Q.z : kNoKey, r3 >= wj ? (j0 + (3u << 20)) | Q.w : kNoKey));
+            } else if (c == kFF) {
                 k1 = min(min(r0 >= wj ? i0 | r0 : kNoKey, r1 >= wj ? (i0 + (1u << 16)) | r1 : kNoKey),
                          min(r2 >= wj ? (i0 + (2u << 16)) | r2 : kNoKey, r3 >= wj ? (i0 + (3u << 16)) | r3 : kNoKey));
                 k2 = min(min(r0 >= wj ? i0 | c0 : kNoKey, r1 >= wj ? (i0 + (1u << 16)) | c1 : kNoKey),
                          min(r2 >= wj ? (i0 + (2u << 16)) | c2 : kNoKey, r3 >= wj ? (i0 + (3u << 16)) | c3 : kNoKey));
                 k2 = __reduce_min_sync(kFull, k2);
+            } else if (W10) {
+                k1 = min(min(r0 == R ? j0 | Q.x : kNoKey, r1 == R ? (j0 + (1u << 20)) | Q.y : kNoKey),
+                         min(r2 == R ? (j0 + (2u << 20)) | Q.z : kNoKey, r3 == R ? (j0 + (3u << 20)) | Q.w : kNoKey));
+                if (IDX) cR = __reduce_add_sync(kFull, (r0 == R) + (r1 == R) + (r2 == R) + (r3 == R));
             } else {
                 k1 = min(min(r0 == R ? i0 | c0 : kNoKey, r1 == R ? (i0 + (1u << 16)) | c1 : kNoKey),
                          min(r2 == R ? (i0 + (2u << 16)) | c2 : kNoKey, r3 == R ? (i0 + (3u << 16)) | c3 : kNoKey));
                 if (IDX) cR = __reduce_add_sync(kFull, (r0 == R) + (r1 == R) + (r2 == R) + (r3 == R));
             }
             k1 = __reduce_min_sync(kFull, k1);
-            const uint32_t b = hit ? 128u * sf + (k1 >> 16) : L;
-            const uint32_t r_old = hit ? (c == kFF ? (k1 & 0xFFFFu) : R) : Bn;
-            const uint32_t Bt = hit ? ((c == kFF ? k2 : k1) & 0xFFFFu) : Bn;
+            uint32_t b, r_old, Bt;
+            if (W10) {                                 // (index << 20) | (residual << 10) | capacity
+                b = hit ? 128u * sf + (k1 >> 20) : L;
+                r_old = hit ? (k1 >> 10) & 0x3FFu : Bn;
+                Bt = hit ? k1 & 0x3FFu : Bn;
+            } else {
+                b = hit ? 128u * sf + (k1 >> 16) : L;
+                r_old = hit ? (c == kFF ? (k1 & 0xFFFFu) : R) : Bn;
+                Bt = hit ? ((c == kFF ? k2 : k1) & 0xFFFFu) : Bn;
+            }
             const uint32_t r_new = r_old - wj;
             const bool fire = (Bt < 2u * r_old) && (2u * r_new <= Bt);     // Rule 5
             const uint32_t Lf = hit ? L : L + 1u;      // where a divided-off bin goes
             // every lane writes the same words; a bin that does not divide
             // writes the pad word past the slots
-            slots[b] = (r_new << 16) | Bt;
-            slots[fire ? Lf : cap_bins] = (Bt << 16) | Bt;
+            slots[b] = (r_new << kR) | Bt;
+            slots[fire ? Lf : cap_bins] = (Bt << kR) | Bt;
             const uint32_t sb = b >> 7, sfire = Lf >> 7;
 
             // 3. segment maxima
@@ -397,6 +418,9 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         const uint32_t B1 = __shfl_sync(kFull, Bl, 0);
         const bool use_idx = g.rows != nullptr && H1Warp<NS, CRIT>::kBFItems &&
                              B1 <= static_cast<uint32_t>(kIndexMaxRes);
+        const bool w10 = B1 <= 1023u;                 // 10-bit slot form
+        const int kR = w10 ? 10 : 16;
+        const uint32_t kCapMask = w10 ? 0x3FFu : 0xFFFFu;
 
         // every slot reads as empty until its bin exists; index rows start clear
         for (int q = lane; q < p.slot_cap / 4; q += 32)
@@ -407,7 +431,7 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         uint32_t L = 0;
         if (p.preopen) {                     // literal Rule 2: one empty bin per type
             if (lane < n) {
-                g.slots[lane] = (Bl << 16) | Bl;
+                g.slots[lane] = (Bl << kR) | Bl;
                 if (use_idx) atomicOr(&g.rows[Bl * NS], 1u);     // segment 0
             }
             L = static_cast<uint32_t>(n);
@@ -415,11 +439,14 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         }
         unsigned long long fit_tests = 0;
         bool done;
+        const uint32_t k32 = static_cast<uint32_t>(k);
         if constexpr (H1Warp<NS, CRIT>::kBFItems) {
-            done = use_idx ? g.template run<true>(p, i, w, 0, static_cast<uint32_t>(k), raw, n, L, fit_tests)
-                           : g.template run<false>(p, i, w, 0, static_cast<uint32_t>(k), raw, n, L, fit_tests);
+            done = use_idx ? g.template run<true, true>(p, i, w, 0, k32, raw, n, L, fit_tests)
+                 : w10     ? g.template run<false, true>(p, i, w, 0, k32, raw, n, L, fit_tests)
+                           : g.template run<false, false>(p, i, w, 0, k32, raw, n, L, fit_tests);
         } else {
-            done = g.template run<false>(p, i, w, 0, static_cast<uint32_t>(k), raw, n, L, fit_tests);
+            done = w10 ? g.template run<false, true>(p, i, w, 0, k32, raw, n, L, fit_tests)
+                       : g.template run<false, false>(p, i, w, 0, k32, raw, n, L, fit_tests);
         }
         if (!done) continue;                 // spilled: a full-size launch repacks it
 
@@ -432,7 +459,7 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         uint32_t cnt = 0;
         for (uint32_t b = b0; b < b1; ++b) {
             const uint32_t s = g.slots[b];
-            cnt += static_cast<uint32_t>((s >> 16) < (s & 0xFFFFu));
+            cnt += static_cast<uint32_t>((s >> kR) < (s & kCapMask));
         }
         const uint32_t excl = warp_exclusive_scan(cnt, lane);
         const uint32_t used_total = __shfl_sync(kFull, excl + cnt, 31);
@@ -440,8 +467,8 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         uint64_t tot = 0;
         for (uint32_t b = b0; b < b1; ++b) {
             const uint32_t s = g.slots[b];
-            const uint32_t cap = s & 0xFFFFu;
-            if ((s >> 16) < cap) {
+            const uint32_t cap = s & kCapMask;
+            if ((s >> kR) < cap) {
                 types_out[dd] = static_cast<int32_t>(g.type_of(cap, n));
                 g.slots[b] = dd;
                 tot += cap;
