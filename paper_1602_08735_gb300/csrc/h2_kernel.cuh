@@ -239,19 +239,18 @@ __device__ __forceinline__ uint32_t h2_min_tree(uint32_t (&t)[N], int cnt) {
 // slot of the item at step q in bits 4q..4q+3.  K > 0: exactly K items
 // (compile time); K = 0: k items.  COUNT: fit gets the fit tests of the
 // method (bins alive when each item arrives).
-template <int S, int CRIT, int K, bool COUNT>
-__device__ __forceinline__ uint32_t h2_pack_narrow(uint32_t perm, int k, const uint32_t* wsub,
-                                                   const uint32_t* bnew, uint64_t seed, int64_t g, int rank,
-                                                   uint32_t (&v)[2 * S], uint32_t& rawp, uint32_t& fit) {
+// Item steps Q0 .. Q1-1 of one permutation, narrow slot words (running
+// state: slots v, slot per step rawp, used capacity tot; with COUNT, fit
+// tests fit and bins alive).  K > 0: exactly K items (compile time); K = 0:
+// k items.
+template <int S, int CRIT, int Q0, int Q1, int K, bool COUNT>
+__device__ __forceinline__ void h2_steps_narrow(uint32_t perm, int k, const uint32_t* wsub, const uint32_t* bnew,
+                                                uint64_t seed, int64_t g, int rank, uint32_t (&v)[2 * S],
+                                                uint32_t& rawp, uint32_t& tot, uint32_t& fit, uint32_t& alive) {
     constexpr int kSlots = 2 * S;
     constexpr uint32_t kNo = 0xFFFFFFFFu;
 #pragma unroll
-    for (int x = 0; x < kSlots; ++x) v[x] = 0u;
-    rawp = 0;
-    uint32_t tot = 0, alive = 0;
-    fit = 0;
-#pragma unroll
-    for (int q = 0; q < S; ++q) {
+    for (int q = Q0; q < Q1; ++q) {
         if (K > 0 ? q < K : q < k) {
             const uint32_t it = (perm >> (3 * q)) & 7u;
             const uint32_t wq = wsub[it], bn = bnew[it];
@@ -297,6 +296,18 @@ __device__ __forceinline__ uint32_t h2_pack_narrow(uint32_t perm, int k, const u
             rawp |= xs << (4 * q);
         }
     }
+}
+
+template <int S, int CRIT, int K, bool COUNT>
+__device__ __forceinline__ uint32_t h2_pack_narrow(uint32_t perm, int k, const uint32_t* wsub,
+                                                   const uint32_t* bnew, uint64_t seed, int64_t g, int rank,
+                                                   uint32_t (&v)[2 * S], uint32_t& rawp, uint32_t& fit) {
+#pragma unroll
+    for (int x = 0; x < 2 * S; ++x) v[x] = 0u;
+    rawp = 0;
+    uint32_t tot = 0, alive = 0;
+    fit = 0;
+    h2_steps_narrow<S, CRIT, 0, S, K, COUNT>(perm, k, wsub, bnew, seed, g, rank, v, rawp, tot, fit, alive);
     return tot;
 }
 
@@ -456,7 +467,52 @@ __global__ void __launch_bounds__(128) h2_pack_kernel_reg(const H2Params p) {
                     uint32_t bestkey = 0xFFFFFFFFu, bv[kSlots], brawp = 0, bperm = 0;
 #pragma unroll
                     for (int x = 0; x < kSlots; ++x) bv[x] = 0u;
-                    for (int rb = 0; rb < nperm; rb += 32) {
+                    // Full sublists, fixed criterion: permutations 2e and 2e+1
+                    // share their first S-2 items (they differ in the order of
+                    // the last two), so a lane packs that prefix once and
+                    // finishes both from copies of its state.
+                    constexpr bool kShare = CRIT != kRandom && S >= 3;
+                    const int nlane = (kShare && k == S) ? nperm / 2 : 0;
+                    for (int rb = 0; rb < nlane; rb += 32) {
+                        const int e = rb + lane;
+                        const bool active = e < nlane;
+                        const uint32_t pa = tab[active ? 2 * e : 0], pb = tab[active ? 2 * e + 1 : 1];
+                        uint32_t va[kSlots], rawa = 0, tota = 0, fita = 0, alivea = 0;
+#pragma unroll
+                        for (int x = 0; x < kSlots; ++x) va[x] = 0u;
+                        if (p.counters)
+                            h2_steps_narrow<S, CRIT, 0, S - 2, S, true>(pa, k, ws, bs, p.seed, g, 2 * e, va, rawa,
+                                                                     tota, fita, alivea);
+                        else
+                            h2_steps_narrow<S, CRIT, 0, S - 2, S, false>(pa, k, ws, bs, p.seed, g, 2 * e, va, rawa,
+                                                                      tota, fita, alivea);
+                        uint32_t vb[kSlots], rawb = rawa, totb = tota, fitb = fita, aliveb = alivea;
+#pragma unroll
+                        for (int x = 0; x < kSlots; ++x) vb[x] = va[x];
+                        if (p.counters) {
+                            h2_steps_narrow<S, CRIT, S - 2, S, S, true>(pa, k, ws, bs, p.seed, g, 2 * e, va, rawa,
+                                                                     tota, fita, alivea);
+                            h2_steps_narrow<S, CRIT, S - 2, S, S, true>(pb, k, ws, bs, p.seed, g, 2 * e + 1, vb,
+                                                                     rawb, totb, fitb, aliveb);
+                            const uint32_t f = __reduce_add_sync(kFull, active ? fita + fitb : 0u);
+                            if (lane == 0) atomicAdd(p.counters + 1, static_cast<unsigned long long>(f));
+                        } else {
+                            h2_steps_narrow<S, CRIT, S - 2, S, S, false>(pa, k, ws, bs, p.seed, g, 2 * e, va, rawa,
+                                                                      tota, fita, alivea);
+                            h2_steps_narrow<S, CRIT, S - 2, S, S, false>(pb, k, ws, bs, p.seed, g, 2 * e + 1, vb,
+                                                                      rawb, totb, fitb, aliveb);
+                        }
+                        const uint32_t ka = active ? (tota << 10) | static_cast<uint32_t>(2 * e) : 0xFFFFFFFFu;
+                        const uint32_t kb = active ? (totb << 10) | static_cast<uint32_t>(2 * e + 1) : 0xFFFFFFFFu;
+                        const bool ba = ka < bestkey && ka < kb;       // ka < kb: equal totals go to the lower rank
+                        const bool bb = !ba && kb < bestkey;
+                        bestkey = ba ? ka : bb ? kb : bestkey;
+                        brawp = ba ? rawa : bb ? rawb : brawp;
+                        bperm = ba ? pa : bb ? pb : bperm;
+#pragma unroll
+                        for (int x = 0; x < kSlots; ++x) bv[x] = ba ? va[x] : bb ? vb[x] : bv[x];
+                    }
+                    for (int rb = nlane > 0 ? nperm : 0; rb < nperm; rb += 32) {
                         const int rank = rb + lane;
                         const bool active = rank < nperm;
                         const uint32_t perm = tab[active ? rank : 0];
