@@ -62,6 +62,9 @@ def _bind(lib):
                                 i32p, i32p, i64p, i64p]
     lib.oracle_opt_bruteforce.restype = ctypes.c_int64
     lib.oracle_opt_bruteforce.argtypes = [i32p, ctypes.c_int32, i32p, ctypes.c_int32]
+    lib.oracle_fit_tests.restype = ctypes.c_uint64
+    lib.oracle_fit_tests.argtypes = [i32p, ctypes.c_int64, i32p, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64]
     lib.oracle_pack_many.restype = ctypes.c_int
     lib.oracle_pack_many.argtypes = [ctypes.c_int64, i32p, i64p, i32p, i32p,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
@@ -124,6 +127,16 @@ class OracleLib:
                                    _ptr(nb, ctypes.c_int64), _ptr(tot, ctypes.c_int64))
         k = int(nb[0])
         return PackResult(int(rc), bin_of_item[:m].copy(), bin_type[:k].copy(), k, int(tot[0]))
+
+    def fit_tests(self, w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
+                  preopen: int = 0, seed: int = 0) -> int:
+        """Rule 4 fit tests oracle_pack performs on this instance."""
+        w = np.ascontiguousarray(w, dtype=np.int32)
+        B = np.ascontiguousarray(B, dtype=np.int32)
+        wbuf = w if w.shape[0] > 0 else np.zeros(1, dtype=np.int32)
+        return int(self._lib.oracle_fit_tests(_ptr(wbuf, ctypes.c_int32), int(w.shape[0]),
+                                              _ptr(B, ctypes.c_int32), int(B.shape[0]), heuristic, criterion,
+                                              sublist_size, preopen, seed & (2**64 - 1)))
 
     def opt_bruteforce(self, w, B) -> int:
         """Exact VSBPP optimum by subset DP (m <= 20); -1 if infeasible/invalid."""
@@ -199,6 +212,11 @@ def splitmix64(seed: int, key: int) -> int:
 def pack(w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
          preopen: int = 0, seed: int = 0) -> PackResult:
     return default().pack(w, B, heuristic, criterion, sublist_size, preopen, seed)
+
+
+def fit_tests(w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
+              preopen: int = 0, seed: int = 0) -> int:
+    return default().fit_tests(w, B, heuristic, criterion, sublist_size, preopen, seed)
 
 
 def opt_bruteforce(w, B) -> int:

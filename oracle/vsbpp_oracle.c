@@ -68,6 +68,11 @@
 #define OR_H2_DEFAULT_SUBLIST 5
 #define OR_H2_MAX_SUBLIST 6
 
+/* Fit tests of Rule 4 performed by this thread's calls: for every item, one
+ * per bin membrane alive when it arrives (summed over every permutation the
+ * second heuristic tries).  Read by oracle_fit_tests. */
+static _Thread_local uint64_t or_fit_tests;
+
 /* ------------------------------------------------------------------------ */
 /* SplitMix64 (Steele, Lea & Flood 2014): state advances by the golden-ratio  */
 /* increment; the output is the state passed through the variant-13 mixer.   */
@@ -118,6 +123,7 @@ static int64_t or_membrane_run(const int32_t *seq, const int32_t *crit, int64_t 
         int64_t chosen_res = 0;
         /* Rule 4: every bin membrane tests whether w fits (G5); the
          * criterion picks one, lowest creation index on ties (G6). */
+        or_fit_tests += (uint64_t)nb;
         for (int64_t x = 0; x < nb; ++x) {
             const int64_t res = (int64_t)B[bins[x].type] - bins[x].load;
             if (res < w)
@@ -340,6 +346,29 @@ int oracle_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
     if (num_bins) *num_bins = bin_offset;
     if (total_capacity) *total_capacity = total;
     return OR_OK;
+}
+
+/*
+ * The number of Rule 4 fit tests (one per bin membrane alive when an item
+ * arrives; every permutation counted for the second heuristic) that
+ * oracle_pack performs for this instance.  Returns 0 on invalid input.
+ */
+uint64_t oracle_fit_tests(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                          int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                          int32_t preopen, uint64_t seed)
+{
+    int32_t *boi = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int32_t *bt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    if (!boi || !bt) {
+        free(boi); free(bt);
+        return 0;
+    }
+    or_fit_tests = 0;
+    int64_t nb = 0, tot = 0;
+    const int rc = oracle_pack(w, m, B, n, heuristic, criterion, sublist_size, preopen, seed,
+                               boi, bt, &nb, &tot);
+    free(boi); free(bt);
+    return rc == OR_OK ? or_fit_tests : 0;
 }
 
 /*

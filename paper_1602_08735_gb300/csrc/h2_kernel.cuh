@@ -315,12 +315,14 @@ __device__ __forceinline__ uint32_t h2_pack_narrow(uint32_t perm, int k, const u
 template <int S, int CRIT>
 __device__ __forceinline__ uint64_t h2_pack_wide(uint32_t perm, int k, const uint32_t* wsub, const uint32_t* bnew,
                                                  uint64_t seed, int64_t g, int rank, uint32_t (&r)[2 * S],
-                                                 uint32_t (&cp)[2 * S], uint32_t& rawp) {
+                                                 uint32_t (&cp)[2 * S], uint32_t& rawp, uint32_t& fit) {
     constexpr int kSlots = 2 * S;
     constexpr uint64_t kNo = ~0ull;
 #pragma unroll
     for (int x = 0; x < kSlots; ++x) { r[x] = 0u; cp[x] = 0u; }
     rawp = 0;
+    fit = 0;
+    uint32_t alive = 0;
 #pragma unroll
     for (int q = 0; q < S; ++q) {
         if (q < k) {
@@ -349,6 +351,8 @@ __device__ __forceinline__ uint64_t h2_pack_wide(uint32_t perm, int k, const uin
             const uint32_t r_new = r_old - wq;
             const bool fire = (static_cast<uint64_t>(cap) < 2ull * r_old) &&
                               (2ull * r_new <= static_cast<uint64_t>(cap));     // Rule 5
+            fit += alive;                      // Rule 4 fit tests (counters)
+            alive += (hit ? 0u : 1u) + (fire ? 1u : 0u);
 #pragma unroll
             for (int x = 0; x < 2 * q; ++x) r[x] = xs == static_cast<uint32_t>(x) ? r_new : r[x];
             r[2 * q] = hit ? 0u : r_new;
@@ -555,8 +559,12 @@ __global__ void __launch_bounds__(128) h2_pack_kernel_reg(const H2Params p) {
                         const int rank = rb + lane;
                         const bool active = rank < nperm;
                         const uint32_t perm = tab[active ? rank : 0];
-                        uint32_t r[kSlots], c[kSlots], rawp;
-                        const uint64_t tot = h2_pack_wide<S, CRIT>(perm, k, ws, bs, p.seed, g, rank, r, c, rawp);
+                        uint32_t r[kSlots], c[kSlots], rawp, fit;
+                        const uint64_t tot = h2_pack_wide<S, CRIT>(perm, k, ws, bs, p.seed, g, rank, r, c, rawp, fit);
+                        if (p.counters) {
+                            fit = __reduce_add_sync(kFull, active ? fit : 0u);
+                            if (lane == 0) atomicAdd(p.counters + 1, static_cast<unsigned long long>(fit));
+                        }
                         const uint64_t key = active ? (tot << 10) | static_cast<uint64_t>(rank) : ~0ull;
                         const bool better = key < bestkey;
                         bestkey = better ? key : bestkey;
@@ -568,6 +576,7 @@ __global__ void __launch_bounds__(128) h2_pack_kernel_reg(const H2Params p) {
                             bc[x] = better ? c[x] : bc[x];
                         }
                     }
+                    if (p.counters && lane == 0) atomicAdd(p.counters, static_cast<unsigned long long>(k));
                     const uint64_t wkey = warp_min_u64(bestkey);
                     if (bestkey == wkey) {
                         uint32_t used = 0;

@@ -29,6 +29,8 @@ import itertools
 import json
 import os
 
+import math
+
 import numpy as np
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
@@ -269,8 +271,35 @@ def pin_errors(lib):
     assert r.status == 0 and r.num_bins == 0 and r.total == 0
 
 
+def pin_fit_tests(lib, seed=16):
+    """The fit-test count (Rule 4: every bin membrane alive when an item
+    arrives tests it).  Closed form: with every weight equal to B_1 the first
+    item finds no bin, opens one, fills it and Rule 5 divides off an empty
+    bin; item j >= 1 then meets j + 1 bins, takes the empty one and divides
+    off another, so m items make 2 + 3 + ... + m = (m - 1)(m + 2) / 2 tests,
+    for every criterion and with one type or several.  The second heuristic
+    repeats that for each of the s! permutations of every sublist.  Hand
+    example (BF, B = {8, 6, 4}, w = 3,3,3,3,4,4,1): the 3s and 4s each fill a
+    fresh 4-bin that divides, so the items meet 0, 2, 3, 4, 5, 6, 7 bins: 27."""
+    assert lib.fit_tests([3, 3, 3, 3, 4, 4, 1], [8, 6, 4], 1, 1) == 27
+    rng = np.random.default_rng(seed)
+    for t in range(20):
+        n = int(rng.integers(1, 6))
+        B = sorted(rng.choice(np.arange(1, 500), size=n, replace=False).tolist(), reverse=True)
+        m = int(rng.integers(1, 60))
+        for crit in (0, 1, 2, 3):
+            assert lib.fit_tests([B[0]] * m, B, 1, crit, 0, 0, t) == (m - 1) * (m + 2) // 2
+        s = int(rng.integers(1, 7))
+        full, rest = divmod(m, s)
+        per = lambda k: (k - 1) * (k + 2) // 2 * math.factorial(k)
+        assert lib.fit_tests([B[0]] * m, B, 2, int(rng.integers(0, 3)), s) == full * per(s) + (per(rest) if rest else 0)
+    # with the literal Rule 2 start every item also meets the n pre-opened bins
+    assert lib.fit_tests([5], [5, 3], 1, 1, 0, 1) == 2
+
+
 ALL_PINS = [pin_hand_examples, pin_splitmix64, pin_textbook_n1, pin_optimum,
-            pin_closed_forms, pin_h2_is_best_permutation, pin_invariants, pin_errors]
+            pin_closed_forms, pin_h2_is_best_permutation, pin_invariants, pin_errors,
+            pin_fit_tests]
 
 
 def failing_pins(lib):

@@ -165,3 +165,71 @@ def test_server_concurrent_submitters_and_errors():
         t = srv.submit([0, 1], [5])
         rc, _ = srv.poll(t)
         assert rc == native.EINVAL
+
+
+@pytest.mark.parametrize("h,s", [(1, 0), (1, 7), (2, 5), (2, 4), (2, 6)])
+def test_counters_match_the_method_fit_tests(h, s):
+    """The kernels' fit-test counters equal the oracle's count of Rule 4 fit
+    tests (every bin alive when an item arrives; every permutation for the
+    second heuristic), instance by instance summed."""
+    b = I.config3(N=12, m_hi=700, seed=21)
+    db = native.DeviceBatch.from_host(b)
+    out = native.DeviceResult.empty(db.N, db.total_items)
+    native.counters_enable(True)
+    try:
+        for crit in (native.FF, native.BF, native.WF, native.RANDOM):
+            native.counters_read(reset=True)
+            assert native.pack_batch(db, out, h, crit, s, seed=9) == 0
+            got = native.counters_read(reset=True)
+            want = sum(oracle.fit_tests(*b.instance(i), h, crit, s, 0, 9) for i in range(b.N))
+            assert got["fit_tests"] == want, (h, s, crit)
+            assert got["items"] == b.total_items
+    finally:
+        native.counters_enable(False)
+
+
+def test_counters_second_heuristic_wide_capacities():
+    """Capacities above 4095 take the second heuristic's wide-slot path; its
+    counters follow the same definition."""
+    rng = np.random.default_rng(22)
+    inst = [(rng.integers(1, 9001, size=int(m)).astype(np.int32), np.array([9000, 5000, 4100], dtype=np.int32))
+            for m in rng.integers(20, 200, size=6)]
+    b = I.from_instances(inst)
+    db = native.DeviceBatch.from_host(b)
+    out = native.DeviceResult.empty(db.N, db.total_items)
+    native.counters_enable(True)
+    try:
+        for crit in (native.FF, native.BF, native.WF, native.RANDOM):
+            native.counters_read(reset=True)
+            assert native.pack_batch(db, out, 2, crit, 5, seed=3) == 0
+            got = native.counters_read(reset=True)
+            want = sum(oracle.fit_tests(*b.instance(i), 2, crit, 5, 0, 3) for i in range(b.N))
+            assert got["fit_tests"] == want, crit
+    finally:
+        native.counters_enable(False)
+
+
+def test_kernel_timing_hook():
+    """One event-timed duration per uncaptured batched call, none for plan
+    replays (captured launches) and none while disabled."""
+    b = I.config3(N=30, m_hi=2000, seed=23)
+    db = native.DeviceBatch.from_host(b)
+    out = native.DeviceResult.empty(db.N, db.total_items)
+    native.kernel_timing_enable(True)
+    try:
+        for (h, c, s) in ((1, native.BF, 0), (2, native.BF, 5), (1, native.FF, 0)):
+            assert native.pack_batch(db, out, h, c, s) == 0
+        t = native.kernel_timing_read()
+        assert len(t) == 3 and all(x > 0 for x in t)
+        assert native.kernel_timing_read() == []
+        pl = native.Plan(db.N, db.total_items, db.max_m, 1, native.BF, 0)
+        try:
+            pl.run(db, out)
+            pl.run(db, out)
+        finally:
+            pl.close()
+        assert len(native.kernel_timing_read()) <= 1     # at most the call made while recording
+    finally:
+        native.kernel_timing_enable(False)
+    assert native.pack_batch(db, out, 1, native.BF, 0) == 0
+    assert native.kernel_timing_read() == []

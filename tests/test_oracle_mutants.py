@@ -56,6 +56,7 @@ MUTANTS = {
     "opt_largest_capacity": ("for (int32_t i = n - 1; i >= 0; --i) {  /* smallest capacity first */",
                              "for (int32_t i = 0; i < n; ++i) {"),
     "total_counts_loads": ("sum += B[bins[x].type];", "sum += bins[x].load;"),
+    "fit_tests_off_by_one": ("or_fit_tests += (uint64_t)nb;", "or_fit_tests += (uint64_t)nb + 1;"),
 }
 
 
