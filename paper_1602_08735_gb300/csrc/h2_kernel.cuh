@@ -203,12 +203,13 @@ __device__ __forceinline__ void h2_decode(int rank, int k, int (&perm)[S]) {
 // bin's slot is known at compile time; a slot never created reads as an
 // empty word that never fits and is never used.
 //
-// Capacities <= 4095 (narrow): one word per slot, v = (residual << 16) |
-// (slot << 12) | capacity, so each selection is one operation pair per slot
-//   FF  the lowest fitting slot (v >= w << 16),
-//   BF  min(v - (w << 16)): a slot that does not fit wraps above 2^31,
-//   WF  min(v ^ 0xFFFF0000): the largest residual, then the lowest slot,
-// and the chosen word carries the bin's residual, slot and capacity.
+// Capacities <= 2047 and n <= 16 (narrow): one word per slot, v =
+// (residual << 20) | (slot << 16) | (type << 12) | capacity, so each
+// selection is one operation pair per slot
+//   FF  the lowest fitting slot (v >= w << 20),
+//   BF  min(v - (w << 20)): a slot that does not fit wraps above 2^31,
+//   WF  min(v ^ 0xFFF00000): the largest residual, then the lowest slot,
+// and the chosen word carries the bin's residual, slot, type and capacity.
 // Larger capacities (wide): residual and capacity words per slot, 64-bit
 // selection keys.
 // Permutations are packed 3 bits per position, one table per sublist
@@ -237,8 +238,6 @@ __device__ __forceinline__ uint32_t h2_min_tree(uint32_t (&t)[N], int cnt) {
 // Pack one permutation, narrow slot words.  Returns the used capacity (a
 // bin's capacity counts from the item that finds it empty); rawp gets the
 // slot of the item at step q in bits 4q..4q+3.  K > 0: exactly K items
-// (compile time); K = 0: k items.  COUNT: fit gets the fit tests of the
-// method (bins alive when each item arrives).
 // Item steps Q0 .. Q1-1 of one permutation, narrow slot words (running
 // state: slots v, slot per step rawp, used capacity tot; with COUNT, fit
 // tests fit and bins alive).  K > 0: exactly K items (compile time); K = 0:
@@ -253,8 +252,9 @@ __device__ __forceinline__ void h2_steps_narrow(uint32_t perm, int k, const uint
     for (int q = Q0; q < Q1; ++q) {
         if (K > 0 ? q < K : q < k) {
             const uint32_t it = (perm >> (3 * q)) & 7u;
-            const uint32_t wq = wsub[it], bn = bnew[it];
-            const uint32_t W = wq << 16;
+            const uint32_t wq = wsub[it], bnp = bnew[it];     // bnp = new bin's (type << 12) | capacity
+            const uint32_t bn = bnp & 0xFFFu;
+            const uint32_t W = wq << 20;
             const int c = CRIT == kRandom
                               ? pick_criterion(kRandom, seed, static_cast<uint64_t>((g * 720 + rank) * 8 + q))
                               : CRIT;
@@ -275,13 +275,14 @@ __device__ __forceinline__ void h2_steps_narrow(uint32_t perm, int k, const uint
             } else {
                 uint32_t t[kSlots];
 #pragma unroll
-                for (int x = 0; x < 2 * q; ++x) t[x] = v[x] ^ 0xFFFF0000u;
-                best = h2_min_tree<kSlots>(t, 2 * q) ^ 0xFFFF0000u;
-                hit = (best >> 16) >= wq;
+                for (int x = 0; x < 2 * q; ++x) t[x] = v[x] ^ 0xFFF00000u;
+                best = h2_min_tree<kSlots>(t, 2 * q) ^ 0xFFF00000u;
+                hit = (best >> 20) >= wq;
             }
-            const uint32_t xs = hit ? (best >> 12) & 15u : static_cast<uint32_t>(2 * q);
-            const uint32_t r_old = hit ? best >> 16 : bn;
-            const uint32_t cap = hit ? best & 0xFFFu : bn;
+            const uint32_t xs = hit ? (best >> 16) & 15u : static_cast<uint32_t>(2 * q);
+            const uint32_t r_old = hit ? best >> 20 : bn;
+            const uint32_t tc = hit ? best & 0xFFFFu : bnp;    // (type << 12) | capacity
+            const uint32_t cap = tc & 0xFFFu;
             const uint32_t r_new = r_old - wq;
             const bool fire = (cap < 2u * r_old) && (2u * r_new <= cap);     // Rule 5
             tot += r_old == cap ? cap : 0u;        // the bin's first item: it becomes used
@@ -291,8 +292,8 @@ __device__ __forceinline__ void h2_steps_narrow(uint32_t perm, int k, const uint
             }
 #pragma unroll
             for (int x = 0; x < 2 * q; ++x) v[x] = xs == static_cast<uint32_t>(x) ? v[x] - W : v[x];
-            v[2 * q] = hit ? 0u : (r_new << 16) | (static_cast<uint32_t>(2 * q) << 12) | cap;
-            v[2 * q + 1] = fire ? (cap << 16) | (static_cast<uint32_t>(2 * q + 1) << 12) | cap : 0u;
+            v[2 * q] = hit ? 0u : (r_new << 20) | (static_cast<uint32_t>(2 * q) << 16) | tc;
+            v[2 * q + 1] = fire ? (cap << 20) | (static_cast<uint32_t>(2 * q + 1) << 16) | tc : 0u;
             rawp |= xs << (4 * q);
         }
     }
@@ -371,17 +372,14 @@ __device__ __forceinline__ uint64_t h2_pack_wide(uint32_t perm, int k, const uin
 // The winner's result in sublist-local form: used slots (load > 0) get
 // dense ids in slot order (= creation order).
 template <int S>
-__device__ __forceinline__ void h2_write_winner(const H2Params& p, const uint32_t (&cap)[2 * S],
+__device__ __forceinline__ void h2_write_winner(const H2Params& p, const uint32_t (&typ)[2 * S],
                                                 uint32_t used, uint32_t rawp, uint32_t perm, int k,
-                                                const uint32_t* Bs, int n, int64_t uid, int64_t base,
-                                                uint64_t total) {
+                                                int64_t uid, int64_t base, uint64_t total) {
     int cnt = 0;
 #pragma unroll
     for (int x = 0; x < 2 * S; ++x) {
         if ((used >> x) & 1u) {
-            int t = 0;
-            for (int y = 0; y < n; ++y) t = Bs[y] == cap[x] ? y : t;
-            p.out.local_types[base + cnt] = t;
+            p.out.local_types[base + cnt] = static_cast<int32_t>(typ[x]);
             ++cnt;
         }
     }
@@ -447,18 +445,19 @@ __global__ void __launch_bounds__(128) h2_pack_kernel_reg(const H2Params p) {
             const int64_t a1 = (seg_end - ub) * S < m ? (seg_end - ub) * S : m;
             const int cnt = static_cast<int>(a1 - a0);
             if (tid < kMaxTypes) Bs[tid] = tid < n ? static_cast<uint32_t>(B[tid]) : 0u;
+            const bool narrow = static_cast<uint32_t>(B[0]) <= 2047u && n <= 16;
             for (int t = tid; t < cnt; t += blockDim.x) {
                 const uint32_t x = static_cast<uint32_t>(p.in.w_all[wb + a0 + t]);
-                uint32_t bn = 0;
+                uint32_t bn = 0, tn = 0;                   // smallest type holding x
                 for (int y = 0; y < n; ++y) {
                     const uint32_t c = static_cast<uint32_t>(B[y]);
+                    tn = c >= x ? static_cast<uint32_t>(y) : tn;
                     bn = c >= x ? c : bn;
                 }
                 wrun[t] = x;
-                brun[t] = bn;
+                brun[t] = narrow ? (tn << 12) | bn : bn;
             }
             __syncthreads();
-            const bool narrow = static_cast<uint32_t>(B[0]) <= 4095u;
             for (int64_t u = uid + warp; u < seg_end; u += kWarps) {
                 const int64_t g = u - ub;
                 const int64_t a = g * S;
@@ -542,13 +541,13 @@ __global__ void __launch_bounds__(128) h2_pack_kernel_reg(const H2Params p) {
                     if (p.counters && lane == 0) atomicAdd(p.counters, static_cast<unsigned long long>(k));
                     const uint32_t wkey = __reduce_min_sync(kFull, bestkey);
                     if (bestkey == wkey) {
-                        uint32_t used = 0, capx[kSlots];
+                        uint32_t used = 0, typx[kSlots];
 #pragma unroll
                         for (int x = 0; x < kSlots; ++x) {
-                            capx[x] = bv[x] & 0xFFFu;
-                            used |= ((bv[x] >> 16) < capx[x] ? 1u : 0u) << x;
+                            typx[x] = (bv[x] >> 12) & 15u;
+                            used |= ((bv[x] >> 20) < (bv[x] & 0xFFFu) ? 1u : 0u) << x;
                         }
-                        h2_write_winner<S>(p, capx, used, brawp, bperm, k, Bs, n, u, wb + a, wkey >> 10);
+                        h2_write_winner<S>(p, typx, used, brawp, bperm, k, u, wb + a, wkey >> 10);
                     }
                 } else {
                     uint64_t bestkey = ~0ull;
@@ -579,10 +578,15 @@ __global__ void __launch_bounds__(128) h2_pack_kernel_reg(const H2Params p) {
                     if (p.counters && lane == 0) atomicAdd(p.counters, static_cast<unsigned long long>(k));
                     const uint64_t wkey = warp_min_u64(bestkey);
                     if (bestkey == wkey) {
-                        uint32_t used = 0;
+                        uint32_t used = 0, typx[kSlots];
 #pragma unroll
-                        for (int x = 0; x < kSlots; ++x) used |= (br[x] < bc[x] ? 1u : 0u) << x;
-                        h2_write_winner<S>(p, bc, used, brawp, bperm, k, Bs, n, u, wb + a, wkey >> 10);
+                        for (int x = 0; x < kSlots; ++x) {
+                            used |= (br[x] < bc[x] ? 1u : 0u) << x;
+                            uint32_t t = 0;
+                            for (int y = 0; y < n; ++y) t = Bs[y] == bc[x] ? static_cast<uint32_t>(y) : t;
+                            typx[x] = t;
+                        }
+                        h2_write_winner<S>(p, typx, used, brawp, bperm, k, u, wb + a, wkey >> 10);
                     }
                 }
             }

@@ -227,3 +227,19 @@ def test_spill_and_rerun(pct):
                         f"spill plain {pct} c{crit}")
     finally:
         native.set_config(**saved)
+
+
+def test_second_heuristic_slot_forms():
+    """The second heuristic's one-word slots hold capacities up to 2047 and
+    16 types; B_1 = 2048 or a 17th type takes the wide slots.  Both sides of
+    each boundary against the oracle, every criterion, sublists of 4-6."""
+    rng = np.random.default_rng(61)
+    def inst(B1, n, m):
+        B = np.sort(rng.choice(np.arange(1, B1), size=n - 1, replace=False))[::-1]
+        B = np.concatenate([[B1], B]).astype(np.int32)
+        return rng.integers(1, B1 + 1, size=m).astype(np.int32), B
+    b = I.from_instances([inst(2047, 5, 97), inst(2048, 5, 101), inst(900, 16, 64), inst(900, 17, 66),
+                          inst(2047, 16, 40), inst(3000, 32, 55)])
+    for s in (4, 5, 6):
+        for crit in H1_CRITERIA:
+            assert_same(b, run_batch(b, 2, crit, s, seed=8), run_oracle(b, 2, crit, s, seed=8), f"s={s} c{crit}")
