@@ -149,8 +149,15 @@ __global__ void __launch_bounds__(32) kc_pack_kernel(const KCParams p) {
             for (int t = 0; t < n; ++t) W.append(L++, static_cast<uint32_t>(B[t]), static_cast<uint32_t>(t));
         }
         unsigned long long fit_tests = 0;
+        // weights a 32-item block ahead (lane l holds item block + l); each
+        // item's weight is a shuffle off the dependent chain, and the items'
+        // bins are written once per block
+        uint32_t wcur = lane < m ? static_cast<uint32_t>(__ldg(w + lane)) : 0u;
+        uint32_t wnext = 32 + lane < m ? static_cast<uint32_t>(__ldg(w + 32 + lane)) : 0u;
+        uint32_t bout = 0;
         for (int64_t j = 0; j < m; ++j) {
-            const uint32_t wj = static_cast<uint32_t>(w[j]);
+            const int jj = static_cast<int>(j & 31);
+            const uint32_t wj = __shfl_sync(kFull, wcur, jj);
             const int c = pick_criterion(p.criterion, p.seed, static_cast<uint64_t>(j));
             fit_tests += L;
             const uint32_t ntiles = (L + kTileBins - 1) / kTileBins;
@@ -283,7 +290,12 @@ __global__ void __launch_bounds__(32) kc_pack_kernel(const KCParams p) {
                 W.append(L, Bt, t);
                 ++L;
             }
-            if (lane == 0) raw[j] = static_cast<int32_t>(b);
+            bout = lane == jj ? b : bout;
+            if (jj == 31 || j + 1 == m) {
+                if (lane <= jj) raw[j - jj + lane] = static_cast<int32_t>(bout);
+                wcur = wnext;
+                wnext = j + 33 + lane < m ? static_cast<uint32_t>(__ldg(w + j + 33 + lane)) : 0u;
+            }
         }
 
         // --- objective and dense ids (used bins in creation order)
