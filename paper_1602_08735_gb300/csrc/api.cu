@@ -142,6 +142,7 @@ struct Scratch {
 
     uint32_t* kc_slots = nullptr; int64_t cap_kc_slots = 0;   // global-memory bins
     int32_t* spill_list = nullptr; int64_t cap_spill_list = 0;  // systems to repack at full size
+    int32_t* spill_list2 = nullptr; int64_t cap_spill_list2 = 0;  // ... and those beyond it (global memory)
 
     uint32_t* hist() const { return reinterpret_cast<uint32_t*>(fixed); }
     int64_t* cursor() const { return reinterpret_cast<int64_t*>(fixed + kClasses * kBuckets * 4); }
@@ -169,6 +170,7 @@ struct Scratch {
         cudaFree(cls); cudaFree(order); cudaFree(nu); cudaFree(unit_base); cudaFree(unit_count);
         cudaFree(unit_total); cudaFree(local_types); cudaFree(fixed); cudaFree(kc_slots);
         cudaFree(spill_list);
+        cudaFree(spill_list2);
         cudaFree(h_w); cudaFree(h_B); cudaFree(h_boi); cudaFree(h_bt); cudaFree(h_small);
         *this = Scratch();
     }
@@ -244,10 +246,25 @@ int64_t cap_for_budget(int budget, bool wide, int chunk, int G, int bf_index) {
 // cap_m = the largest system whose worst case (2m + 32 slots) the shape could
 // hold; slot_cap = pct% of that plus 64 (never above the worst case).
 int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int chunk, int smem_max,
-               int sms, int64_t hard_cap, int pct, int bf_index, int criterion) {
+               int sms, int64_t hard_cap, int pct, int bf_index, int criterion, bool spills = false) {
     sh.chunk = chunk;
     sh.bf_index = bf_index;
     int64_t cap = std::min<int64_t>(want_m, cap_for_budget(smem_max / groups, wide, chunk, G, bf_index));
+    if (spills && !wide && G == 1) {
+        // The one-warp kernel spills a system that outgrows its slots (it is
+        // packed again by the worst-case shape, or in global memory), so its
+        // reach is set by the pct estimate rather than the worst case.
+        int64_t lo = cap, hi = want_m + 1;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) / 2;
+            const int64_t sc = round128(mid * pct / 100 + 64);
+            const bool fits = h1w_supported(static_cast<int>(std::min<int64_t>(sc, 1 << 30))) &&
+                              group_bytes(false, 1, static_cast<int>(sc), chunk, bf_index) <=
+                                                         smem_max / groups;
+            if (fits) lo = mid; else hi = mid;
+        }
+        cap = lo;
+    }
     cap = std::min<int64_t>(cap, hard_cap);
     cap = std::max<int64_t>(cap, 1);
     sh.G = G;
@@ -344,12 +361,12 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
     int rc = make_shape(lp.full, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752, 200, bfi,
                         prm.criterion);
     if (rc != VSBPP_OK) return rc;
-    rc = make_shape(lp.large, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752,
-                    lp.cfg.slot_pct, bfi, prm.criterion);
+    rc = make_shape(lp.large, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30,
+                    lp.cfg.slot_pct, bfi, prm.criterion, true);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.small, false, 1, lp.cfg.small_warps_per_block,
                     std::min<int64_t>(max_m, std::max(1, lp.cfg.small_m)), std::min(chunk, 256), smax,
-                    di.sms, 32752, lp.cfg.slot_pct, bfi, prm.criterion);
+                    di.sms, 32752, lp.cfg.slot_pct, bfi, prm.criterion, true);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.wide, true, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30, 200, bfi,
                     prm.criterion);
@@ -358,7 +375,9 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
     cap_grid(lp.small, N);
     cap_grid(lp.wide, N);
     cap_grid(lp.full, N);
-    if (max_m > lp.large.cap_m) {
+    // global memory for systems beyond the shared-memory classes, and for
+    // those that outgrow even the worst-case shape after a spill
+    if (max_m > std::min(lp.large.cap_m, lp.full.cap_m)) {
         KCShape& kc = lp.kc;
         kc.enabled = true;
         const int64_t want_bins = std::min<int64_t>(2 * max_m + kMaxTypes, int64_t(kMaxTiles) * kTileBins);
@@ -385,6 +404,7 @@ int ensure_scratch(Scratch& sc, const LaunchPlan& lp, int64_t N, int64_t total_m
     if (!lp.mode.compose) {
         if ((rc = grow(sc.order, sc.cap_order, N))) return rc;
         if ((rc = grow(sc.spill_list, sc.cap_spill_list, N))) return rc;
+        if ((rc = grow(sc.spill_list2, sc.cap_spill_list2, N))) return rc;
         if (lp.kc.enabled && (rc = grow(sc.kc_slots, sc.cap_kc_slots, int64_t(lp.kc.grid) * lp.kc.bin_cap)))
             return rc;
         return VSBPP_OK;
@@ -438,7 +458,8 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
     if (!lp.mode.compose) {
         pp.classify = 1;
         pp.small_m = plain ? 0 : lp.cfg.small_m;      // plain path: no single-warp class
-        pp.narrow_cap = lp.full.cap_m;
+        pp.narrow_cap = lp.large.cap_m;
+        pp.narrow_bins = lp.large.warp_kernel ? (int64_t(1) << 40) : 65536;   // one-warp shapes spill instead
         pp.small_cap = lp.small.cap_m;
         pp.wide_cap = lp.wide.cap_m;
         pp.huge_cap = lp.kc.enabled ? lp.kc.cap_m : 0;
@@ -479,12 +500,15 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
             timing_end(timed, st);
         }
         {
-            // systems that outgrew their slots, repacked from the start at full size
+            // systems that outgrew their slots, repacked from the start at full
+            // size; a system that outgrows that too is listed for global memory
             H1Params p = h1_params(in, out, prm, lp.full);
             p.order = sc.spill_list;
             p.seg = sc.spill_seg();
             p.segment = 0;
             p.queue = sc.queue() + kClasses;
+            p.spill_list = sc.spill_list2;
+            p.spill_seg = sc.spill_seg() + 2;
             VS_TRY(launch_shape(lp.full, false, p, 1, lp.full.grid, st));
         }
         if (lp.kc.enabled) {
@@ -504,6 +528,12 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
             kp.max_B1 = lp.kc.max_B1;
             kp.pres_words = lp.kc.pres_words;
             kp.counters = g_counters;
+            VS_TRY(kc_launch(kp, lp.kc.grid, lp.kc.smem, st));
+            // systems that outgrew the worst-case shared-memory shape
+            kp.order = sc.spill_list2;
+            kp.seg = sc.spill_seg() + 2;
+            kp.segment = 0;
+            kp.queue = sc.queue() + kClasses + 1;
             VS_TRY(kc_launch(kp, lp.kc.grid, lp.kc.smem, st));
         }
         return VSBPP_OK;

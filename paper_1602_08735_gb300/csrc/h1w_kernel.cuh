@@ -158,8 +158,13 @@ struct H1Warp {
         for (uint32_t j0 = 0; j0 < k; j0 += 32u) {
             const uint32_t cnt = min(32u, k - j0);
             // an item adds at most two bins: stop before the block could
-            // outgrow the slots (a worst-case-sized launch repacks the system)
-            if (p.spill_list && L + 2u * cnt > cap_bins) {
+            // outgrow the slots (a larger shape, or global memory, repacks the
+            // system from the start); after 2048 items also stop when the
+            // bins so far, extrapolated to all k items, pass 9/8 of the slots
+            const bool trend = j0 >= 2048u &&
+                               static_cast<uint64_t>(L) * k >
+                                   static_cast<uint64_t>(cap_bins) * j0 + ((static_cast<uint64_t>(cap_bins) * j0) >> 3);
+            if (p.spill_list && (L + 2u * cnt > cap_bins || trend)) {
                 if (lane == 0) {
                     const unsigned long long pos = atomicAdd(
                         reinterpret_cast<unsigned long long*>(p.spill_seg + 1), 1ull);

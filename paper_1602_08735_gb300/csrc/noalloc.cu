@@ -116,6 +116,7 @@ extern "C" int vsbpp_pack_batch_noalloc(int64_t N, const int32_t* w_all, const i
     pp.classify = 1;
     pp.small_m = 0;
     pp.narrow_cap = cap_m;
+    pp.narrow_bins = 65536;
     pp.small_cap = 0;
     pp.wide_cap = 0;
     pp.huge_cap = 0;

@@ -68,9 +68,9 @@ __global__ void validate_kernel(const PrepParams p) {
         int c = kClassNone;
         if (code == VSBPP_OK && m > 0 && p.classify) {
             const int64_t bins = 2 * m + (p.preopen ? n : 0);
-            if (B1 <= p.narrow_max_B && m <= p.small_m && m <= p.small_cap && bins <= 65536) {
+            if (B1 <= p.narrow_max_B && m <= p.small_m && m <= p.small_cap && bins <= p.narrow_bins) {
                 c = kClassSmall;
-            } else if (B1 <= p.narrow_max_B && m <= p.narrow_cap && bins <= 65536) {
+            } else if (B1 <= p.narrow_max_B && m <= p.narrow_cap && bins <= p.narrow_bins) {
                 c = kClassLarge;
             } else if (m <= p.wide_cap) {
                 c = kClassWide;
@@ -121,8 +121,8 @@ __global__ void order_kernel(uint32_t* hist, int64_t* cursor, int64_t* seg,
         for (int c = 0; c < kClasses; ++c) seg[c] = base[c];
         seg[kClasses] = run;
     }
-    if (lane <= kClasses) queue[lane] = 0ull;
-    if (spill_seg && lane < 2) spill_seg[lane] = 0;
+    if (lane <= kClasses + 1) queue[lane] = 0ull;
+    if (spill_seg && lane < 4) spill_seg[lane] = 0;
 }
 
 __global__ void scatter_kernel(BatchView in, const int32_t* cls, int64_t* cursor, int32_t* order) {

@@ -107,3 +107,23 @@ def test_many_warps_per_block(wpb):
             assert_same(b, run_batch(b, 1, c, seed=6), run_oracle(b, 1, c, seed=6), f"wpb {wpb} c{c}")
     finally:
         native.set_config(**saved)
+
+
+def test_large_systems_routes():
+    """Systems past the worst-case shared-memory size: held by the one-warp
+    kernel when the slot estimate suffices (20k items of U[1,150]), spilled
+    twice and finished in global memory when it does not (30k items that
+    each fill half a bin: two bins per item), and in global memory from the
+    start beyond the estimate's reach (45k items).  Results equal the
+    oracle's whatever the route."""
+    rng = np.random.default_rng(71)
+    B = np.array([150, 120, 100, 80, 50], dtype=np.int32)
+    inst = [(rng.integers(1, 151, size=20_000).astype(np.int32), B),
+            (rng.integers(51, 101, size=30_000).astype(np.int32), np.array([100, 60], dtype=np.int32)),
+            (rng.integers(1, 151, size=45_000).astype(np.int32), B),
+            (rng.integers(1, 151, size=3_000).astype(np.int32), B)]
+    b = I.from_instances(inst)
+    for c in CRITS:
+        ref = run_oracle(b, 1, c, seed=7)
+        assert_same(b, run_batch(b, 1, c, seed=7), ref, f"routes c{c}")
+        assert_same(b, run_batch(b, 1, c, seed=7, plain=True), ref, f"routes plain c{c}")
