@@ -57,7 +57,7 @@ extern "C" {
 
 #define VSBPP_VERSION 10000          /* 1.0.0 */
 #define VSBPP_MAX_TYPES 32           /* bin types per instance */
-#define VSBPP_H2_MAX_SUBLIST 6       /* 6! = 720 permutations per sublist */
+#define VSBPP_H2_MAX_SUBLIST 12      /* s <= 6: Section 6.4 (s! <= 720); 7..12: exhaustive search */
 
 /* Selection criterion of Rule 3 / Rule 4 (Section 1 defines FF, BF, WF). */
 typedef enum {
@@ -80,7 +80,10 @@ typedef struct {
     int32_t  heuristic;     /* VSBPP_H1 or VSBPP_H2                                     */
     int32_t  criterion;     /* vsbpp_criterion                                          */
     int64_t  sublist_size;  /* Rule 1 sublist length s.  H1: 0 means s = m (one membrane
-                               system per instance).  H2: 0 means 5; at most 6.  The
+                               system per instance).  H2: 0 means 5; at most 12 (s <= 6
+                               is Section 6.4's block per sublist; 7..12 runs every one
+                               of the s! permutations across the whole GPU, the
+                               exhaustive search Section 7 compares against).  The
                                list is cut into contiguous chunks of s items in order.   */
     int32_t  preopen;       /* 0: no bin open at the start (a bin opens when nothing
                                fits).  1: literal Rule 2, one empty bin of every type,

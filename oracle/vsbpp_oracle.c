@@ -43,7 +43,9 @@
  *   G10 ties between permutations go to the lowest rank;
  *   G12 the RANDOM criterion draws c = SplitMix64(seed, key) mod 3 with
  *       0=FF, 1=BF, 2=WF; key = item index (first heuristic) or
- *       (sublist*720 + rank)*8 + step (second heuristic).  SplitMix64 is the
+ *       (sublist*720 + rank)*8 + step (second heuristic, s <= 6), or
+ *       (sublist*12! + rank)*16 + step (s = 7..12, the exhaustive search of
+ *       Section 7's parallel comparison).  SplitMix64 is the
  *       published generator of Steele, Lea & Flood (OOPSLA 2014): the
  *       key-th output (0-based) of the stream seeded with `seed`.
  */
@@ -66,7 +68,8 @@
 #define OR_H2 2
 
 #define OR_H2_DEFAULT_SUBLIST 5
-#define OR_H2_MAX_SUBLIST 6
+#define OR_H2_MAX_SUBLIST 12   /* s <= 6: Section 6.4; up to 12: Section 7's exhaustive search */
+#define OR_FACT12 479001600ull
 
 /* Fit tests of Rule 4 performed by this thread's calls: for every item, one
  * per bin membrane alive when it arrives (summed over every permutation the
@@ -315,7 +318,9 @@ int oracle_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
                     seq[q] = w[a + perm[q]];
                     crit[q] = criterion == OR_RANDOM
                                   ? or_random_criterion(
-                                        seed, (uint64_t)((g * 720 + rank) * 8 + q))
+                                        seed, s <= 6
+                                                  ? (uint64_t)((g * 720 + rank) * 8 + q)
+                                                  : ((uint64_t)g * OR_FACT12 + (uint64_t)rank) * 16u + (uint64_t)q)
                                   : criterion;
                 }
                 const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw);
