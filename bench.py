@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -221,6 +222,30 @@ def config4_pass(native, I, dev, stream, N, m=1_000_000):
     plan.close()
     return {"instances": db.N, "items": db.total_items, "pass": "H1-BF", "ms": ms,
             "items_per_s": db.total_items / (ms / 1e3), "instances_ok": ok}
+
+
+def exhaustive_search(native, I, dev, stream):
+    """The exhaustive second heuristic (Section 7's comparison): one list of
+    10 and one of 12 items, every permutation packed (BF)."""
+    import torch
+    rng = np.random.default_rng(12)
+    res = {}
+    for m in (10, 12):
+        b = I.from_instances([I.random_instance(rng, m, 5, 150)])
+        db = native.DeviceBatch.from_host(b, device=dev)
+        out = native.DeviceResult.empty(db.N, db.total_items, device=dev)
+        assert native.pack_batch(db, out, 2, 1, m, stream=stream) == 0
+        e0, e1 = _events(torch)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        assert native.pack_batch(db, out, 2, 1, m, stream=stream) == 0
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        perms = math.factorial(m)
+        res[f"m{m}"] = {"ms": ms, "permutations": perms, "permutations_per_s": perms / (ms / 1e3),
+                        "total": int(out.total[0].item())}
+    return res
 
 
 def serving_run(native, I, rate, n_req):
@@ -546,6 +571,7 @@ def run_ours(args, ws, rank, local):
         side["single_instance"] = single_instance_latency(native, I, dev, stream)
         side["config4"] = config4_pass(native, I, dev, stream, args.config4_instances, args.config4_m)
         side["serving"] = serving_run(native, I, args.serve_rate, args.serve_requests)
+        side["exhaustive"] = exhaustive_search(native, I, dev, stream)
 
     if rank == 0:
         line = {

@@ -83,7 +83,8 @@ typedef struct {
                                system per instance).  H2: 0 means 5; at most 12 (s <= 6
                                is Section 6.4's block per sublist; 7..12 runs every one
                                of the s! permutations across the whole GPU, the
-                               exhaustive search Section 7 compares against).  The
+                               exhaustive search Section 7 compares against, and
+                               requires preopen = 0, else EINVAL).  The
                                list is cut into contiguous chunks of s items in order.   */
     int32_t  preopen;       /* 0: no bin open at the start (a bin opens when nothing
                                fits).  1: literal Rule 2, one empty bin of every type,

@@ -143,6 +143,7 @@ struct Scratch {
     uint32_t* kc_slots = nullptr; int64_t cap_kc_slots = 0;   // global-memory bins
     int32_t* spill_list = nullptr; int64_t cap_spill_list = 0;  // systems to repack at full size
     int32_t* spill_list2 = nullptr; int64_t cap_spill_list2 = 0;  // ... and those beyond it (global memory)
+    unsigned long long* h2x_best = nullptr; int64_t cap_h2x_best = 0;  // exhaustive search: best key per sublist
 
     uint32_t* hist() const { return reinterpret_cast<uint32_t*>(fixed); }
     int64_t* cursor() const { return reinterpret_cast<int64_t*>(fixed + kClasses * kBuckets * 4); }
@@ -171,6 +172,7 @@ struct Scratch {
         cudaFree(unit_total); cudaFree(local_types); cudaFree(fixed); cudaFree(kc_slots);
         cudaFree(spill_list);
         cudaFree(spill_list2);
+        cudaFree(h2x_best);
         cudaFree(h_w); cudaFree(h_B); cudaFree(h_boi); cudaFree(h_bt); cudaFree(h_small);
         *this = Scratch();
     }
@@ -217,6 +219,7 @@ struct LaunchPlan {
     H1Shape full{};       // worst-case slots: repacks systems that outgrew large/small
     KCShape kc{};
     int h2_threads = 0, h2_smem = 0, h2_grid = 0, h2_max_bins = 0;
+    bool h2x = false;     // sublists of 7..12 items: the exhaustive search
     int prep_grid = 0;
 };
 
@@ -325,6 +328,16 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
     if (prm.heuristic == VSBPP_H2) {
         const int s = static_cast<int>(prm.sublist_size == 0 ? 5 : prm.sublist_size);
         lp.mode = {VSBPP_H2, 1, s};
+        if (s >= 7) {
+            // s! permutations per sublist searched across the GPU (no
+            // pre-opened bins on this path)
+            if (prm.preopen) return VSBPP_EINVAL;
+            lp.h2x = true;
+            const int occ = h2x_blocks_per_sm(s, prm.criterion);
+            if (occ <= 0) return record(cudaErrorInvalidConfiguration);
+            lp.h2_grid = occ * di.sms;
+            return VSBPP_OK;
+        }
         int f = 1;
         for (int x = 2; x <= s; ++x) f *= x;
         // literal Rule 2 start: one thread per permutation (shared-memory
@@ -413,6 +426,7 @@ int ensure_scratch(Scratch& sc, const LaunchPlan& lp, int64_t N, int64_t total_m
     if ((rc = grow(sc.nu, sc.cap_nu, N))) return rc;
     if ((rc = grow(sc.unit_base, sc.cap_unit_base, N + 1))) return rc;
     if ((rc = grow(sc.unit_count, sc.cap_unit_count, U))) return rc;
+    if (lp.h2x && (rc = grow(sc.h2x_best, sc.cap_h2x_best, U))) return rc;
     if ((rc = grow(sc.unit_total, sc.cap_unit_total, U))) return rc;
     if ((rc = grow(sc.local_types, sc.cap_local_types, total_m))) return rc;
     return VSBPP_OK;
@@ -557,9 +571,30 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
     cp.sublist = lp.mode.s;
     cp.only_instance = -1;
     const int64_t instances = plain ? in.N : 1;
+    if (lp.h2x)      // exhaustive search: every best key starts above every key
+        VS_TRY(cudaMemsetAsync(sc.h2x_best, 0xFF, sizeof(unsigned long long) * sc.cap_h2x_best, st));
     for (int64_t it = 0; it < instances; ++it) {
         const int64_t only = plain ? it : -1;
-        if (lp.mode.heuristic == VSBPP_H2) {
+        if (lp.mode.heuristic == VSBPP_H2 && lp.h2x) {
+            H2XParams xp;
+            std::memset(&xp, 0, sizeof(xp));
+            xp.in = in;
+            xp.out = out;
+            xp.units.unit_base = sc.unit_base;
+            xp.units.sublist = lp.mode.s;
+            xp.criterion = prm.criterion;
+            xp.sublist = static_cast<int32_t>(lp.mode.s);
+            xp.seed = prm.seed;
+            xp.seg_units = sc.seg_units();
+            xp.best = sc.h2x_best;
+            xp.queue = sc.queue();
+            xp.counters = g_counters;
+            xp.only_instance = only;
+            VS_TRY(cudaMemsetAsync(sc.queue(), 0, sizeof(unsigned long long), st));     // task counter
+            const bool timed = !plain && timing_begin(st);
+            VS_TRY(h2x_launch(xp, plain ? 1 : lp.h2_grid, st));
+            timing_end(timed, st);
+        } else if (lp.mode.heuristic == VSBPP_H2) {
             H2Params hp;
             std::memset(&hp, 0, sizeof(hp));
             hp.in = in;

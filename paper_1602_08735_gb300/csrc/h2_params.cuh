@@ -20,6 +20,21 @@ struct H2Params {
     unsigned long long* counters;   // null, or {items, fit tests} to add to (register kernel)
 };
 
+// Exhaustive second heuristic (sublists of 7..12 items, h2x_kernel.cuh).
+struct H2XParams {
+    BatchView in;
+    OutView out;                    // compose-mode fields are used
+    UnitMap units;
+    int32_t criterion;
+    int32_t sublist;                // s (7..12)
+    uint64_t seed;
+    const int64_t* seg_units;       // [1] = number of sublists (device)
+    unsigned long long* best;       // per sublist: least (total << 29) | rank
+    unsigned long long* queue;      // task counter (zero at the start)
+    unsigned long long* counters;   // null, or {items, fit tests} to add to
+    int64_t only_instance;          // -1: every sublist; else that instance's
+};
+
 __host__ __device__ inline int h2_smem_bytes(int threads, int max_bins) {
     return max_bins * threads * 4      // residuals
          + max_bins * threads          // types

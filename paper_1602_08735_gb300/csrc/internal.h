@@ -37,6 +37,9 @@ cudaError_t kc_launch(const KCParams& p, int grid, int smem, cudaStream_t st);
 int kc_blocks_per_sm(int smem);
 
 cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaStream_t st);
+// Exhaustive second heuristic (sublists of 7..12 items): search, then write.
+cudaError_t h2x_launch(const H2XParams& p, int grid, cudaStream_t st);
+int h2x_blocks_per_sm(int sublist, int criterion);
 int h2_blocks_per_sm(int threads, int smem);
 int h2_blocks_per_sm_reg(int threads, int sublist, int criterion);   // register kernel (no preopen)
 

@@ -200,7 +200,8 @@ def test_errors():
     assert native.pack([99, 0], [50]).status == native.ETOOBIG
     assert native.pack([1], list(range(40, 7, -1))).status == native.EINVAL    # n = 33
     assert native.pack([1], [5], heuristic=3).status == native.EINVAL
-    assert native.pack([1], [5], heuristic=2, sublist_size=7).status == native.EINVAL
+    assert native.pack([1], [5], heuristic=2, sublist_size=13).status == native.EINVAL
+    assert native.pack([1] * 8, [5], heuristic=2, sublist_size=8, preopen=1).status == native.EINVAL
     # mixed batch: bad instances flagged, good ones packed
     b = I.from_instances([([1, 2, 3], [5]), ([0], [5]), ([6], [5]), ([4, 4], [5, 4]), ([1], [3, 3])])
     got = run_batch(b, 1, native.BF)
@@ -243,3 +244,27 @@ def test_second_heuristic_slot_forms():
     for s in (4, 5, 6):
         for crit in H1_CRITERIA:
             assert_same(b, run_batch(b, 2, crit, s, seed=8), run_oracle(b, 2, crit, s, seed=8), f"s={s} c{crit}")
+
+
+@pytest.mark.parametrize("s", [7, 8, 9])
+def test_exhaustive_second_heuristic(s):
+    """Sublists of 7..12 items: every permutation searched across the GPU
+    (Section 7's exhaustive comparison); equal to the oracle on several
+    sublists per instance, ragged last sublists, all criteria, both paths."""
+    rng = np.random.default_rng(80 + s)
+    inst = [I.random_instance(rng, int(m), int(rng.integers(1, 6)), 60) for m in (s, 2 * s + 3, 3 * s - 1, 5)]
+    inst.append((rng.integers(1, 5001, size=s + 2).astype(np.int32), np.array([5000, 3000, 900], dtype=np.int32)))
+    b = I.from_instances(inst)
+    for crit in H1_CRITERIA:
+        ref = run_oracle(b, 2, crit, s, seed=4)
+        assert_same(b, run_batch(b, 2, crit, s, seed=4), ref, f"s={s} c{crit}")
+        assert_same(b, run_batch(b, 2, crit, s, seed=4, plain=True), ref, f"s={s} plain c{crit}")
+
+
+def test_exhaustive_ten_items():
+    """One 10-item list: all 3,628,800 permutations (the largest case Section
+    7 reports for its exhaustive implementations)."""
+    rng = np.random.default_rng(90)
+    b = I.from_instances([I.random_instance(rng, 10, 3, 100)])
+    for crit in (native.FF, native.BF, native.WF):
+        assert_same(b, run_batch(b, 2, crit, 10), run_oracle(b, 2, crit, 10), f"ten c{crit}")

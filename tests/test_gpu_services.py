@@ -167,7 +167,7 @@ def test_server_concurrent_submitters_and_errors():
         assert rc == native.EINVAL
 
 
-@pytest.mark.parametrize("h,s", [(1, 0), (1, 7), (2, 5), (2, 4), (2, 6)])
+@pytest.mark.parametrize("h,s", [(1, 0), (1, 7), (2, 5), (2, 4), (2, 6), (2, 7)])
 def test_counters_match_the_method_fit_tests(h, s):
     """The kernels' fit-test counters equal the oracle's count of Rule 4 fit
     tests (every bin alive when an item arrives; every permutation for the
