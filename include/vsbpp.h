@@ -304,6 +304,9 @@ typedef struct {
                                can create two bins).  A system that outgrows its slots is packed
                                again from the start by a worst-case-sized launch, so the result
                                never depends on this value (50..200)                           */
+    int32_t h2_blocks_per_sm; /* second heuristic: resident blocks per SM at most (0 = as many as
+                               fit; fewer leaves room for work running beside it on another
+                               stream, e.g. first-heuristic passes) (0..32)                    */
 } vsbpp_config;
 
 int vsbpp_get_config(vsbpp_config *out);

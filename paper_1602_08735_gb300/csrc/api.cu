@@ -92,6 +92,7 @@ vsbpp_config g_cfg = {
     /*small_warps_per_block=*/16,
     /*chunk=*/512,
     /*slot_pct=*/80,
+    /*h2_blocks_per_sm=*/0,
 };
 
 int record(cudaError_t e) {
@@ -345,8 +346,9 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         lp.h2_threads = prm.preopen ? std::max(32, (f + 31) / 32 * 32) : 128;
         lp.h2_max_bins = 2 * s + (prm.preopen ? kMaxTypes : 0);
         lp.h2_smem = h2_smem_bytes(lp.h2_threads, lp.h2_max_bins);
-        const int occ = prm.preopen ? h2_blocks_per_sm(lp.h2_threads, lp.h2_smem)
-                                    : h2_blocks_per_sm_reg(lp.h2_threads, s, prm.criterion);
+        int occ = prm.preopen ? h2_blocks_per_sm(lp.h2_threads, lp.h2_smem)
+                              : h2_blocks_per_sm_reg(lp.h2_threads, s, prm.criterion);
+        if (lp.cfg.h2_blocks_per_sm > 0) occ = std::min(occ, lp.cfg.h2_blocks_per_sm);
         if (occ <= 0) return record(cudaErrorInvalidConfiguration);
         lp.h2_grid = occ * di.sms;
         const int64_t units = N * ((max_m + s - 1) / s);
@@ -886,6 +888,7 @@ int vsbpp_set_config(const vsbpp_config* cfg) {
     if (cfg->small_m < 0 || cfg->chunk < 32 || cfg->chunk % 32 != 0 || cfg->chunk > 8192)
         return VSBPP_EINVAL;
     if (cfg->slot_pct < 50 || cfg->slot_pct > 200) return VSBPP_EINVAL;
+    if (cfg->h2_blocks_per_sm < 0 || cfg->h2_blocks_per_sm > 32) return VSBPP_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     g_cfg = *cfg;
     return VSBPP_OK;
@@ -1032,8 +1035,9 @@ int vsbpp_tune_save(const char* path) {
     if (!f) return VSBPP_EINVAL;
     std::fprintf(f,
                  "{\"large_warps\": %d, \"small_m\": %d, \"small_warps_per_block\": %d, \"chunk\": %d, "
-                 "\"slot_pct\": %d}\n",
-                 g_cfg.large_warps, g_cfg.small_m, g_cfg.small_warps_per_block, g_cfg.chunk, g_cfg.slot_pct);
+                 "\"slot_pct\": %d, \"h2_blocks_per_sm\": %d}\n",
+                 g_cfg.large_warps, g_cfg.small_m, g_cfg.small_warps_per_block, g_cfg.chunk, g_cfg.slot_pct,
+                 g_cfg.h2_blocks_per_sm);
     std::fclose(f);
     return VSBPP_OK;
 }
@@ -1047,11 +1051,13 @@ int vsbpp_tune_load(const char* path) {
     std::fclose(f);
     buf[n] = 0;
     vsbpp_config c = g_cfg;
-    const char* names[5] = {"\"large_warps\"", "\"small_m\"", "\"small_warps_per_block\"", "\"chunk\"",
-                            "\"slot_pct\""};
-    int* fields[5] = {&c.large_warps, &c.small_m, &c.small_warps_per_block, &c.chunk, &c.slot_pct};
-    for (int k = 0; k < 5; ++k) {
+    const char* names[6] = {"\"large_warps\"", "\"small_m\"", "\"small_warps_per_block\"", "\"chunk\"",
+                            "\"slot_pct\"", "\"h2_blocks_per_sm\""};
+    int* fields[6] = {&c.large_warps, &c.small_m, &c.small_warps_per_block, &c.chunk, &c.slot_pct,
+                      &c.h2_blocks_per_sm};
+    for (int k = 0; k < 6; ++k) {
         const char* q = std::strstr(buf, names[k]);
+        if (!q && k == 5) continue;            // files written before the field existed
         if (!q) return VSBPP_EINVAL;
         q = std::strchr(q, ':');
         if (!q) return VSBPP_EINVAL;

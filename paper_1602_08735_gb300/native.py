@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("large_warps", ctypes.c_int32), ("small_m", ctypes.c_int32),
                 ("small_warps_per_block", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("slot_pct", ctypes.c_int32)]
+                ("slot_pct", ctypes.c_int32), ("h2_blocks_per_sm", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
