@@ -252,7 +252,7 @@ def serving_run(native, I, rate, n_req):
     """Config 5: Poisson arrivals through the continuous-batching server."""
     reqs = I.config5(seed=5, num_requests=n_req, rate_per_s=rate)
     items = sum(len(w) for (_, w, _) in reqs)
-    with native.Server(device_mem_budget=8 << 30, max_slots=64, lanes=8) as srv:
+    with native.Server(device_mem_budget=8 << 30, max_slots=64, lanes=32) as srv:
         t0 = time.perf_counter()
         tickets = []
         for (t_arr, w, B) in reqs:

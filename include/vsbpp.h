@@ -170,9 +170,12 @@ int vsbpp_pack_device(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
  *
  * Instances are handed out largest first to resident thread groups through an
  * atomic queue (work stealing).  The first call for a given shape may
- * allocate scratch memory (cudaMalloc) and must not be made while `stream`
- * is being captured; vsbpp_plan_* below pre-allocates and records a CUDA
- * graph.  Returns a host-side status.
+ * allocate scratch memory and should not be made while `stream` is being
+ * captured; vsbpp_plan_* below pre-allocates and records a CUDA graph.
+ * Scratch belongs to the stream and grows with the stream-ordered allocator
+ * (cudaMallocFromPoolAsync / cudaFreeAsync on `stream`, from a library pool
+ * that keeps freed memory), so growing it never waits on other streams'
+ * work.  Returns a host-side status.
  */
 int vsbpp_pack_batch(int64_t N, const int32_t *w_all, const int64_t *w_off,
                      const int32_t *B_all, const int32_t *B_off, int64_t max_m,

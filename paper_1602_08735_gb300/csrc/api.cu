@@ -108,24 +108,52 @@ int record(cudaError_t e) {
         if (_rc != VSBPP_OK) return _rc;          \
     } while (0)
 
-template <typename T>
-int grow(T*& p, int64_t& cap, int64_t need) {
-    if (need <= cap && p) return VSBPP_OK;
-    int64_t n = std::max<int64_t>(need, 1);
-    n = std::max<int64_t>(n, cap + cap / 2);
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    void* q = nullptr;
-    const cudaError_t e = cudaMalloc(&q, static_cast<size_t>(n) * sizeof(T));
-    if (e != cudaSuccess) return record(e);
-    p = static_cast<T*>(q);
-    cap = n;
-    return VSBPP_OK;
+// The memory pool of stream-ordered scratch on the current device: memory a
+// stream frees is kept for reuse (no release threshold), and is handed to
+// another stream only once the free has completed, never by making that
+// stream wait on the freeing one.  Null where pools are unsupported.
+cudaMemPool_t scratch_pool() {
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPool_t pool = nullptr;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;
+    } else {
+        uint64_t keep = ~0ull;
+        int no = 0;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+    }
+    pools[dev] = pool;
+    return pool;
 }
 
 // Scratch owned by the library for one stream (or one plan).
+//
+// Scratch bound to a stream (the per-stream scratch of the batched and
+// single-instance calls) grows with the stream-ordered allocator on that
+// stream: freeing an outgrown buffer then waits only for that stream's earlier
+// work, where cudaFree would wait for the whole device, every other stream's
+// kernels included (a server packing on several streams would stall its
+// admissions behind its longest request).  Plan scratch (read by recorded
+// graphs), and buffers made while the stream is being captured, come from
+// cudaMalloc; an outgrown buffer met under capture is set aside and freed by
+// the next call made outside capture.
 struct Scratch {
+    bool ordered = false;            // grows in stream order on `ord`
+    cudaStream_t ord = nullptr;
+    std::vector<void*> sync_bufs;    // cudaMalloc buffers of an ordered scratch
+    std::vector<void*> retired;      // outgrown under capture, not yet freed
+
     int32_t* cls = nullptr;        int64_t cap_cls = 0;
     int32_t* order = nullptr;      int64_t cap_order = 0;
     int64_t* nu = nullptr;         int64_t cap_nu = 0;
@@ -154,14 +182,68 @@ struct Scratch {
     int64_t* spill_seg() const { return reinterpret_cast<int64_t*>(queue() + 8); }
     static size_t fixed_bytes() { return kClasses * kBuckets * 4 + kClasses * kBuckets * 8 + 32 * 8; }
 
+    bool stream_order() const {
+        if (!ordered) return false;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        return cudaStreamIsCapturing(ord, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    }
+    int alloc(void** q, size_t bytes) {
+        *q = nullptr;
+        if (stream_order()) {
+            cudaMemPool_t pool = scratch_pool();
+            return record(pool ? cudaMallocFromPoolAsync(q, bytes, pool, ord) : cudaMallocAsync(q, bytes, ord));
+        }
+        const cudaError_t e = cudaMalloc(q, bytes);
+        if (e == cudaSuccess && ordered) sync_bufs.push_back(*q);
+        return record(e);
+    }
+    // Frees now: in stream order for a stream-ordered buffer.
+    void free_buf(void* q) {
+        if (!q) return;
+        auto it = std::find(sync_bufs.begin(), sync_bufs.end(), q);
+        if (!ordered || it != sync_bufs.end()) {
+            if (it != sync_bufs.end()) sync_bufs.erase(it);
+            cudaFree(q);
+        } else {
+            cudaFreeAsync(q, ord);
+        }
+    }
+    // An outgrown buffer: freed now, or set aside while the stream is captured.
+    void drop(void* q) {
+        if (!q) return;
+        if (ordered && !stream_order()) retired.push_back(q);
+        else free_buf(q);
+    }
+    void free_retired() {
+        if (retired.empty() || !stream_order()) return;
+        for (void* q : retired) free_buf(q);
+        retired.clear();
+    }
+    template <typename T>
+    int grow(T*& p, int64_t& cap, int64_t need) {
+        if (need <= cap && p) return VSBPP_OK;
+        int64_t n = std::max<int64_t>(need, 1);
+        n = std::max<int64_t>(n, cap + cap / 2);
+        drop(p);
+        p = nullptr;
+        cap = 0;
+        void* q = nullptr;
+        const int rc = alloc(&q, static_cast<size_t>(n) * sizeof(T));
+        if (rc != VSBPP_OK) return rc;
+        p = static_cast<T*>(q);
+        cap = n;
+        return VSBPP_OK;
+    }
+
     int ensure_fixed() {
         if (fixed) return VSBPP_OK;
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, fixed_bytes());
-        if (e != cudaSuccess) return record(e);
-        e = cudaMemset(q, 0, fixed_bytes());
+        int rc = alloc(&q, fixed_bytes());
+        if (rc != VSBPP_OK) return rc;
+        const cudaError_t e = stream_order() ? cudaMemsetAsync(q, 0, fixed_bytes(), ord)
+                                             : cudaMemset(q, 0, fixed_bytes());
         if (e != cudaSuccess) {
-            cudaFree(q);
+            free_buf(q);
             return record(e);
         }
         fixed = static_cast<uint8_t*>(q);
@@ -169,12 +251,10 @@ struct Scratch {
     }
 
     void release() {
-        cudaFree(cls); cudaFree(order); cudaFree(nu); cudaFree(unit_base); cudaFree(unit_count);
-        cudaFree(unit_total); cudaFree(local_types); cudaFree(fixed); cudaFree(kc_slots);
-        cudaFree(spill_list);
-        cudaFree(spill_list2);
-        cudaFree(h2x_best);
-        cudaFree(h_w); cudaFree(h_B); cudaFree(h_boi); cudaFree(h_bt); cudaFree(h_small);
+        void* bufs[] = {cls, order, nu, unit_base, unit_count, unit_total, local_types, fixed, kc_slots,
+                        spill_list, spill_list2, h2x_best, h_w, h_B, h_boi, h_bt, h_small};
+        for (void* q : bufs) free_buf(q);
+        for (void* q : retired) free_buf(q);
         *this = Scratch();
     }
 };
@@ -182,6 +262,18 @@ struct Scratch {
 std::map<cudaStream_t, Scratch>& stream_scratch() {
     static std::map<cudaStream_t, Scratch> m;
     return m;
+}
+
+// The scratch of stream `st` (created on first use, growing in stream order).
+Scratch& scratch_for(cudaStream_t st) {
+    auto& m = stream_scratch();
+    auto it = m.find(st);
+    if (it == m.end()) {
+        it = m.emplace(st, Scratch()).first;
+        it->second.ordered = true;
+        it->second.ord = st;
+    }
+    return it->second;
 }
 
 // ------------------------------------------------------------ launch plan
@@ -413,24 +505,25 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
 }
 
 int ensure_scratch(Scratch& sc, const LaunchPlan& lp, int64_t N, int64_t total_m) {
+    sc.free_retired();
     int rc = sc.ensure_fixed();
     if (rc) return rc;
-    if ((rc = grow(sc.cls, sc.cap_cls, N))) return rc;
+    if ((rc = sc.grow(sc.cls, sc.cap_cls, N))) return rc;
     if (!lp.mode.compose) {
-        if ((rc = grow(sc.order, sc.cap_order, N))) return rc;
-        if ((rc = grow(sc.spill_list, sc.cap_spill_list, N))) return rc;
-        if ((rc = grow(sc.spill_list2, sc.cap_spill_list2, N))) return rc;
-        if (lp.kc.enabled && (rc = grow(sc.kc_slots, sc.cap_kc_slots, int64_t(lp.kc.grid) * lp.kc.bin_cap)))
+        if ((rc = sc.grow(sc.order, sc.cap_order, N))) return rc;
+        if ((rc = sc.grow(sc.spill_list, sc.cap_spill_list, N))) return rc;
+        if ((rc = sc.grow(sc.spill_list2, sc.cap_spill_list2, N))) return rc;
+        if (lp.kc.enabled && (rc = sc.grow(sc.kc_slots, sc.cap_kc_slots, int64_t(lp.kc.grid) * lp.kc.bin_cap)))
             return rc;
         return VSBPP_OK;
     }
     const int64_t U = total_m / std::max<int64_t>(lp.mode.s, 1) + N;   // >= sum ceil(m_i/s)
-    if ((rc = grow(sc.nu, sc.cap_nu, N))) return rc;
-    if ((rc = grow(sc.unit_base, sc.cap_unit_base, N + 1))) return rc;
-    if ((rc = grow(sc.unit_count, sc.cap_unit_count, U))) return rc;
-    if (lp.h2x && (rc = grow(sc.h2x_best, sc.cap_h2x_best, U))) return rc;
-    if ((rc = grow(sc.unit_total, sc.cap_unit_total, U))) return rc;
-    if ((rc = grow(sc.local_types, sc.cap_local_types, total_m))) return rc;
+    if ((rc = sc.grow(sc.nu, sc.cap_nu, N))) return rc;
+    if ((rc = sc.grow(sc.unit_base, sc.cap_unit_base, N + 1))) return rc;
+    if ((rc = sc.grow(sc.unit_count, sc.cap_unit_count, U))) return rc;
+    if (lp.h2x && (rc = sc.grow(sc.h2x_best, sc.cap_h2x_best, U))) return rc;
+    if ((rc = sc.grow(sc.unit_total, sc.cap_unit_total, U))) return rc;
+    if ((rc = sc.grow(sc.local_types, sc.cap_local_types, total_m))) return rc;
     return VSBPP_OK;
 }
 
@@ -655,7 +748,7 @@ int batch_common(int64_t N, const int32_t* w_all, const int64_t* w_off, const in
     LaunchPlan lp;
     if ((rc = build_plan(prm, max_m, N, lp))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Scratch& sc = stream_scratch()[st];
+    Scratch& sc = scratch_for(st);
     // sublist scratch is sized from the host-side bound N * max_m, so the call
     // never has to read the device offsets back
     const int64_t total_m = lp.mode.compose ? N * std::max<int64_t>(max_m, 1) : 0;
@@ -690,7 +783,7 @@ int time_config(const vsbpp_config& cfg, int64_t N, const int32_t* w_all, const 
         g_cfg = saved;
         return rc;
     }
-    Scratch& sc = stream_scratch()[st];
+    Scratch& sc = scratch_for(st);
     const int64_t total_m = lp.mode.compose ? N * std::max<int64_t>(max_m, 1) : 0;
     if ((rc = ensure_scratch(sc, lp, N, total_m))) {
         g_cfg = saved;
@@ -755,7 +848,7 @@ int vsbpp_pack_device(const int32_t* w, int64_t m, const int32_t* B, int32_t n, 
     LaunchPlan lp;
     if ((rc = build_plan(prm, std::max<int64_t>(m, 1), 1, lp))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Scratch& sc = stream_scratch()[st];
+    Scratch& sc = scratch_for(st);
     if ((rc = ensure_scratch(sc, lp, 1, m))) return rc;
     BatchView in{1, w, nullptr, m, B, nullptr, n};
     OutView out{bin_of_item, bin_type, num_bins, total_capacity, status, nullptr, nullptr, nullptr};
@@ -773,12 +866,12 @@ int vsbpp_pack(const int32_t* w, int64_t m, const int32_t* B, int32_t n, const v
     std::lock_guard<std::recursive_mutex> lk(g_mu);
     static cudaStream_t own = nullptr;
     if (!own) VS_TRY(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-    Scratch& sc = stream_scratch()[own];
-    if ((rc = grow(sc.h_w, sc.cap_h_w, m))) return rc;
-    if ((rc = grow(sc.h_B, sc.cap_h_B, n))) return rc;
-    if ((rc = grow(sc.h_boi, sc.cap_h_boi, m))) return rc;
-    if ((rc = grow(sc.h_bt, sc.cap_h_bt, m))) return rc;
-    if ((rc = grow(sc.h_small, sc.cap_h_small, 3))) return rc;
+    Scratch& sc = scratch_for(own);
+    if ((rc = sc.grow(sc.h_w, sc.cap_h_w, m))) return rc;
+    if ((rc = sc.grow(sc.h_B, sc.cap_h_B, n))) return rc;
+    if ((rc = sc.grow(sc.h_boi, sc.cap_h_boi, m))) return rc;
+    if ((rc = sc.grow(sc.h_bt, sc.cap_h_bt, m))) return rc;
+    if ((rc = sc.grow(sc.h_small, sc.cap_h_small, 3))) return rc;
     if (m > 0) VS_TRY(cudaMemcpyAsync(sc.h_w, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, own));
     VS_TRY(cudaMemcpyAsync(sc.h_B, B, sizeof(int32_t) * n, cudaMemcpyHostToDevice, own));
     int32_t* d_status = reinterpret_cast<int32_t*>(sc.h_small + 2);

@@ -85,6 +85,10 @@ struct vsbpp_server {
     int max_slots = 1, nlanes = 1, max_queued = 1;
     int device = 0;
     std::vector<cudaStream_t> lanes;
+    // Request buffers: freed memory is kept (release threshold = budget) and
+    // reused by another lane only once its free has completed, never by making
+    // that lane wait on the freeing one.
+    cudaMemPool_t pool = nullptr;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Req*> waiting;
@@ -154,7 +158,7 @@ int launch(Req* r, cudaStream_t st) {
     const size_t ow = align256(4 * static_cast<size_t>(m));
     const size_t oB = align256(4 * static_cast<size_t>(n));
     const size_t om = align256(4 * static_cast<size_t>(std::max<int64_t>(m, 1)));
-    cudaError_t e = cudaMallocAsync(&r->d_buf, r->need, st);
+    cudaError_t e = cudaMallocFromPoolAsync(&r->d_buf, r->need, r->srv->pool, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VSBPP_ENOMEM : VSBPP_ECUDA;
     char* d = static_cast<char*>(r->d_buf);
     int32_t* d_w = reinterpret_cast<int32_t*>(d);
@@ -247,10 +251,24 @@ int vsbpp_server_create(size_t device_mem_budget, int32_t max_slots, int32_t lan
     s->nlanes = lanes;
     s->max_queued = max_queued;
     cudaGetDevice(&s->device);
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = s->device;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+        delete s;
+        return VSBPP_ECUDA;
+    }
+    uint64_t keep = device_mem_budget;
+    int no = 0;
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     for (int i = 0; i < lanes; ++i) {
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             for (cudaStream_t x : s->lanes) cudaStreamDestroy(x);
+            cudaMemPoolDestroy(s->pool);
             delete s;
             return VSBPP_ECUDA;
         }
@@ -382,6 +400,7 @@ int vsbpp_server_destroy(vsbpp_server* s) {
     if (s->worker.joinable()) s->worker.join();
     for (cudaStream_t st : s->lanes) cudaStreamSynchronize(st);
     for (cudaStream_t st : s->lanes) cudaStreamDestroy(st);
+    cudaMemPoolDestroy(s->pool);
     for (auto& kv : s->tickets) release_req(s, kv.second);
     s->tickets.clear();
     s->pinned.release();

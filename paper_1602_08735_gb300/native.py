@@ -398,7 +398,7 @@ def tune_load(path: str) -> None:
 class Server:
     """Continuous-batching packing server (vsbpp_server_*)."""
 
-    def __init__(self, device_mem_budget: int, max_slots: int = 64, lanes: int = 8,
+    def __init__(self, device_mem_budget: int, max_slots: int = 64, lanes: int = 32,
                  max_queued: int = 1 << 20):
         self._lib = load()
         h = ctypes.c_void_p()

@@ -94,3 +94,21 @@ def test_config4_full_size(crit):
             k = 20_000
             pre = oracle.pack(w[:k], B, 1, crit)
             _check_prefix(res.bin_of_item, res.bin_type, pre)
+
+
+def test_many_tiny_instances():
+    """100,000 instances of 0..12 items (empty ones included) in one batch:
+    the size-class machinery, the work queue and the composition pass at a
+    scale where per-instance overheads dominate; both heuristics."""
+    rng = np.random.default_rng(101)
+    ms = rng.integers(0, 13, size=100_000)
+    inst = []
+    for m in ms:
+        n = int(rng.integers(1, 5))
+        B = np.sort(rng.choice(np.arange(1, 200), size=n, replace=False))[::-1].astype(np.int32)
+        inst.append((rng.integers(1, int(B[0]) + 1, size=int(m)).astype(np.int32), B))
+    b = I.from_instances(inst)
+    for (h, c, s, plain) in ((1, 1, 0, False), (1, 3, 0, True), (2, 1, 5, False), (2, 0, 3, True),
+                             (1, 2, 4, False)):
+        got = run_batch(b, h, c, s, seed=6, plain=plain)
+        assert_same(b, got, run_oracle(b, h, c, s, seed=6), f"tiny h{h} c{c} s{s} plain={plain}")
