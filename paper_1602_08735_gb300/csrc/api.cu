@@ -310,6 +310,7 @@ struct LaunchPlan {
     vsbpp_config cfg;
     H1Shape large{}, small{}, wide{}, sub{};
     H1Shape full{};       // worst-case slots: repacks systems that outgrew large/small
+    int64_t large16_cap_m = 0;   // one-warp 16-bit slots (B_1 <= 255): largest m taken (0: none)
     KCShape kc{};
     int h2_threads = 0, h2_smem = 0, h2_grid = 0, h2_max_bins = 0;
     bool h2x = false;     // sublists of 7..12 items: the exhaustive search
@@ -478,6 +479,25 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
     rc = make_shape(lp.wide, true, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30, 200, bfi,
                     prm.criterion);
     if (rc != VSBPP_OK) return rc;
+    // systems with B_1 <= 255 past the large shape's reach (only the largest
+    // one-warp shape has any) take 16-bit slots in the same warp's shared
+    // memory, grown to the 16-bit layout (one warp per SM either way),
+    // admitted while 60% of their items would fill the slots; those that
+    // outgrow them go to global memory
+    lp.large16_cap_m = 0;
+    if (lp.large.warp_kernel && lp.large.groups == 1 && h1w_segment_words(lp.large.slot_cap) == 8) {
+        const int64_t cap16 = std::min<int64_t>(max_m, (h1w16_slots() - 64) * 100 / 60);
+        const int bytes16 = h1w16_bytes(bfi);
+        if (cap16 > lp.large.cap_m && bytes16 <= smax) {
+            lp.large16_cap_m = cap16;
+            if (bytes16 > lp.large.smem) {
+                lp.large.smem = bytes16;
+                const int occ = h1w_blocks_per_sm(lp.large.slot_cap, prm.criterion, 1, bytes16);
+                if (occ <= 0) return record(cudaErrorInvalidConfiguration);
+                lp.large.grid = occ * di.sms;
+            }
+        }
+    }
     cap_grid(lp.large, N);
     cap_grid(lp.small, N);
     cap_grid(lp.wide, N);
@@ -501,6 +521,7 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         if (occ <= 0) return record(cudaErrorInvalidConfiguration);
         kc.grid = static_cast<int>(std::min<int64_t>(int64_t(occ) * di.sms, std::max<int64_t>(N, 1)));
     }
+    if (!lp.kc.enabled) lp.large16_cap_m = 0;     // no global-memory fallback for its spills
     return VSBPP_OK;
 }
 
@@ -549,6 +570,15 @@ H1Params h1_params(const BatchView& in, const OutView& out, const vsbpp_params& 
     return p;
 }
 
+// The large class's 16-bit slot systems: m past the 32-bit reach, B_1 <= 255;
+// those that outgrow the slots are listed for global memory.
+void set_h16(H1Params& p, const LaunchPlan& lp, Scratch& sc) {
+    if (lp.large16_cap_m <= 0 || !lp.kc.enabled) return;
+    p.h16_min_m = lp.large.cap_m + 1;
+    p.spill_list2 = sc.spill_list2;
+    p.spill_seg2 = sc.spill_seg() + 2;
+}
+
 // Enqueue the whole pipeline on `st`.  plain = one launch per instance.
 int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutView& out0,
             const vsbpp_params& prm, bool plain, cudaStream_t st) {
@@ -569,6 +599,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
         pp.small_m = plain ? 0 : lp.cfg.small_m;      // plain path: no single-warp class
         pp.narrow_cap = lp.large.cap_m;
         pp.narrow_bins = lp.large.warp_kernel ? (int64_t(1) << 40) : 65536;   // one-warp shapes spill instead
+        pp.narrow_cap16 = lp.large16_cap_m;
         pp.small_cap = lp.small.cap_m;
         pp.wide_cap = lp.wide.cap_m;
         pp.huge_cap = lp.kc.enabled ? lp.kc.cap_m : 0;
@@ -589,6 +620,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
                     p.want_cls = kClassLarge;
                     p.spill_list = sc.spill_list;
                     p.spill_seg = sc.spill_seg();
+                    set_h16(p, lp, sc);
                     VS_TRY(launch_shape(sh, false, p, 1, 1, st));
                 }
                 continue;
@@ -604,6 +636,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
                 p.spill_list = sc.spill_list;
                 p.spill_seg = sc.spill_seg();
             }
+            if (c == kClassLarge) set_h16(p, lp, sc);
             const bool timed = c == kClassLarge && timing_begin(st);
             VS_TRY(launch_shape(sh, c == kClassWide, p, sh.groups, sh.grid, st));
             timing_end(timed, st);

@@ -19,6 +19,7 @@ constexpr int kWF = VSBPP_WF;
 constexpr int kRandom = VSBPP_RANDOM;
 constexpr int kMaxTypes = VSBPP_MAX_TYPES;
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kH16MaxB = 255;   // B_1 limit of the one-warp kernel's 16-bit slot form
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the key-th output of the
 // stream seeded with `seed` is the variant-13 mix of seed + (key+1)*gamma.

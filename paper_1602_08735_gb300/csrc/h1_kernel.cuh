@@ -110,6 +110,13 @@ struct H1Params {
     // spill_seg[1]); a worst-case-sized launch packs it again from the start.
     int32_t* spill_list;
     int64_t* spill_seg;
+    // One-warp kernel only: a system with B_1 <= 255 and at least h16_min_m
+    // items (0: none) packs in 16-bit slots, twice slot_cap of them; one that
+    // outgrows those goes to spill_list2 (count in spill_seg2[1]), which
+    // global memory packs.
+    int64_t h16_min_m;
+    int32_t* spill_list2;
+    int64_t* spill_seg2;
     unsigned long long* counters;  // null, or {items, fit tests} to add to
     int32_t compose;        // 1: write sublist-local results (see OutView)
     int32_t bf_index;       // 1: the BF residual index is laid out (used when B_1 <= 1023)

@@ -25,6 +25,12 @@ int h1w_supported(int slot_cap) { return h1w_ns(slot_cap) > 0; }
 
 int h1w_bytes(int slot_cap, int bf_index) { return h1w_group_bytes(slot_cap, bf_index); }
 
+int h1w_segment_words(int slot_cap) { return h1w_ns(slot_cap); }
+
+int h1w16_slots() { return static_cast<int>(kH16Slots); }
+
+int h1w16_bytes(int bf_index) { return h1w16_group_bytes(bf_index); }
+
 cudaError_t h1w_launch(const H1Params& p, int groups, int grid, int smem, cudaStream_t st) {
     const void* k = h1w_kernel_for(p.slot_cap, p.criterion);
     if (!k || groups < 1 || groups > 16 || p.compose) return cudaErrorInvalidValue;

@@ -1,5 +1,6 @@
 // h1w_kernel.cuh -- the first heuristic of Section 6.3, one warp per membrane
-// system, for systems of at most 32768 bins with B_1 <= 32767.
+// system, for systems of at most 32768 bins with B_1 <= 32767, or of at most
+// 65536 bins with B_1 <= 255 (16-bit slots, run16 below).
 //
 // Same method as h1_kernel.cuh (Rules 2-6: items in list order, fit test
 // residual >= w, FF / BF / WF with the lowest creation index winning ties,
@@ -39,6 +40,8 @@
 namespace vsbpp {
 
 constexpr int kWarpMaxSlots = 32768;      // 8 segment words per lane at most
+constexpr int kNS16 = 12;                  // 16-bit slots: segment words per lane
+constexpr uint32_t kH16Slots = 32u * kNS16 * 256u;   // 98304 bins
 
 // Segment words per lane for a system of slot_cap bins (0: too large).
 __host__ __device__ inline int h1w_ns(int slot_cap) {
@@ -55,12 +58,21 @@ __host__ __device__ inline int h1w_group_bytes(int slot_cap, int bf_index) {
     return 4 * slot_cap + 16 + (bf_index ? 4 * (kIndexMaxRes + 1) * ns + 16 : 0) + 4 * kMaxTypes;
 }
 
+// Shared memory of the 16-bit slot layout (one warp): slots, a 16-byte pad,
+// the BF rows (256 residuals x kNS16 words) and a pad when laid out,
+// capacities.
+__host__ __device__ inline int h1w16_group_bytes(int bf_index) {
+    return 2 * static_cast<int>(kH16Slots) + 16 + (bf_index ? 4 * (kH16MaxB + 1) * kNS16 + 16 : 0) +
+           4 * kMaxTypes;
+}
+
 template <int NS, int CRIT>
 struct H1Warp {
     static constexpr bool kSeg = CRIT != kBF;                      // FF or WF items occur
     static constexpr bool kBFItems = CRIT == kBF || CRIT == kRandom;
     static constexpr uint32_t kNoKey = 0xFFFFFFFFu;
     static constexpr uint32_t kRowsPad = (kIndexMaxRes + 1) * NS;   // index word past the rows
+    static constexpr bool kLaneRows = NS >= 4;      // index row words spread over the lanes
 
     uint32_t* slots;
     uint32_t* rows;      // BF index rows (null when not laid out)
@@ -192,9 +204,11 @@ struct H1Warp {
             //    residual; R = the residual sought (BF, WF)
             bool hit;
             uint32_t sf = 0, Mseg = 0, R = 0;
-            uint32_t rw[NS], rn[NS];          // index rows of r_old and of r_new
+            // index rows of r_old and of r_new: all NS words in every lane
+            // (NS < 4), or word `lane` in lane `lane` (kLaneRows)
+            uint32_t rw[kLaneRows ? 1 : NS], rn[kLaneRows ? 1 : NS];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) rw[q] = rn[q] = 0;
+            for (int q = 0; q < (kLaneRows ? 1 : NS); ++q) rw[q] = rn[q] = 0;
             if (kSeg && c == kFF) {
                 uint32_t key = kNoKey;
 #pragma unroll
@@ -226,14 +240,22 @@ struct H1Warp {
                 pend_bit = 0;
                 // the row the chosen bin leaves and the row it enters, read together
                 const uint32_t Rn = (hit ? R : Bn) - wj;
+                if constexpr (kLaneRows) {
+                    rw[0] = ulane < NS ? rows[R * NS + ulane] : 0u;
+                    rn[0] = ulane < NS ? rows[Rn * NS + ulane] : 0u;
+                    const uint32_t sk = rw[0] ? 32u * ulane + static_cast<uint32_t>(__ffs(rw[0]) - 1) : kNoKey;
+                    sf = __reduce_min_sync(kFull, sk);
+                    sf = hit ? sf : 0u;
+                } else {
 #pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    rw[q] = rows[R * NS + q];
-                    rn[q] = rows[Rn * NS + q];
+                    for (int q = 0; q < NS; ++q) {
+                        rw[q] = rows[R * NS + q];
+                        rn[q] = rows[Rn * NS + q];
+                    }
+#pragma unroll
+                    for (int q = NS - 1; q >= 0; --q)
+                        sf = rw[q] ? 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1) : sf;
                 }
-#pragma unroll
-                for (int q = NS - 1; q >= 0; --q)
-                    sf = rw[q] ? 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1) : sf;
             } else {
                 const uint32_t key = bf_scan<kR>(wj, L);
                 hit = key != kNoKey;
@@ -323,10 +345,15 @@ struct H1Warp {
                     rows[pend_at] = pend_word | pend_bit;
                     pend_at = kRowsPad;
                     pend_bit = 0;
+                    if constexpr (kLaneRows) {
+                        rw[0] = ulane < NS ? rows[r_old * NS + ulane] : 0u;
+                        rn[0] = ulane < NS ? rows[r_new * NS + ulane] : 0u;
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < NS; ++q) {
-                        rw[q] = rows[r_old * NS + q];
-                        rn[q] = rows[r_new * NS + q];
+                        for (int q = 0; q < NS; ++q) {
+                            rw[q] = rows[r_old * NS + q];
+                            rn[q] = rows[r_new * NS + q];
+                        }
                     }
                     if (c == kFF)
                         cR = __reduce_add_sync(kFull, (r0 == r_old) + (r1 == r_old) + (r2 == r_old) + (r3 == r_old));
@@ -336,20 +363,240 @@ struct H1Warp {
                 // selects and plain stores only: an update that does not
                 // apply writes the pad word
                 const bool clear = hit && cR == 1u;
-                uint32_t any = 0, word = 0, wnew = 0;
+                bool any;
+                if constexpr (kLaneRows) {
+                    // the lane holding word sb / 32 writes both rows' words
+                    const bool here = ulane == (sb >> 5);
+                    const uint32_t cl = here ? rw[0] & ~(1u << (sb & 31)) : rw[0];
+                    any = __any_sync(kFull, cl != 0u);
+                    if (here) {
+                        rows[clear ? r_old * NS + (sb >> 5) : kRowsPad] = cl;
+                        rows[r_new > 0u ? r_new * NS + (sb >> 5) : kRowsPad] = rn[0] | (1u << (sb & 31));
+                    }
+                } else {
+                    uint32_t anyw = 0, word = 0, wnew = 0;
 #pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    const bool here = (sb >> 5) == static_cast<uint32_t>(q);
-                    const uint32_t cl = here ? rw[q] & ~(1u << (sb & 31)) : rw[q];
-                    word = here ? cl : word;
-                    any |= cl;
-                    wnew = here ? rn[q] : wnew;
+                    for (int q = 0; q < NS; ++q) {
+                        const bool here = (sb >> 5) == static_cast<uint32_t>(q);
+                        const uint32_t cl = here ? rw[q] & ~(1u << (sb & 31)) : rw[q];
+                        word = here ? cl : word;
+                        anyw |= cl;
+                        wnew = here ? rn[q] : wnew;
+                    }
+                    any = anyw != 0u;
+                    rows[clear ? r_old * NS + (sb >> 5) : kRowsPad] = word;
+                    rows[r_new > 0u ? r_new * NS + (sb >> 5) : kRowsPad] = wnew | (1u << (sb & 31));
                 }
-                rows[clear ? r_old * NS + (sb >> 5) : kRowsPad] = word;
                 wb = (clear && !any && (r_old >> 5) == ulane) ? wb & ~(1u << (r_old & 31)) : wb;
-                rows[r_new > 0u ? r_new * NS + (sb >> 5) : kRowsPad] = wnew | (1u << (sb & 31));
                 wb = (r_new > 0u && (r_new >> 5) == ulane) ? wb | (1u << (r_new & 31)) : wb;
                 pend_at = fire ? Bt * NS + (sfire >> 5) : kRowsPad;
+                pend_bit = fire ? 1u << (sfire & 31) : 0u;
+                wb = (fire && (Bt >> 5) == ulane) ? wb | (1u << (Bt & 31)) : wb;
+            }
+            L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
+            bout = ulane == jj ? b : bout;
+            d = dn;
+            __syncwarp();
+        }
+            if (ulane < cnt) raw[j0 + ulane] = static_cast<int32_t>(bout);
+        }
+        L_io = L;
+        return true;
+    }
+
+    // 16-bit slots (B_1 <= 255): slot = (residual << 8) | capacity, kH16Slots
+    // of them in segments of 256 bins (one 16-byte read per lane still covers
+    // a segment; kNS16 segment words per lane), with the BF index rows r16 of
+    // 256 residuals after them.  A key (index in the segment << 16) | slot
+    // carries index, residual and capacity at once.  BF items use the
+    // residual index (IDX: laid out whenever BF items occur).  A system that
+    // would outgrow the slots, or whose bins so far, extrapolated to all k
+    // items, pass them, is appended to spill_list2 and packed in global
+    // memory.
+    template <bool IDX>
+    __device__ __forceinline__ bool run16(const H1Params& p, int64_t i, const int32_t* w, uint32_t k,
+                                          int32_t* raw, int n, uint32_t& L_io,
+                                          unsigned long long& fit_tests, uint32_t* r16) const {
+        constexpr uint32_t kPad16 = (kH16MaxB + 1) * kNS16;     // index word past the rows
+        uint16_t* s16 = reinterpret_cast<uint16_t*>(slots);
+        uint32_t L = L_io;
+        constexpr uint32_t cap_bins = kH16Slots;
+        const uint32_t ulane = static_cast<uint32_t>(lane);
+
+        uint32_t sm[kNS16];                 // segment maxima, segment 32q + lane
+        uint32_t wb = 0;                 // residuals 32*lane .. 32*lane+31 present
+#pragma unroll
+        for (int q = 0; q < kNS16; ++q) sm[q] = 0;
+        if (kSeg && L > 0 && lane == 0) sm[0] = Bs[0];
+        if (IDX) {
+            for (uint32_t t = 0; t < L; ++t) {
+                const uint32_t r = Bs[t];
+                if ((r >> 5) == ulane) wb |= 1u << (r & 31);
+            }
+        }
+        uint32_t pend_at = kPad16, pend_bit = 0;
+        uint32_t dnext = descriptor(weight(w, ulane, k), ulane, n, p.seed, 0);
+        uint32_t wpre = weight(w, 32 + ulane, k);
+        for (uint32_t j0 = 0; j0 < k; j0 += 32u) {
+            const uint32_t cnt = min(32u, k - j0);
+            const bool trend = j0 >= 2048u &&
+                               static_cast<uint64_t>(L) * k > static_cast<uint64_t>(cap_bins) * j0;
+            if (L + 2u * cnt > cap_bins || trend) {
+                if (lane == 0) {
+                    const unsigned long long pos = atomicAdd(
+                        reinterpret_cast<unsigned long long*>(p.spill_seg2 + 1), 1ull);
+                    p.spill_list2[pos] = static_cast<int32_t>(i);
+                }
+                __syncwarp();
+                return false;
+            }
+            const uint32_t dblk = dnext;
+            dnext = descriptor(wpre, static_cast<int64_t>(j0) + 32 + ulane, n, p.seed, 0);
+            wpre = weight(w, static_cast<int64_t>(j0) + 64 + ulane, k);
+            uint32_t d = __shfl_sync(kFull, dblk, 0);
+            uint32_t bout = 0;
+        for (uint32_t jj = 0; jj < cnt; ++jj) {
+            const uint32_t dn = __shfl_sync(kFull, dblk, static_cast<int>((jj + 1u) & 31u));
+            const uint32_t wj = d & 0x7FFFu;
+            const uint32_t Bn = (d >> 16) & 0x7FFFu;
+            const int c = CRIT == kRandom ? static_cast<int>(((d >> 15) & 1u) | ((d >> 30) & 2u)) : CRIT;
+            fit_tests += L;
+            uint32_t pend_word = 0;
+            if (IDX) pend_word = r16[pend_at];
+
+            // 1. the segment holding the answer (as in the 32-bit form)
+            bool hit = false;
+            uint32_t sf = 0, Mseg = 0, R = 0;
+            uint32_t rwl = 0, rnl = 0;        // word `lane` of the two index rows
+            if (kSeg && c == kFF) {
+                uint32_t key = kNoKey;
+#pragma unroll
+                for (int q = kNS16 - 1; q >= 0; --q)
+                    key = sm[q] >= wj ? ((32u * q + ulane) << 16) | sm[q] : key;
+                key = __reduce_min_sync(kFull, key);
+                hit = key != kNoKey;
+                sf = hit ? key >> 16 : 0u;
+                Mseg = key & 0xFFFFu;
+            } else if (kSeg && c == kWF) {
+                uint32_t key = 0;
+#pragma unroll
+                for (int q = 0; q < kNS16; ++q) key = max(key, (sm[q] << 9) | (511u - (32u * q + ulane)));
+                key = __reduce_max_sync(kFull, key);
+                Mseg = key >> 9;
+                sf = 511u - (key & 511u);
+                hit = Mseg >= wj;
+                R = Mseg;
+            } else if (IDX) {
+                const uint32_t wi = wj >> 5;
+                const uint32_t x = wb & (ulane < wi ? 0u : ulane == wi ? ~((1u << (wj & 31)) - 1u) : 0xFFFFFFFFu);
+                uint32_t key = x ? 32u * ulane + static_cast<uint32_t>(__ffs(x) - 1) : kNoKey;
+                key = __reduce_min_sync(kFull, key);
+                hit = key != kNoKey;
+                R = hit ? key : 0u;
+                r16[pend_at] = pend_word | pend_bit;
+                pend_at = kPad16;
+                pend_bit = 0;
+                // the row the chosen bin leaves and the row it enters: word q
+                // of each in lane q; the first segment holding R by one
+                // warp minimum
+                const uint32_t Rn = (hit ? R : Bn) - wj;
+                rwl = ulane < kNS16 ? r16[R * kNS16 + ulane] : 0u;
+                rnl = ulane < kNS16 ? r16[Rn * kNS16 + ulane] : 0u;
+                const uint32_t sk = rwl ? 32u * ulane + static_cast<uint32_t>(__ffs(rwl) - 1) : kNoKey;
+                sf = __reduce_min_sync(kFull, sk);
+                sf = hit ? sf : 0u;
+            }
+            if (kSeg && c == kBF) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int q = 0; q < kNS16; ++q) v = (sf >> 5) == static_cast<uint32_t>(q) ? sm[q] : v;
+                Mseg = __shfl_sync(kFull, v, static_cast<int>(sf & 31));
+            }
+
+            // 2. in segment sf: eight 16-bit slots per lane
+            const uint4 Q = reinterpret_cast<const uint4*>(slots)[32u * sf + ulane];
+            uint32_t h[8];
+            h[0] = Q.x & 0xFFFFu; h[1] = Q.x >> 16; h[2] = Q.y & 0xFFFFu; h[3] = Q.y >> 16;
+            h[4] = Q.z & 0xFFFFu; h[5] = Q.z >> 16; h[6] = Q.w & 0xFFFFu; h[7] = Q.w >> 16;
+            const uint32_t i0 = (8u * ulane) << 16;
+            uint32_t k1 = kNoKey, cR = 0, cM = 0, M2 = 0;
+            if (kSeg) {
+                uint32_t nm = 0, m2 = 0;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t r = h[e] >> 8;
+                    nm += r == Mseg ? 1u : 0u;
+                    m2 = max(m2, r != Mseg ? r : 0u);
+                }
+                cM = __reduce_add_sync(kFull, nm);
+                M2 = __reduce_max_sync(kFull, m2);
+            }
+            if (c == kFF) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    k1 = min(k1, (h[e] >> 8) >= wj ? (i0 + (static_cast<uint32_t>(e) << 16)) | h[e] : kNoKey);
+            } else {
+                uint32_t nr = 0;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const bool eq = (h[e] >> 8) == R;
+                    k1 = min(k1, eq ? (i0 + (static_cast<uint32_t>(e) << 16)) | h[e] : kNoKey);
+                    nr += eq ? 1u : 0u;
+                }
+                if (IDX) cR = __reduce_add_sync(kFull, nr);
+            }
+            k1 = __reduce_min_sync(kFull, k1);
+            const uint32_t b = hit ? 256u * sf + (k1 >> 16) : L;
+            const uint32_t r_old = hit ? (k1 >> 8) & 0xFFu : Bn;
+            const uint32_t Bt = hit ? k1 & 0xFFu : Bn;
+            const uint32_t r_new = r_old - wj;
+            const bool fire = (Bt < 2u * r_old) && (2u * r_new <= Bt);     // Rule 5
+            const uint32_t Lf = hit ? L : L + 1u;
+            s16[b] = static_cast<uint16_t>((r_new << 8) | Bt);
+            s16[fire ? Lf : cap_bins] = static_cast<uint16_t>((Bt << 8) | Bt);
+            const uint32_t sb = b >> 8, sfire = Lf >> 8;
+
+            // 3. segment maxima
+            if (kSeg) {
+                const uint32_t top = (r_old != Mseg || cM >= 2u) ? Mseg : max(M2, r_new);
+#pragma unroll
+                for (int q = 0; q < kNS16; ++q) {
+                    const uint32_t s = 32u * q + ulane;
+                    uint32_t v = sm[q];
+                    v = s == sb ? (hit ? top : max(v, r_new)) : v;
+                    v = (fire && s == sfire) ? max(v, Bt) : v;
+                    sm[q] = v;
+                }
+            }
+            // 4. the BF index
+            if (IDX) {
+                if (c != kBF) {
+                    r16[pend_at] = pend_word | pend_bit;
+                    pend_at = kPad16;
+                    pend_bit = 0;
+                    rwl = ulane < kNS16 ? r16[r_old * kNS16 + ulane] : 0u;
+                    rnl = ulane < kNS16 ? r16[r_new * kNS16 + ulane] : 0u;
+                    if (c == kFF) {
+                        uint32_t nr = 0;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) nr += (h[e] >> 8) == r_old ? 1u : 0u;
+                        cR = __reduce_add_sync(kFull, nr);
+                    } else {
+                        cR = cM;
+                    }
+                }
+                // the lane holding word sb / 32 writes both rows' words
+                const bool clear = hit && cR == 1u;
+                const bool here = ulane == (sb >> 5);
+                const uint32_t cl = here ? rwl & ~(1u << (sb & 31)) : rwl;
+                const bool any = __any_sync(kFull, cl != 0u);
+                if (here) {
+                    r16[clear ? r_old * kNS16 + (sb >> 5) : kPad16] = cl;
+                    r16[r_new > 0u ? r_new * kNS16 + (sb >> 5) : kPad16] = rnl | (1u << (sb & 31));
+                }
+                wb = (clear && !any && (r_old >> 5) == ulane) ? wb & ~(1u << (r_old & 31)) : wb;
+                wb = (r_new > 0u && (r_new >> 5) == ulane) ? wb | (1u << (r_new & 31)) : wb;
+                pend_at = fire ? Bt * kNS16 + (sfire >> 5) : kPad16;
                 pend_bit = fire ? 1u << (sfire & 31) : 0u;
                 wb = (fire && (Bt >> 5) == ulane) ? wb | (1u << (Bt & 31)) : wb;
             }
@@ -373,7 +620,8 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
     const int lane = static_cast<int>(threadIdx.x) & 31;
     const int wid = static_cast<int>(threadIdx.x) >> 5;
     const int groups = static_cast<int>(blockDim.x) >> 5;
-    unsigned char* base = smem + static_cast<size_t>(wid) * static_cast<size_t>(p.group_bytes);
+    unsigned char* const group = smem + static_cast<size_t>(wid) * static_cast<size_t>(p.group_bytes);
+    unsigned char* base = group;
     H1Warp<NS, CRIT> g;
     g.lane = lane;
     g.slots = reinterpret_cast<uint32_t*>(base);
@@ -383,7 +631,11 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         g.rows = reinterpret_cast<uint32_t*>(base);
         base += 4 * (kIndexMaxRes + 1) * NS + 16;
     }
-    g.Bs = reinterpret_cast<uint32_t*>(base);
+    // capacities: the last bytes of the group (past either slot layout)
+    g.Bs = reinterpret_cast<uint32_t*>(group + p.group_bytes - 4 * kMaxTypes);
+    // the 16-bit layout's BF rows (after its slots)
+    uint32_t* const rows16 = reinterpret_cast<uint32_t*>(group + 2 * kH16Slots + 16);
+    const bool fits16 = p.group_bytes >= h1w16_group_bytes(p.bf_index);
 
     int64_t begin, end;
     if (p.seg) {
@@ -424,28 +676,42 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         const bool use_idx = g.rows != nullptr && H1Warp<NS, CRIT>::kBFItems &&
                              B1 <= static_cast<uint32_t>(kIndexMaxRes);
         const bool w10 = B1 <= 1023u;                 // 10-bit slot form
-        const int kR = w10 ? 10 : 16;
-        const uint32_t kCapMask = w10 ? 0x3FFu : 0xFFFFu;
+        // 16-bit slot form: systems too large for the 32-bit slots (only the
+        // largest shape, NS = 8, has systems past its reach)
+        const bool use16 = NS == 8 && fits16 && p.spill_list2 != nullptr && p.h16_min_m > 0 &&
+                           B1 <= kH16MaxB && k >= p.h16_min_m &&
+                           (!H1Warp<NS, CRIT>::kBFItems || p.bf_index);
+        const int kR = use16 ? 8 : w10 ? 10 : 16;
+        const uint32_t kCapMask = use16 ? 0xFFu : w10 ? 0x3FFu : 0xFFFFu;
+        uint16_t* s16 = reinterpret_cast<uint16_t*>(g.slots);
 
         // every slot reads as empty until its bin exists; index rows start clear
-        for (int q = lane; q < p.slot_cap / 4; q += 32)
+        const int quads = use16 ? static_cast<int>(kH16Slots / 8) : p.slot_cap / 4;
+        for (int q = lane; q < quads; q += 32)
             reinterpret_cast<uint4*>(g.slots)[q] = make_uint4(0u, 0u, 0u, 0u);
-        if (use_idx)
+        if (use16 && H1Warp<NS, CRIT>::kBFItems)
+            for (uint32_t x = static_cast<uint32_t>(lane); x < (B1 + 1u) * kNS16; x += 32u) rows16[x] = 0u;
+        else if (use_idx)
             for (uint32_t x = static_cast<uint32_t>(lane); x < (B1 + 1u) * NS; x += 32u) g.rows[x] = 0u;
         __syncwarp();
         uint32_t L = 0;
         if (p.preopen) {                     // literal Rule 2: one empty bin per type
             if (lane < n) {
-                g.slots[lane] = (Bl << kR) | Bl;
-                if (use_idx) atomicOr(&g.rows[Bl * NS], 1u);     // segment 0
+                if (use16) s16[lane] = static_cast<uint16_t>((Bl << 8) | Bl);
+                else g.slots[lane] = (Bl << kR) | Bl;
+                if (use16 && H1Warp<NS, CRIT>::kBFItems) atomicOr(&rows16[Bl * kNS16], 1u);   // segment 0
+                else if (use_idx) atomicOr(&g.rows[Bl * NS], 1u);
             }
             L = static_cast<uint32_t>(n);
             __syncwarp();
         }
         unsigned long long fit_tests = 0;
-        bool done;
+        bool done = false;
         const uint32_t k32 = static_cast<uint32_t>(k);
-        if constexpr (H1Warp<NS, CRIT>::kBFItems) {
+        if (use16) {
+            if constexpr (NS == 8)
+                done = g.template run16<H1Warp<NS, CRIT>::kBFItems>(p, i, w, k32, raw, n, L, fit_tests, rows16);
+        } else if constexpr (H1Warp<NS, CRIT>::kBFItems) {
             done = use_idx ? g.template run<true, true>(p, i, w, 0, k32, raw, n, L, fit_tests)
                  : w10     ? g.template run<false, true>(p, i, w, 0, k32, raw, n, L, fit_tests)
                            : g.template run<false, false>(p, i, w, 0, k32, raw, n, L, fit_tests);
@@ -463,7 +729,7 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         const uint32_t b1 = (b0 + per) < L ? (b0 + per) : L;
         uint32_t cnt = 0;
         for (uint32_t b = b0; b < b1; ++b) {
-            const uint32_t s = g.slots[b];
+            const uint32_t s = use16 ? static_cast<uint32_t>(s16[b]) : g.slots[b];
             cnt += static_cast<uint32_t>((s >> kR) < (s & kCapMask));
         }
         const uint32_t excl = warp_exclusive_scan(cnt, lane);
@@ -471,18 +737,27 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         uint32_t dd = excl;
         uint64_t tot = 0;
         for (uint32_t b = b0; b < b1; ++b) {
-            const uint32_t s = g.slots[b];
+            const uint32_t s = use16 ? static_cast<uint32_t>(s16[b]) : g.slots[b];
             const uint32_t cap = s & kCapMask;
             if ((s >> kR) < cap) {
                 types_out[dd] = static_cast<int32_t>(g.type_of(cap, n));
-                g.slots[b] = dd;
+                if (use16) s16[b] = static_cast<uint16_t>(dd);      // low 16 bits (see below)
+                else g.slots[b] = dd;
                 tot += cap;
                 ++dd;
             }
         }
         __syncwarp();
-        for (int64_t j = lane; j < k; j += 32)
-            raw[j] = static_cast<int32_t>(g.slots[static_cast<uint32_t>(raw[j])]);
+        // 16-bit slots keep the low 16 bits of a dense id d <= b.  b - d counts
+        // the unused bins before b: bins left empty by Rule 5 (each the
+        // division of a distinct bin that does hold items, so at most half of
+        // the 98304 slots) and the preopened ones, fewer than 65536 in all;
+        // so d = b - ((b - low) mod 65536).
+        for (int64_t j = lane; j < k; j += 32) {
+            const uint32_t b = static_cast<uint32_t>(raw[j]);
+            raw[j] = static_cast<int32_t>(use16 ? b - ((b - static_cast<uint32_t>(s16[b])) & 0xFFFFu)
+                                                : g.slots[b]);
+        }
         tot = warp_sum_u64(tot);
         if (lane == 0) {
             if (p.counters) {

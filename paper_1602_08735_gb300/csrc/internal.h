@@ -32,6 +32,12 @@ int h1w_supported(int slot_cap);
 int h1w_bytes(int slot_cap, int bf_index);
 cudaError_t h1w_launch(const H1Params& p, int groups, int grid, int smem, cudaStream_t st);
 int h1w_blocks_per_sm(int slot_cap, int criterion, int groups, int smem);
+// Segment words per lane of a one-warp shape (1, 2, 4, 8; 0: none).  The
+// 8-word shapes also take systems with B_1 <= 255 in 16-bit slots: that
+// layout's bins and its shared memory per warp.
+int h1w_segment_words(int slot_cap);
+int h1w16_slots();
+int h1w16_bytes(int bf_index);
 
 cudaError_t kc_launch(const KCParams& p, int grid, int smem, cudaStream_t st);
 int kc_blocks_per_sm(int smem);

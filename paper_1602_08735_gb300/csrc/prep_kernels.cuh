@@ -72,6 +72,8 @@ __global__ void validate_kernel(const PrepParams p) {
                 c = kClassSmall;
             } else if (B1 <= p.narrow_max_B && m <= p.narrow_cap && bins <= p.narrow_bins) {
                 c = kClassLarge;
+            } else if (B1 <= static_cast<int64_t>(kH16MaxB) && m <= p.narrow_cap16) {
+                c = kClassLarge;                    // 16-bit slots of the one-warp kernel
             } else if (m <= p.wide_cap) {
                 c = kClassWide;
             } else if (m <= p.huge_cap && B1 <= p.huge_max_B1 && bins <= 2 * p.huge_cap + 32) {

@@ -26,6 +26,7 @@ struct PrepParams {
     int64_t huge_max_B1;     // largest B_1 the global-memory kernel holds
     int64_t narrow_max_B;    // B_1 limit of the narrow slots
     int64_t narrow_bins;     // worst-case bins (2m + preopen n) the narrow classes accept
+    int64_t narrow_cap16;    // largest m the one-warp kernel's 16-bit slots take (B_1 <= 255; 0: none)
     int32_t preopen;
     int32_t* cls;            // [N]
     uint32_t* hist;          // [kClasses * kBuckets]

@@ -1,7 +1,8 @@
-"""The one-warp first-heuristic kernel (systems of at most 32768 bins, one
-warp each) against the oracle, element by element: every segment-register
-count it is built for, the BF residual index and the full-scan BF it uses
-when B_1 > 1023, the literal Rule 2 start, and the spill-and-rerun path."""
+"""The one-warp first-heuristic kernel (systems of at most 32768 bins, or
+65536 in 16-bit slots when B_1 <= 255, one warp each) against the oracle,
+element by element: every segment-register count it is built for, the BF
+residual index and the full-scan BF it uses when B_1 > 1023, the literal
+Rule 2 start, the 16-bit slot form, and the spill-and-rerun paths."""
 import numpy as np
 import pytest
 
@@ -113,9 +114,9 @@ def test_large_systems_routes():
     """Systems past the worst-case shared-memory size: held by the one-warp
     kernel when the slot estimate suffices (20k items of U[1,150]), spilled
     twice and finished in global memory when it does not (30k items that
-    each fill half a bin: two bins per item), and in global memory from the
-    start beyond the estimate's reach (45k items).  Results equal the
-    oracle's whatever the route."""
+    each fill half a bin: two bins per item), and in the one-warp kernel's
+    16-bit slots beyond the 32-bit estimate's reach (45k items, B_1 = 150).
+    Results equal the oracle's whatever the route."""
     rng = np.random.default_rng(71)
     B = np.array([150, 120, 100, 80, 50], dtype=np.int32)
     inst = [(rng.integers(1, 151, size=20_000).astype(np.int32), B),
@@ -127,3 +128,31 @@ def test_large_systems_routes():
         ref = run_oracle(b, 1, c, seed=7)
         assert_same(b, run_batch(b, 1, c, seed=7), ref, f"routes c{c}")
         assert_same(b, run_batch(b, 1, c, seed=7, plain=True), ref, f"routes plain c{c}")
+
+
+def test_sixteen_bit_slots():
+    """Systems with B_1 <= 255 past the 32-bit slots' reach (more than about
+    40.8k items) in the one-warp kernel's 16-bit slots (at most 65536 bins):
+    config-5-like requests of 60k and 100k items, B_1 = 255 exactly; one
+    system that needs a bin per item (every item fills more than half of the
+    largest bin) and leaves the 16-bit slots at once, and one that passes
+    65536 bins late (small items, then large ones): both finish in global
+    memory.  Every criterion; the literal Rule 2 start and the plain path
+    for BF.  Results equal the oracle's whatever the route."""
+    rng = np.random.default_rng(72)
+    B5 = np.array([150, 120, 100, 80, 50], dtype=np.int32)
+    late = np.concatenate([rng.integers(1, 21, size=30_000), rng.integers(129, 256, size=70_000)])
+    inst = [(rng.integers(1, 151, size=100_000).astype(np.int32), B5),
+            (I.mixture_weights(rng, 0.7, (1, 37), (75, 150), 60_000), B5),
+            (rng.integers(1, 256, size=50_000).astype(np.int32), np.array([255, 254, 17], dtype=np.int32)),
+            (rng.integers(129, 256, size=70_000).astype(np.int32), np.array([255, 200, 130], dtype=np.int32)),
+            (late.astype(np.int32), np.array([255, 130], dtype=np.int32)),
+            (rng.integers(1, 151, size=2_000).astype(np.int32), B5)]
+    b = I.from_instances(inst)
+    for c in CRITS:
+        ref = run_oracle(b, 1, c, seed=8)
+        assert_same(b, run_batch(b, 1, c, seed=8), ref, f"16-bit c{c}")
+        if c == native.BF:
+            assert_same(b, run_batch(b, 1, c, seed=8, plain=True), ref, f"16-bit plain c{c}")
+            assert_same(b, run_batch(b, 1, c, preopen=1, seed=8), run_oracle(b, 1, c, preopen=1, seed=8),
+                        f"16-bit preopen c{c}")
