@@ -219,19 +219,32 @@ __global__ void __launch_bounds__(32) kc_pack_kernel(const KCParams p) {
                     s[4 * k] = v4.x; s[4 * k + 1] = v4.y; s[4 * k + 2] = v4.z; s[4 * k + 3] = v4.w;
                 }
                 const uint32_t W16 = wj << 16;
-                uint32_t key = 0xFFFFFFFFu;
+                // BF / WF: the least and the second-least key of the tile (the
+                // second tells whether another bin has the chosen residual,
+                // and for WF the tile's next-largest residual)
+                uint32_t key = 0xFFFFFFFFu, sec = 0xFFFFFFFFu;
                 if (c == kFF) {
 #pragma unroll
                     for (int x = 4 * kTileQuadsPerLane - 1; x >= 0; --x)
                         if (s[x] >= W16) key = ((s[x] & 0xFFFFu) << 16) | (s[x] >> 16);
                 } else if (c == kWF) {
 #pragma unroll
-                    for (int x = 0; x < 4 * kTileQuadsPerLane; ++x) key = min(key, s[x] ^ 0xFFFF0000u);
+                    for (int x = 0; x < 4 * kTileQuadsPerLane; ++x) {
+                        const uint32_t v = s[x] ^ 0xFFFF0000u;
+                        sec = min(sec, max(key, v));
+                        key = min(key, v);
+                    }
                 } else {
 #pragma unroll
-                    for (int x = 0; x < 4 * kTileQuadsPerLane; ++x) key = min(key, s[x] - W16);
+                    for (int x = 0; x < 4 * kTileQuadsPerLane; ++x) {
+                        const uint32_t v = s[x] - W16;
+                        sec = min(sec, max(key, v));
+                        key = min(key, v);
+                    }
                 }
+                const uint32_t lane_key = key;
                 key = __reduce_min_sync(kFull, key);
+                const uint32_t key2 = c == kFF ? 0xFFFFFFFFu : __reduce_min_sync(kFull, lane_key == key ? sec : lane_key);
                 uint32_t low;
                 if (c == kFF) { low = key >> 16; r_old = key & 0xFFFFu; }
                 else if (c == kWF) { low = key & 0xFFFFu; r_old = 0xFFFFu - (key >> 16); }
@@ -248,7 +261,11 @@ __global__ void __launch_bounds__(32) kc_pack_kernel(const KCParams p) {
                 const uint32_t new_slot = (r_new << 16) | low;
                 const uint32_t old_max = W.tile_max[tile];
                 uint32_t mx = old_max;
-                if (r_old == old_max) {            // the chosen bin held the maximum
+                if (c == kWF) {
+                    // the chosen bin held the maximum: the new one is the
+                    // larger of its new residual and the next-largest
+                    mx = max(r_new, 0xFFFFu - (key2 >> 16));
+                } else if (r_old == old_max) {     // the chosen bin held the maximum
                     uint32_t top = 0;
 #pragma unroll
                     for (int x = 0; x < 4 * kTileQuadsPerLane; ++x) {
@@ -258,7 +275,9 @@ __global__ void __launch_bounds__(32) kc_pack_kernel(const KCParams p) {
                     mx = __reduce_max_sync(kFull, top) >> 16;
                 }
                 bool still = true;
-                if (W.track) {                      // does the tile still hold r_old?
+                if (W.track && c != kFF) {          // BF / WF keys order by residual
+                    still = (key2 >> 16) == (key >> 16);
+                } else if (W.track) {               // does the tile still hold r_old?
                     bool other = false;
 #pragma unroll
                     for (int x = 0; x < 4 * kTileQuadsPerLane; ++x)
