@@ -1122,12 +1122,12 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
     const int smalls[] = {0, 128, 512, 1024, 2048, 4096, 8192, 16384};
     const int wpb[] = {2, 4, 8, 16};
     const int chunks[] = {256, 512, 1024, 2048};
-    const int pcts[] = {80, 100, 130, 200};
+    const int pcts[] = {60, 70, 80, 100, 130, 200};
     for (int pass = 0; pass < 2; ++pass) {
         for (int knob = 0; knob < 5; ++knob) {
             const int* vals = knob == 0 ? warps : knob == 1 ? smalls : knob == 2 ? wpb
                               : knob == 3 ? chunks : pcts;
-            const int nv = knob == 0 ? 6 : knob == 1 ? 8 : 4;
+            const int nv = knob == 0 ? 6 : knob == 1 ? 8 : knob == 4 ? 6 : 4;
             for (int v = 0; v < nv; ++v) {
                 vsbpp_config c = cur;
                 if (knob == 0) c.large_warps = vals[v];
