@@ -348,9 +348,18 @@ def cpu_baseline(batch, sample_n: int, seed: int = 123):
         oracle.pack_many(sub.w_all, sub.w_off, sub.B_all, sub.B_off, h, c, s, 0, 0, nthreads=cores)
     dt = time.perf_counter() - t0
     items = 4 * sub.total_items
+    # one host thread, on the first quarter of the same sample
+    one = sub.subset(np.arange(max(1, len(idx) // 4)))
+    t1 = time.perf_counter()
+    for (_, h, c, s) in PASSES:
+        oracle.pack_many(one.w_all, one.w_off, one.B_all, one.B_off, h, c, s, 0, 0, nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": items / dt, "unit": "items/s", "cores": cores, "kind": "oracle",
             "sample": f"{len(idx)} of {batch.N} instances ({sub.total_items} items) x 4 passes "
-                      f"(H1 FF/BF/WF, H2 BF), {dt:.2f} s wall"}
+                      f"(H1 FF/BF/WF, H2 BF), {dt:.2f} s wall",
+            "one_core": {"value": 4 * one.total_items / dt1, "unit": "items/s", "cores": 1,
+                         "sample": f"{one.N} of those instances ({one.total_items} items) x 4 passes, "
+                                   f"{dt1:.2f} s"}}
 
 
 def run_reference(args, ws, rank):
