@@ -133,6 +133,26 @@ def test_server_results_alone_and_in_the_mix():
         assert a.total == m.total == ref.total
 
 
+def test_server_large_requests_in_the_mix():
+    """Requests across config 5's whole range: the largest (6*10^4 and 10^5
+    items, B_1 = 150) are packed in the one-warp kernel's 16-bit slots (or in
+    global memory if they outgrow them); all are submitted at once in
+    increasing size, so lanes grow their scratch while other requests are in
+    flight.  Each result equals the oracle's."""
+    rng = np.random.default_rng(56)
+    reqs = [I.config5_request(rng, r, 100, 20_000) for r in range(24)]
+    reqs += [I.config5_request(rng, 0, 60_000, 60_000), I.config5_request(rng, 1, 100_000, 100_000)]
+    reqs.sort(key=lambda x: len(x[0]))
+    with native.Server(device_mem_budget=256 << 20, max_slots=16, lanes=4) as srv:
+        tickets = [srv.submit(w, B, 1, 1) for (w, B) in reqs]
+        got = [srv.poll(t) for t in tickets]
+    for (w, B), (rc, res) in zip(reqs, got):
+        ref = oracle.pack(w, B, 1, 1)
+        assert rc == 0 and res.total == ref.total, len(w)
+        assert res.bin_of_item.tobytes() == ref.bin_of_item.tobytes(), len(w)
+        assert res.bin_type.tobytes() == ref.bin_type.tobytes(), len(w)
+
+
 def test_server_concurrent_submitters_and_errors():
     rng = np.random.default_rng(9)
     with native.Server(device_mem_budget=8 << 20, max_slots=4, lanes=2) as srv:
