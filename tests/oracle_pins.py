@@ -13,8 +13,8 @@ mathematics fixes:
     different form (no empty bins, no division rule);
   * the exact optimum from an independent set-partition enumeration, and
     heuristic >= optimum;
-  * closed forms: a single item costs min{B_i >= w}; m items of weight B_1
-    cost m*B_1;
+  * closed forms: a single item costs min{B_i >= w} (also when w equals a
+    capacity); m items of weight B_1 cost m*B_1;
   * the second heuristic equals the cheapest permutation, enumerated here with
     itertools (Section 6.4);
   * invariants of any packing (each item once, no bin over capacity, total =
@@ -204,6 +204,10 @@ def pin_closed_forms(lib, seed=13):
                 r = lib.pack([x], B, h, crit, 0, 0, t)
                 assert r.total == want and r.num_bins == 1
                 assert r.bin_type.tolist() == [B.index(want)]
+        # an item exactly as heavy as a capacity takes a bin of that type
+        i = int(rng.integers(0, n))
+        r = lib.pack([B[i]], B, 1, int(rng.integers(0, 3)))
+        assert r.total == B[i] and r.bin_type.tolist() == [i]
         m = int(rng.integers(1, 30))
         r = lib.pack([B[0]] * m, B, 1, int(rng.integers(0, 3)))
         assert r.total == m * B[0] and r.num_bins == m

@@ -57,6 +57,12 @@ MUTANTS = {
                              "for (int32_t i = 0; i < n; ++i) {"),
     "total_counts_loads": ("sum += B[bins[x].type];", "sum += bins[x].load;"),
     "fit_tests_off_by_one": ("or_fit_tests += (uint64_t)nb;", "or_fit_tests += (uint64_t)nb + 1;"),
+    "ff_last_fitting": ('            if (chosen < 0 ||\n                (c == OR_BF && res < chosen_res) ||\n                (c == OR_WF && res > chosen_res)) {\n                chosen = x;\n                chosen_res = res;\n            }\n            if (c == OR_FF)\n                break;\n',
+                        '            if (chosen < 0 || c == OR_FF ||\n                (c == OR_BF && res < chosen_res) ||\n                (c == OR_WF && res > chosen_res)) {\n                chosen = x;\n                chosen_res = res;\n            }\n'),
+    "rule5_every_item_past_half": ("if (2 * before < cap && cap <= 2 * after) {", "if (cap <= 2 * after) {"),
+    "fallback_strict_capacity": ("if (B[i] >= w)\n                    t = i;",
+                                 "if (B[i] > w)\n                    t = i;"),
+    "last_partial_sublist_dropped": ("for (int64_t g = 0; g * s < m; ++g) {", "for (int64_t g = 0; (g + 1) * s <= m; ++g) {"),
 }
 
 
