@@ -7,7 +7,8 @@ mathematics fixes:
   * hand-worked packings (tests/golden/hand_examples.json, traced by hand from
     Section 6.3 Rules 2-6, Section 6.4 and the FF/BF/WF definitions of
     Section 1);
-  * the published SplitMix64 test vectors (RANDOM criterion, Rule 3);
+  * the published SplitMix64 test vectors (RANDOM criterion, Rule 3), both
+    as raw outputs and through the criterion each one gives an item;
   * with one bin type (n = 1, classical bin packing, Section 1), FF and BF
     reduce to the textbook First-Fit and Best-Fit written out below in a
     different form (no empty bins, no division rule);
@@ -162,6 +163,28 @@ def pin_splitmix64(lib):
         assert lib.splitmix64(d["seed"], k) == int(v)
 
 
+def pin_random_criterion_vectors(lib):
+    """RANDOM (Rule 3 with the criterion drawn per item, reading G12: item j
+    of the instance takes criterion SplitMix64(seed, j) mod 3, 0 = FF, 1 = BF,
+    2 = WF) against the published SplitMix64 outputs for seed 1234567, read
+    off the packing itself.  With one type of capacity 100, the items
+    [100] * (p - 2) + [60, 80] are placed the same way under every criterion
+    (each fits only the empty bin the previous one divided off) and leave
+    bins with room 40 (dense id p - 2), 20 (p - 1) and an empty one (p);
+    item p = 15 then goes to p - 2 under FF, p - 1 under BF and p under WF.
+    After [60] alone (room 40, and an empty bin) an item of 30 separates WF
+    from FF / BF."""
+    d = load_golden("splitmix64_vectors.json")
+    seed = int(d["seed"])
+    crit = [int(x) % 3 for x in d["outputs"]]
+    for p in (2, 3, 4):
+        r = lib.pack([100] * (p - 2) + [60, 80, 15], [100], 1, 3, 0, 0, seed)
+        assert r.status == 0
+        assert int(r.bin_of_item[p]) == p - 2 + crit[p], (p, crit[p], r.bin_of_item.tolist())
+    r = lib.pack([60, 30], [100], 1, 3, 0, 0, seed)
+    assert int(r.bin_of_item[1]) == (1 if crit[1] == 2 else 0), (crit[1], r.bin_of_item.tolist())
+
+
 def pin_textbook_n1(lib, trials=150, seed=11):
     rng = np.random.default_rng(seed)
     for t in range(trials):
@@ -305,7 +328,7 @@ def pin_fit_tests(lib, seed=16):
     assert lib.fit_tests([5], [5, 3], 1, 1, 0, 1) == 2
 
 
-ALL_PINS = [pin_hand_examples, pin_splitmix64, pin_textbook_n1, pin_optimum,
+ALL_PINS = [pin_hand_examples, pin_splitmix64, pin_random_criterion_vectors, pin_textbook_n1, pin_optimum,
             pin_closed_forms, pin_h2_is_best_permutation, pin_invariants, pin_errors,
             pin_fit_tests]
 

@@ -62,6 +62,10 @@ MUTANTS = {
     "rule5_every_item_past_half": ("if (2 * before < cap && cap <= 2 * after) {", "if (cap <= 2 * after) {"),
     "fallback_strict_capacity": ("if (B[i] >= w)\n                    t = i;",
                                  "if (B[i] > w)\n                    t = i;"),
+    "permutations_suffix_not_reversed": ("    for (int32_t a = i + 1, b = k - 1; a < b; ++a, --b) {\n        t = p[a]; p[a] = p[b]; p[b] = t;\n    }\n",
+                                         ""),
+    "random_criterion_mapping": ("return (int32_t)(oracle_splitmix64(seed, key) % 3u);",
+                                 "return (int32_t)((oracle_splitmix64(seed, key) >> 1) % 3u);"),
     "last_partial_sublist_dropped": ("for (int64_t g = 0; g * s < m; ++g) {", "for (int64_t g = 0; (g + 1) * s <= m; ++g) {"),
 }
 
