@@ -66,6 +66,11 @@ MUTANTS = {
                                          ""),
     "random_criterion_mapping": ("return (int32_t)(oracle_splitmix64(seed, key) % 3u);",
                                  "return (int32_t)((oracle_splitmix64(seed, key) >> 1) % 3u);"),
+    "zero_weight_accepted": ("if (w[j] < 1)\n            return OR_EINVAL;", "if (w[j] < 0)\n            return OR_EINVAL;"),
+    "equal_capacities_accepted": ("if (i > 0 && B[i] >= B[i - 1])", "if (i > 0 && B[i] > B[i - 1])"),
+    "h2_types_of_last_permutation": ("                    best_used = used;\n", "                    best_used = used;\n                }\n                {\n"),
+    "rule5_strictly_past_half": ("if (2 * before < cap && cap <= 2 * after) {", "if (2 * before < cap && cap < 2 * after) {"),
+    "preopen_all_largest_type": ("bins[nb].type = i;\n            ++nb;", "bins[nb].type = 0;\n            ++nb;"),
     "last_partial_sublist_dropped": ("for (int64_t g = 0; g * s < m; ++g) {", "for (int64_t g = 0; (g + 1) * s <= m; ++g) {"),
 }
 
