@@ -771,24 +771,28 @@ int check_instance_args(int64_t m, int32_t n, const void* w, const void* B) {
 int batch_common(int64_t N, const int32_t* w_all, const int64_t* w_off, const int32_t* B_all,
                  const int32_t* B_off, int64_t max_m, const vsbpp_params* p, int32_t* boi,
                  int32_t* bt, int64_t* nb, int64_t* tot, int32_t* status, void* stream, bool plain) {
-    if (N < 0 || max_m < 0) return VSBPP_EINVAL;
-    if (N == 0) return VSBPP_OK;
-    if (!w_off || !B_all || !B_off || !nb || !tot || !status || !boi || !bt) return VSBPP_EINVAL;
-    int rc = check_params(p);
-    if (rc) return rc;
-    const vsbpp_params prm = defaults(p);
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
-    LaunchPlan lp;
-    if ((rc = build_plan(prm, max_m, N, lp))) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Scratch& sc = scratch_for(st);
-    // sublist scratch is sized from the host-side bound N * max_m, so the call
-    // never has to read the device offsets back
-    const int64_t total_m = lp.mode.compose ? N * std::max<int64_t>(max_m, 1) : 0;
-    if ((rc = ensure_scratch(sc, lp, N, total_m))) return rc;
-    BatchView in{N, w_all, w_off, 0, B_all, B_off, 0};
-    OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
-    return enqueue(lp, sc, in, out, prm, plain, st);
+    try {
+        if (N < 0 || max_m < 0) return VSBPP_EINVAL;
+        if (N == 0) return VSBPP_OK;
+        if (!w_off || !B_all || !B_off || !nb || !tot || !status || !boi || !bt) return VSBPP_EINVAL;
+        int rc = check_params(p);
+        if (rc) return rc;
+        const vsbpp_params prm = defaults(p);
+        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        LaunchPlan lp;
+        if ((rc = build_plan(prm, max_m, N, lp))) return rc;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        Scratch& sc = scratch_for(st);
+        // sublist scratch is sized from the host-side bound N * max_m, so the call
+        // never has to read the device offsets back
+        const int64_t total_m = lp.mode.compose ? N * std::max<int64_t>(max_m, 1) : 0;
+        if ((rc = ensure_scratch(sc, lp, N, total_m))) return rc;
+        BatchView in{N, w_all, w_off, 0, B_all, B_off, 0};
+        OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
+        return enqueue(lp, sc, in, out, prm, plain, st);
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
+    }
 }
 
 // A recorded batch shape (vsbpp_plan_*).
@@ -871,60 +875,68 @@ int vsbpp_last_cuda_error(void) { return g_last_cuda.load(); }
 int vsbpp_pack_device(const int32_t* w, int64_t m, const int32_t* B, int32_t n, const vsbpp_params* p,
                       int32_t* bin_of_item, int32_t* bin_type, int64_t* num_bins,
                       int64_t* total_capacity, int32_t* status, void* stream) {
-    int rc = check_instance_args(m, n, w, B);
-    if (rc) return rc;
-    if (!num_bins || !total_capacity || !status || (m > 0 && (!bin_of_item || !bin_type)))
-        return VSBPP_EINVAL;
-    if ((rc = check_params(p))) return rc;
-    const vsbpp_params prm = defaults(p);
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
-    LaunchPlan lp;
-    if ((rc = build_plan(prm, std::max<int64_t>(m, 1), 1, lp))) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Scratch& sc = scratch_for(st);
-    if ((rc = ensure_scratch(sc, lp, 1, m))) return rc;
-    BatchView in{1, w, nullptr, m, B, nullptr, n};
-    OutView out{bin_of_item, bin_type, num_bins, total_capacity, status, nullptr, nullptr, nullptr};
-    return enqueue(lp, sc, in, out, prm, false, st);
+    try {
+        int rc = check_instance_args(m, n, w, B);
+        if (rc) return rc;
+        if (!num_bins || !total_capacity || !status || (m > 0 && (!bin_of_item || !bin_type)))
+            return VSBPP_EINVAL;
+        if ((rc = check_params(p))) return rc;
+        const vsbpp_params prm = defaults(p);
+        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        LaunchPlan lp;
+        if ((rc = build_plan(prm, std::max<int64_t>(m, 1), 1, lp))) return rc;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        Scratch& sc = scratch_for(st);
+        if ((rc = ensure_scratch(sc, lp, 1, m))) return rc;
+        BatchView in{1, w, nullptr, m, B, nullptr, n};
+        OutView out{bin_of_item, bin_type, num_bins, total_capacity, status, nullptr, nullptr, nullptr};
+        return enqueue(lp, sc, in, out, prm, false, st);
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
+    }
 }
 
 int vsbpp_pack(const int32_t* w, int64_t m, const int32_t* B, int32_t n, const vsbpp_params* p,
                int32_t* bin_of_item, int32_t* bin_type, int64_t* num_bins, int64_t* total_capacity) {
-    int rc = check_instance_args(m, n, w, B);
-    if (rc) return rc;
-    if (!num_bins || !total_capacity || (m > 0 && (!bin_of_item || !bin_type))) return VSBPP_EINVAL;
-    if ((rc = check_params(p))) return rc;
-    *num_bins = 0;
-    *total_capacity = 0;
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
-    static cudaStream_t own = nullptr;
-    if (!own) VS_TRY(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-    Scratch& sc = scratch_for(own);
-    if ((rc = sc.grow(sc.h_w, sc.cap_h_w, m))) return rc;
-    if ((rc = sc.grow(sc.h_B, sc.cap_h_B, n))) return rc;
-    if ((rc = sc.grow(sc.h_boi, sc.cap_h_boi, m))) return rc;
-    if ((rc = sc.grow(sc.h_bt, sc.cap_h_bt, m))) return rc;
-    if ((rc = sc.grow(sc.h_small, sc.cap_h_small, 3))) return rc;
-    if (m > 0) VS_TRY(cudaMemcpyAsync(sc.h_w, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, own));
-    VS_TRY(cudaMemcpyAsync(sc.h_B, B, sizeof(int32_t) * n, cudaMemcpyHostToDevice, own));
-    int32_t* d_status = reinterpret_cast<int32_t*>(sc.h_small + 2);
-    rc = vsbpp_pack_device(sc.h_w, m, sc.h_B, n, p, sc.h_boi, sc.h_bt, sc.h_small, sc.h_small + 1,
-                           d_status, own);
-    if (rc) return rc;
-    int64_t small[3] = {0, 0, 0};
-    VS_TRY(cudaMemcpyAsync(small, sc.h_small, sizeof(small), cudaMemcpyDeviceToHost, own));
-    VS_TRY(cudaStreamSynchronize(own));
-    const int32_t st = static_cast<int32_t>(small[2] & 0xFFFFFFFF);
-    if (st != VSBPP_OK) return st;
-    if (m > 0) {
-        VS_TRY(cudaMemcpyAsync(bin_of_item, sc.h_boi, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, own));
-        if (small[0] > 0)
-            VS_TRY(cudaMemcpyAsync(bin_type, sc.h_bt, sizeof(int32_t) * small[0], cudaMemcpyDeviceToHost, own));
+    try {
+        int rc = check_instance_args(m, n, w, B);
+        if (rc) return rc;
+        if (!num_bins || !total_capacity || (m > 0 && (!bin_of_item || !bin_type))) return VSBPP_EINVAL;
+        if ((rc = check_params(p))) return rc;
+        *num_bins = 0;
+        *total_capacity = 0;
+        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        static cudaStream_t own = nullptr;
+        if (!own) VS_TRY(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+        Scratch& sc = scratch_for(own);
+        if ((rc = sc.grow(sc.h_w, sc.cap_h_w, m))) return rc;
+        if ((rc = sc.grow(sc.h_B, sc.cap_h_B, n))) return rc;
+        if ((rc = sc.grow(sc.h_boi, sc.cap_h_boi, m))) return rc;
+        if ((rc = sc.grow(sc.h_bt, sc.cap_h_bt, m))) return rc;
+        if ((rc = sc.grow(sc.h_small, sc.cap_h_small, 3))) return rc;
+        if (m > 0) VS_TRY(cudaMemcpyAsync(sc.h_w, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, own));
+        VS_TRY(cudaMemcpyAsync(sc.h_B, B, sizeof(int32_t) * n, cudaMemcpyHostToDevice, own));
+        int32_t* d_status = reinterpret_cast<int32_t*>(sc.h_small + 2);
+        rc = vsbpp_pack_device(sc.h_w, m, sc.h_B, n, p, sc.h_boi, sc.h_bt, sc.h_small, sc.h_small + 1,
+                               d_status, own);
+        if (rc) return rc;
+        int64_t small[3] = {0, 0, 0};
+        VS_TRY(cudaMemcpyAsync(small, sc.h_small, sizeof(small), cudaMemcpyDeviceToHost, own));
         VS_TRY(cudaStreamSynchronize(own));
+        const int32_t st = static_cast<int32_t>(small[2] & 0xFFFFFFFF);
+        if (st != VSBPP_OK) return st;
+        if (m > 0) {
+            VS_TRY(cudaMemcpyAsync(bin_of_item, sc.h_boi, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, own));
+            if (small[0] > 0)
+                VS_TRY(cudaMemcpyAsync(bin_type, sc.h_bt, sizeof(int32_t) * small[0], cudaMemcpyDeviceToHost, own));
+            VS_TRY(cudaStreamSynchronize(own));
+        }
+        *num_bins = small[0];
+        *total_capacity = small[1];
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
-    *num_bins = small[0];
-    *total_capacity = small[1];
-    return VSBPP_OK;
 }
 
 int vsbpp_pack_batch(int64_t N, const int32_t* w_all, const int64_t* w_off, const int32_t* B_all,
@@ -983,21 +995,25 @@ int vsbpp_kernel_timing_enable(int enable) {
 }
 
 int vsbpp_kernel_timing_read(float* ms, int32_t max, int32_t* count) {
-    if (!count || max < 0 || (max > 0 && !ms)) return VSBPP_EINVAL;
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
-    *count = 0;
-    const int have = g_timing.count;
-    const int first = (g_timing.head - have + KernelTiming::kRing) % KernelTiming::kRing;
-    for (int x = 0; x < have && x < max; ++x) {
-        auto& pr = g_timing.ev[(first + x) % KernelTiming::kRing];
-        VS_TRY(cudaEventSynchronize(pr[1]));
-        float t = 0.f;
-        VS_TRY(cudaEventElapsedTime(&t, pr[0], pr[1]));
-        ms[x] = t;
-        ++*count;
+    try {
+        if (!count || max < 0 || (max > 0 && !ms)) return VSBPP_EINVAL;
+        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        *count = 0;
+        const int have = g_timing.count;
+        const int first = (g_timing.head - have + KernelTiming::kRing) % KernelTiming::kRing;
+        for (int x = 0; x < have && x < max; ++x) {
+            auto& pr = g_timing.ev[(first + x) % KernelTiming::kRing];
+            VS_TRY(cudaEventSynchronize(pr[1]));
+            float t = 0.f;
+            VS_TRY(cudaEventElapsedTime(&t, pr[0], pr[1]));
+            ms[x] = t;
+            ++*count;
+        }
+        g_timing.count = 0;
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
-    g_timing.count = 0;
-    return VSBPP_OK;
 }
 
 int vsbpp_get_config(vsbpp_config* out) {
@@ -1022,71 +1038,79 @@ int vsbpp_set_config(const vsbpp_config* cfg) {
 
 int vsbpp_plan_create(int64_t N, int64_t total_m, int64_t max_m, const vsbpp_params* p,
                       vsbpp_plan** out) {
-    if (!out) return VSBPP_EINVAL;
-    *out = nullptr;
-    if (N < 0 || total_m < 0 || max_m < 0) return VSBPP_EINVAL;
-    int rc = check_params(p);
-    if (rc) return rc;
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
-    PlanImpl* pl = new (std::nothrow) PlanImpl();
-    if (!pl) return VSBPP_ENOMEM;
-    pl->N = N;
-    pl->total_m = total_m;
-    pl->max_m = max_m;
-    pl->prm = defaults(p);
-    if ((rc = build_plan(pl->prm, max_m, N, pl->lp)) ||
-        (rc = ensure_scratch(pl->sc, pl->lp, N, std::max<int64_t>(total_m, 1))) ||
-        (rc = record(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking)))) {
-        pl->sc.release();
-        delete pl;
-        return rc;
+    try {
+        if (!out) return VSBPP_EINVAL;
+        *out = nullptr;
+        if (N < 0 || total_m < 0 || max_m < 0) return VSBPP_EINVAL;
+        int rc = check_params(p);
+        if (rc) return rc;
+        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        PlanImpl* pl = new (std::nothrow) PlanImpl();
+        if (!pl) return VSBPP_ENOMEM;
+        pl->N = N;
+        pl->total_m = total_m;
+        pl->max_m = max_m;
+        pl->prm = defaults(p);
+        if ((rc = build_plan(pl->prm, max_m, N, pl->lp)) ||
+            (rc = ensure_scratch(pl->sc, pl->lp, N, std::max<int64_t>(total_m, 1))) ||
+            (rc = record(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking)))) {
+            pl->sc.release();
+            delete pl;
+            return rc;
+        }
+        *out = reinterpret_cast<vsbpp_plan*>(pl);
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
-    *out = reinterpret_cast<vsbpp_plan*>(pl);
-    return VSBPP_OK;
 }
 
 int vsbpp_plan_run(vsbpp_plan* plan, const int32_t* w_all, const int64_t* w_off, const int32_t* B_all,
                    const int32_t* B_off, int32_t* boi, int32_t* bt, int64_t* nb, int64_t* tot,
                    int32_t* status, void* stream) {
-    if (!plan) return VSBPP_EINVAL;
-    PlanImpl* pl = reinterpret_cast<PlanImpl*>(plan);
-    if (pl->N == 0) return VSBPP_OK;
-    if (!w_off || !B_all || !B_off || !boi || !bt || !nb || !tot || !status) return VSBPP_EINVAL;
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
-    cudaStream_t ust = static_cast<cudaStream_t>(stream);
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    VS_TRY(cudaStreamIsCapturing(ust, &cs));
-    if (cs == cudaStreamCaptureStatusActive) {
-        // The caller is recording its own graph: put the launches straight into
-        // it (everything is pre-allocated, so nothing here allocates).
-        BatchView in{pl->N, w_all, w_off, 0, B_all, B_off, 0};
-        OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
-        return enqueue(pl->lp, pl->sc, in, out, pl->prm, false, ust);
-    }
-    const void* key[10] = {w_all, w_off, B_all, B_off, boi, bt, nb, tot, status, nullptr};
-    if (!pl->exec || std::memcmp(key, pl->key, sizeof(key)) != 0) {
-        BatchView in{pl->N, w_all, w_off, 0, B_all, B_off, 0};
-        OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
-        cudaGraph_t g = nullptr;
-        VS_TRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeRelaxed));
-        const int rc = enqueue(pl->lp, pl->sc, in, out, pl->prm, false, pl->cap);
-        const cudaError_t ce = cudaStreamEndCapture(pl->cap, &g);
-        if (rc != VSBPP_OK) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
+    try {
+        if (!plan) return VSBPP_EINVAL;
+        PlanImpl* pl = reinterpret_cast<PlanImpl*>(plan);
+        if (pl->N == 0) return VSBPP_OK;
+        if (!w_off || !B_all || !B_off || !boi || !bt || !nb || !tot || !status) return VSBPP_EINVAL;
+        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        cudaStream_t ust = static_cast<cudaStream_t>(stream);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        VS_TRY(cudaStreamIsCapturing(ust, &cs));
+        if (cs == cudaStreamCaptureStatusActive) {
+            // The caller is recording its own graph: put the launches straight into
+            // it (everything is pre-allocated, so nothing here allocates).
+            BatchView in{pl->N, w_all, w_off, 0, B_all, B_off, 0};
+            OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
+            return enqueue(pl->lp, pl->sc, in, out, pl->prm, false, ust);
         }
-        VS_TRY(ce);
-        cudaGraphExec_t ex = nullptr;
-        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
-        cudaGraphDestroy(g);
-        VS_TRY(ie);
-        if (pl->exec) cudaGraphExecDestroy(pl->exec);
-        pl->exec = ex;
-        std::memcpy(pl->key, key, sizeof(key));
-        ++pl->graphs_recorded;
+        const void* key[10] = {w_all, w_off, B_all, B_off, boi, bt, nb, tot, status, nullptr};
+        if (!pl->exec || std::memcmp(key, pl->key, sizeof(key)) != 0) {
+            BatchView in{pl->N, w_all, w_off, 0, B_all, B_off, 0};
+            OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
+            cudaGraph_t g = nullptr;
+            VS_TRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeRelaxed));
+            const int rc = enqueue(pl->lp, pl->sc, in, out, pl->prm, false, pl->cap);
+            const cudaError_t ce = cudaStreamEndCapture(pl->cap, &g);
+            if (rc != VSBPP_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            VS_TRY(ce);
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            VS_TRY(ie);
+            if (pl->exec) cudaGraphExecDestroy(pl->exec);
+            pl->exec = ex;
+            std::memcpy(pl->key, key, sizeof(key));
+            ++pl->graphs_recorded;
+        }
+        VS_TRY(cudaGraphLaunch(pl->exec, ust));
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
-    VS_TRY(cudaGraphLaunch(pl->exec, ust));
-    return VSBPP_OK;
 }
 
 int vsbpp_plan_destroy(vsbpp_plan* plan) {
@@ -1105,53 +1129,57 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
                    const int32_t* B_off, int64_t max_m, const vsbpp_params* p, int32_t* boi,
                    int32_t* bt, int64_t* nb, int64_t* tot, int32_t* status, void* stream,
                    vsbpp_config* best, double* best_ms) {
-    if (N <= 0 || !w_off || !B_all || !B_off || !boi || !bt || !nb || !tot || !status)
-        return VSBPP_EINVAL;
-    int rc = check_params(p);
-    if (rc) return rc;
-    const vsbpp_params prm = defaults(p);
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // Coordinate descent over the four knobs, starting from the current table.
-    vsbpp_config cur = g_cfg;
-    double cur_ms = 0;
-    if ((rc = time_config(cur, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb, tot, status,
-                          st, 3, &cur_ms)))
-        return rc;
-    const int warps[] = {1, 2, 4, 8, 16, 32};
-    const int smalls[] = {0, 128, 512, 1024, 2048, 4096, 8192, 16384};
-    const int wpb[] = {2, 4, 8, 16};
-    const int chunks[] = {256, 512, 1024, 2048};
-    const int pcts[] = {60, 70, 80, 100, 130, 200};
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int knob = 0; knob < 5; ++knob) {
-            const int* vals = knob == 0 ? warps : knob == 1 ? smalls : knob == 2 ? wpb
-                              : knob == 3 ? chunks : pcts;
-            const int nv = knob == 0 ? 6 : knob == 1 ? 8 : knob == 4 ? 6 : 4;
-            for (int v = 0; v < nv; ++v) {
-                vsbpp_config c = cur;
-                if (knob == 0) c.large_warps = vals[v];
-                if (knob == 1) c.small_m = vals[v];
-                if (knob == 2) c.small_warps_per_block = vals[v];
-                if (knob == 3) c.chunk = vals[v];
-                if (knob == 4) c.slot_pct = vals[v];
-                if (std::memcmp(&c, &cur, sizeof(c)) == 0) continue;
-                double ms = 0;
-                const int r2 = time_config(c, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb,
-                                           tot, status, st, 3, &ms);
-                if (r2 == VSBPP_ECAPACITY) continue;   // shape does not fit this batch
-                if (r2) return r2;
-                if (ms < cur_ms) {
-                    cur = c;
-                    cur_ms = ms;
+    try {
+        if (N <= 0 || !w_off || !B_all || !B_off || !boi || !bt || !nb || !tot || !status)
+            return VSBPP_EINVAL;
+        int rc = check_params(p);
+        if (rc) return rc;
+        const vsbpp_params prm = defaults(p);
+        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        // Coordinate descent over the four knobs, starting from the current table.
+        vsbpp_config cur = g_cfg;
+        double cur_ms = 0;
+        if ((rc = time_config(cur, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb, tot, status,
+                              st, 3, &cur_ms)))
+            return rc;
+        const int warps[] = {1, 2, 4, 8, 16, 32};
+        const int smalls[] = {0, 128, 512, 1024, 2048, 4096, 8192, 16384};
+        const int wpb[] = {2, 4, 8, 16};
+        const int chunks[] = {256, 512, 1024, 2048};
+        const int pcts[] = {60, 70, 80, 100, 130, 200};
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int knob = 0; knob < 5; ++knob) {
+                const int* vals = knob == 0 ? warps : knob == 1 ? smalls : knob == 2 ? wpb
+                                  : knob == 3 ? chunks : pcts;
+                const int nv = knob == 0 ? 6 : knob == 1 ? 8 : knob == 4 ? 6 : 4;
+                for (int v = 0; v < nv; ++v) {
+                    vsbpp_config c = cur;
+                    if (knob == 0) c.large_warps = vals[v];
+                    if (knob == 1) c.small_m = vals[v];
+                    if (knob == 2) c.small_warps_per_block = vals[v];
+                    if (knob == 3) c.chunk = vals[v];
+                    if (knob == 4) c.slot_pct = vals[v];
+                    if (std::memcmp(&c, &cur, sizeof(c)) == 0) continue;
+                    double ms = 0;
+                    const int r2 = time_config(c, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb,
+                                               tot, status, st, 3, &ms);
+                    if (r2 == VSBPP_ECAPACITY) continue;   // shape does not fit this batch
+                    if (r2) return r2;
+                    if (ms < cur_ms) {
+                        cur = c;
+                        cur_ms = ms;
+                    }
                 }
             }
         }
+        g_cfg = cur;
+        if (best) *best = cur;
+        if (best_ms) *best_ms = cur_ms;
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
-    g_cfg = cur;
-    if (best) *best = cur;
-    if (best_ms) *best_ms = cur_ms;
-    return VSBPP_OK;
 }
 
 int vsbpp_tune_save(const char* path) {

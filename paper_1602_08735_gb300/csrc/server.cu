@@ -240,154 +240,170 @@ extern "C" {
 
 int vsbpp_server_create(size_t device_mem_budget, int32_t max_slots, int32_t lanes, int32_t max_queued,
                         vsbpp_server** out) {
-    if (!out) return VSBPP_EINVAL;
-    *out = nullptr;
-    if (device_mem_budget == 0 || max_slots < 1 || lanes < 1 || lanes > 64 || max_queued < 1)
-        return VSBPP_EINVAL;
-    vsbpp_server* s = new (std::nothrow) vsbpp_server();
-    if (!s) return VSBPP_ENOMEM;
-    s->budget = device_mem_budget;
-    s->max_slots = max_slots;
-    s->nlanes = lanes;
-    s->max_queued = max_queued;
-    cudaGetDevice(&s->device);
-    cudaMemPoolProps props;
-    std::memset(&props, 0, sizeof(props));
-    props.allocType = cudaMemAllocationTypePinned;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = s->device;
-    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
-        delete s;
-        return VSBPP_ECUDA;
-    }
-    uint64_t keep = device_mem_budget;
-    int no = 0;
-    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
-    for (int i = 0; i < lanes; ++i) {
-        cudaStream_t st = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-            for (cudaStream_t x : s->lanes) cudaStreamDestroy(x);
-            cudaMemPoolDestroy(s->pool);
+    try {
+        if (!out) return VSBPP_EINVAL;
+        *out = nullptr;
+        if (device_mem_budget == 0 || max_slots < 1 || lanes < 1 || lanes > 64 || max_queued < 1)
+            return VSBPP_EINVAL;
+        vsbpp_server* s = new (std::nothrow) vsbpp_server();
+        if (!s) return VSBPP_ENOMEM;
+        s->budget = device_mem_budget;
+        s->max_slots = max_slots;
+        s->nlanes = lanes;
+        s->max_queued = max_queued;
+        cudaGetDevice(&s->device);
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = s->device;
+        if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
             delete s;
             return VSBPP_ECUDA;
         }
-        s->lanes.push_back(st);
+        uint64_t keep = device_mem_budget;
+        int no = 0;
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+        for (int i = 0; i < lanes; ++i) {
+            cudaStream_t st = nullptr;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                for (cudaStream_t x : s->lanes) cudaStreamDestroy(x);
+                cudaMemPoolDestroy(s->pool);
+                delete s;
+                return VSBPP_ECUDA;
+            }
+            s->lanes.push_back(st);
+        }
+        s->lane_items.assign(static_cast<size_t>(lanes), 0);
+        s->worker = std::thread(worker_main, s);
+        *out = s;
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
-    s->lane_items.assign(static_cast<size_t>(lanes), 0);
-    s->worker = std::thread(worker_main, s);
-    *out = s;
-    return VSBPP_OK;
 }
 
 int vsbpp_server_submit(vsbpp_server* s, const int32_t* w, int64_t m, const int32_t* B, int32_t n,
                         const vsbpp_params* p, uint64_t* ticket) {
-    if (!s || !ticket || !B || m < 0 || (m > 0 && !w) || n < 1 || n > VSBPP_MAX_TYPES)
-        return VSBPP_EINVAL;
-    if (p && (p->reserved != 0 || p->heuristic < VSBPP_H1 || p->heuristic > VSBPP_H2 ||
-              p->criterion < VSBPP_FF || p->criterion > VSBPP_RANDOM || (p->preopen & ~1) ||
-              p->sublist_size < 0 || (p->heuristic == VSBPP_H2 && p->sublist_size > VSBPP_H2_MAX_SUBLIST)))
-        return VSBPP_EINVAL;
-    const size_t need = request_bytes(m, n);
-    if (need > s->budget) return VSBPP_ECAPACITY;
-    {
+    try {
+        if (!s || !ticket || !B || m < 0 || (m > 0 && !w) || n < 1 || n > VSBPP_MAX_TYPES)
+            return VSBPP_EINVAL;
+        if (p && (p->reserved != 0 || p->heuristic < VSBPP_H1 || p->heuristic > VSBPP_H2 ||
+                  p->criterion < VSBPP_FF || p->criterion > VSBPP_RANDOM || (p->preopen & ~1) ||
+                  p->sublist_size < 0 || (p->heuristic == VSBPP_H2 && p->sublist_size > VSBPP_H2_MAX_SUBLIST)))
+            return VSBPP_EINVAL;
+        const size_t need = request_bytes(m, n);
+        if (need > s->budget) return VSBPP_ECAPACITY;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (static_cast<int>(s->waiting.size()) >= s->max_queued) return VSBPP_EBUSY;
+        }
+        Req* r = new (std::nothrow) Req();
+        if (!r) return VSBPP_ENOMEM;
+        r->srv = s;
+        r->m = m;
+        r->n = n;
+        std::memset(&r->prm, 0, sizeof(r->prm));
+        r->prm.heuristic = VSBPP_H1;
+        r->prm.criterion = VSBPP_BF;
+        if (p) r->prm = *p;
+        r->need = need;
+        r->in_bytes = 4 * (static_cast<size_t>(m) + static_cast<size_t>(n));
+        r->out_bytes = align256(8 * static_cast<size_t>(std::max<int64_t>(m, 1))) + 64;
+        r->h_in = static_cast<int32_t*>(s->pinned.get(r->in_bytes));
+        r->h_out = static_cast<int32_t*>(s->pinned.get(r->out_bytes));
+        if (!r->h_in || !r->h_out) {
+            release_req(s, r);
+            return VSBPP_ENOMEM;
+        }
+        if (m > 0) std::memcpy(r->h_in, w, 4 * static_cast<size_t>(m));
+        std::memcpy(r->h_in + m, B, 4 * static_cast<size_t>(n));
         std::lock_guard<std::mutex> lk(s->mu);
-        if (static_cast<int>(s->waiting.size()) >= s->max_queued) return VSBPP_EBUSY;
+        if (static_cast<int>(s->waiting.size()) >= s->max_queued) {
+            release_req(s, r);
+            return VSBPP_EBUSY;
+        }
+        r->ticket = s->next_ticket++;
+        r->t_submit = Clock::now();
+        s->tickets[r->ticket] = r;
+        s->waiting.push_back(r);
+        s->cv.notify_all();
+        *ticket = r->ticket;
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
-    Req* r = new (std::nothrow) Req();
-    if (!r) return VSBPP_ENOMEM;
-    r->srv = s;
-    r->m = m;
-    r->n = n;
-    std::memset(&r->prm, 0, sizeof(r->prm));
-    r->prm.heuristic = VSBPP_H1;
-    r->prm.criterion = VSBPP_BF;
-    if (p) r->prm = *p;
-    r->need = need;
-    r->in_bytes = 4 * (static_cast<size_t>(m) + static_cast<size_t>(n));
-    r->out_bytes = align256(8 * static_cast<size_t>(std::max<int64_t>(m, 1))) + 64;
-    r->h_in = static_cast<int32_t*>(s->pinned.get(r->in_bytes));
-    r->h_out = static_cast<int32_t*>(s->pinned.get(r->out_bytes));
-    if (!r->h_in || !r->h_out) {
-        release_req(s, r);
-        return VSBPP_ENOMEM;
-    }
-    if (m > 0) std::memcpy(r->h_in, w, 4 * static_cast<size_t>(m));
-    std::memcpy(r->h_in + m, B, 4 * static_cast<size_t>(n));
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (static_cast<int>(s->waiting.size()) >= s->max_queued) {
-        release_req(s, r);
-        return VSBPP_EBUSY;
-    }
-    r->ticket = s->next_ticket++;
-    r->t_submit = Clock::now();
-    s->tickets[r->ticket] = r;
-    s->waiting.push_back(r);
-    s->cv.notify_all();
-    *ticket = r->ticket;
-    return VSBPP_OK;
 }
 
 int vsbpp_server_poll(vsbpp_server* s, uint64_t ticket, int32_t* bin_of_item, int32_t* bin_type,
                       int64_t* num_bins, int64_t* total_capacity, int64_t timeout_us) {
-    if (!s) return VSBPP_EINVAL;
-    std::unique_lock<std::mutex> lk(s->mu);
-    auto it = s->tickets.find(ticket);
-    if (it == s->tickets.end()) return VSBPP_ENOTFOUND;
-    Req* r = it->second;
-    if (!r->done) {
-        if (timeout_us == 0) return VSBPP_ETIMEDOUT;
-        if (timeout_us < 0) {
-            s->cv.wait(lk, [&] { return r->done; });
-        } else if (!s->cv.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; })) {
-            return VSBPP_ETIMEDOUT;
-        }
-    }
-    s->tickets.erase(it);
-    lk.unlock();
-    int rc = r->status;
-    if (rc == VSBPP_OK) {
-        const int64_t* sm = r->h_small();
-        rc = static_cast<int32_t>(static_cast<uint32_t>(sm[2] & 0xFFFFFFFF));
-        if (rc == VSBPP_OK) {
-            if ((r->m > 0 && (!bin_of_item || !bin_type)) || !num_bins || !total_capacity) {
-                rc = VSBPP_EINVAL;
-            } else {
-                if (r->m > 0) {
-                    std::memcpy(bin_of_item, r->h_out, 4 * static_cast<size_t>(r->m));
-                    std::memcpy(bin_type, r->h_out + std::max<int64_t>(r->m, 1), 4 * static_cast<size_t>(sm[0]));
-                }
-                *num_bins = sm[0];
-                *total_capacity = sm[1];
+    try {
+        if (!s) return VSBPP_EINVAL;
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->tickets.find(ticket);
+        if (it == s->tickets.end()) return VSBPP_ENOTFOUND;
+        Req* r = it->second;
+        if (!r->done) {
+            if (timeout_us == 0) return VSBPP_ETIMEDOUT;
+            if (timeout_us < 0) {
+                s->cv.wait(lk, [&] { return r->done; });
+            } else if (!s->cv.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; })) {
+                return VSBPP_ETIMEDOUT;
             }
         }
+        s->tickets.erase(it);
+        lk.unlock();
+        int rc = r->status;
+        if (rc == VSBPP_OK) {
+            const int64_t* sm = r->h_small();
+            rc = static_cast<int32_t>(static_cast<uint32_t>(sm[2] & 0xFFFFFFFF));
+            if (rc == VSBPP_OK) {
+                if ((r->m > 0 && (!bin_of_item || !bin_type)) || !num_bins || !total_capacity) {
+                    rc = VSBPP_EINVAL;
+                } else {
+                    if (r->m > 0) {
+                        std::memcpy(bin_of_item, r->h_out, 4 * static_cast<size_t>(r->m));
+                        std::memcpy(bin_type, r->h_out + std::max<int64_t>(r->m, 1), 4 * static_cast<size_t>(sm[0]));
+                    }
+                    *num_bins = sm[0];
+                    *total_capacity = sm[1];
+                }
+            }
+        }
+        release_req(s, r);
+        return rc;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
-    release_req(s, r);
-    return rc;
 }
 
 int vsbpp_server_stats(vsbpp_server* s, vsbpp_server_stats_t* out) {
-    if (!s || !out) return VSBPP_EINVAL;
-    std::vector<double> v;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        v = s->lat_us;
-        out->completed = s->completed;
-        out->items_packed = s->items;
-        out->busy_s = s->any ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;
+    try {
+        if (!s || !out) return VSBPP_EINVAL;
+        std::vector<double> v;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            v = s->lat_us;
+            out->completed = s->completed;
+            out->items_packed = s->items;
+            out->busy_s = s->any ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;
+        }
+        out->p50_us = out->p99_us = out->max_us = 0.0;
+        if (!v.empty()) {
+            std::sort(v.begin(), v.end());
+            auto q = [&](double f) {
+                const size_t k = static_cast<size_t>(f * static_cast<double>(v.size() - 1) + 0.5);
+                return v[std::min(k, v.size() - 1)];
+            };
+            out->p50_us = q(0.50);
+            out->p99_us = q(0.99);
+            out->max_us = v.back();
+        }
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
-    out->p50_us = out->p99_us = out->max_us = 0.0;
-    if (!v.empty()) {
-        std::sort(v.begin(), v.end());
-        auto q = [&](double f) {
-            const size_t k = static_cast<size_t>(f * static_cast<double>(v.size() - 1) + 0.5);
-            return v[std::min(k, v.size() - 1)];
-        };
-        out->p50_us = q(0.50);
-        out->p99_us = q(0.99);
-        out->max_us = v.back();
-    }
-    return VSBPP_OK;
 }
 
 int vsbpp_server_destroy(vsbpp_server* s) {
