@@ -32,6 +32,7 @@ _lib = None
 FF, BF, WF, RANDOM = 0, 1, 2, 3
 H1, H2 = 1, 2
 OK, EINVAL, ETOOBIG = 0, -1, -2
+REMARK3 = 1        # flag: Rule 5 with Remark 3's per-type condition (reading in vsbpp_oracle.c, G7)
 
 
 def build(force: bool = False) -> str:
@@ -60,6 +61,11 @@ def _bind(lib):
                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                 ctypes.c_int32, ctypes.c_uint64,
                                 i32p, i32p, i64p, i64p]
+    lib.oracle_pack_flags.restype = ctypes.c_int
+    lib.oracle_pack_flags.argtypes = [i32p, ctypes.c_int64, i32p, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                      ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
+                                      i32p, i32p, i64p, i64p]
     lib.oracle_opt_bruteforce.restype = ctypes.c_int64
     lib.oracle_opt_bruteforce.argtypes = [i32p, ctypes.c_int32, i32p, ctypes.c_int32]
     lib.oracle_fit_tests.restype = ctypes.c_uint64
@@ -109,8 +115,10 @@ class OracleLib:
         return int(self._lib.oracle_splitmix64(seed & (2**64 - 1), key & (2**64 - 1)))
 
     def pack(self, w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
-             preopen: int = 0, seed: int = 0) -> PackResult:
-        """Pack one instance with the hybrid P system (Sections 6.3 / 6.4)."""
+             preopen: int = 0, seed: int = 0, flags: int = 0) -> PackResult:
+        """Pack one instance with the hybrid P system (Sections 6.3 / 6.4).
+        flags: 0, or REMARK3 (Rule 5 divides only when every bin of the type
+        then holds at least half its capacity, Remark 3 of Section 6.3)."""
         w = np.ascontiguousarray(w, dtype=np.int32)
         B = np.ascontiguousarray(B, dtype=np.int32)
         m = int(w.shape[0])
@@ -120,11 +128,11 @@ class OracleLib:
         tot = np.zeros(1, dtype=np.int64)
         wbuf = w if m > 0 else np.zeros(1, dtype=np.int32)
         Bbuf = B if B.shape[0] > 0 else np.zeros(1, dtype=np.int32)
-        rc = self._lib.oracle_pack(_ptr(wbuf, ctypes.c_int32), m, _ptr(Bbuf, ctypes.c_int32),
-                                   int(B.shape[0]), heuristic, criterion, sublist_size, preopen,
-                                   seed & (2**64 - 1),
-                                   _ptr(bin_of_item, ctypes.c_int32), _ptr(bin_type, ctypes.c_int32),
-                                   _ptr(nb, ctypes.c_int64), _ptr(tot, ctypes.c_int64))
+        rc = self._lib.oracle_pack_flags(_ptr(wbuf, ctypes.c_int32), m, _ptr(Bbuf, ctypes.c_int32),
+                                         int(B.shape[0]), heuristic, criterion, sublist_size, preopen,
+                                         seed & (2**64 - 1), flags,
+                                         _ptr(bin_of_item, ctypes.c_int32), _ptr(bin_type, ctypes.c_int32),
+                                         _ptr(nb, ctypes.c_int64), _ptr(tot, ctypes.c_int64))
         k = int(nb[0])
         return PackResult(int(rc), bin_of_item[:m].copy(), bin_type[:k].copy(), k, int(tot[0]))
 
@@ -210,8 +218,8 @@ def splitmix64(seed: int, key: int) -> int:
 
 
 def pack(w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
-         preopen: int = 0, seed: int = 0) -> PackResult:
-    return default().pack(w, B, heuristic, criterion, sublist_size, preopen, seed)
+         preopen: int = 0, seed: int = 0, flags: int = 0) -> PackResult:
+    return default().pack(w, B, heuristic, criterion, sublist_size, preopen, seed, flags)
 
 
 def fit_tests(w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,

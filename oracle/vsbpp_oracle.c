@@ -36,6 +36,10 @@
  *   G5  Rule 4 fit test: residual capacity >= w (Remark 2 of Section 6.3);
  *   G6  ties in FF/BF/WF go to the lowest creation index (Section 1);
  *   G7  Rule 5 fires once per bin, when 2*load first reaches >= B (real half);
+ *       with flag ORACLE_REMARK3 it fires only if, in addition, every bin of
+ *       that type now holds at least half its capacity -- Remark 3 of Section
+ *       6.3 read as a condition (a consequence of Rule 5 under the literal
+ *       Rule 2, but not once G4 can open bins below half);
  *   G8  "used" bins are those with load > 0; bin ids are dense in creation
  *       order among used bins, sublists concatenated in order;
  *   G9  permutations are enumerated in lexicographic order of positions,
@@ -66,6 +70,9 @@
 #define OR_RANDOM 3
 #define OR_H1 1
 #define OR_H2 2
+
+/* flags of oracle_pack_flags */
+#define ORACLE_REMARK3 1       /* G7 with Remark 3's per-type condition */
 
 #define OR_H2_DEFAULT_SUBLIST 5
 #define OR_H2_MAX_SUBLIST 12   /* s <= 6: Section 6.4; up to 12: Section 7's exhaustive search */
@@ -107,9 +114,19 @@ typedef struct {
  * raw[q] receives the creation index of the bin that took step q's item.
  * Returns the number of bins created.
  */
+/* Remark 3 of Section 6.3: does every bin of type t hold at least half of
+ * its capacity? */
+static int or_type_all_half(const or_bin *bins, int64_t nb, const int32_t *B, int32_t t)
+{
+    for (int64_t x = 0; x < nb; ++x)
+        if (bins[x].type == t && 2 * bins[x].load < (int64_t)B[t])
+            return 0;
+    return 1;
+}
+
 static int64_t or_membrane_run(const int32_t *seq, const int32_t *crit, int64_t k,
                                const int32_t *B, int32_t n, int32_t preopen,
-                               or_bin *bins, int64_t *raw)
+                               or_bin *bins, int64_t *raw, int32_t remark3)
 {
     int64_t nb = 0;
     if (preopen) {                         /* Rule 2 taken literally (G3) */
@@ -161,9 +178,11 @@ static int64_t or_membrane_run(const int32_t *seq, const int32_t *crit, int64_t 
             /* Rule 5 (G7): the bin divides when its load first reaches half
              * of its capacity, i.e. 2*before < cap <= 2*after. */
             if (2 * before < cap && cap <= 2 * after) {
-                bins[nb].load = 0;
-                bins[nb].type = bins[chosen].type;
-                ++nb;
+                if (!remark3 || or_type_all_half(bins, nb, B, bins[chosen].type)) {
+                    bins[nb].load = 0;
+                    bins[nb].type = bins[chosen].type;
+                    ++nb;
+                }
             }
         }
         raw[q] = chosen;
@@ -246,18 +265,22 @@ static int or_validate(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
 /*
  * Pack one instance.  bin_of_item[m] receives dense bin ids, bin_type[<= m]
  * receives the 0-based type of each used bin (0 = largest capacity).
+ * flags: 0, or ORACLE_REMARK3 (reading G7 with Remark 3's condition).
  */
-int oracle_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
-                int32_t heuristic, int32_t criterion, int64_t sublist_size,
-                int32_t preopen, uint64_t seed,
-                int32_t *bin_of_item, int32_t *bin_type,
-                int64_t *num_bins, int64_t *total_capacity)
+int oracle_pack_flags(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                      int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                      int32_t preopen, uint64_t seed, int32_t flags,
+                      int32_t *bin_of_item, int32_t *bin_type,
+                      int64_t *num_bins, int64_t *total_capacity)
 {
     if (num_bins) *num_bins = 0;
     if (total_capacity) *total_capacity = 0;
     int rc = or_validate(w, m, B, n, heuristic, criterion, sublist_size, preopen);
     if (rc != OR_OK)
         return rc;
+    if (flags & ~ORACLE_REMARK3)
+        return OR_EINVAL;
+    const int32_t remark3 = (flags & ORACLE_REMARK3) ? 1 : 0;
     if (m == 0)
         return OR_OK;
 
@@ -295,7 +318,7 @@ int oracle_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
                               ? or_random_criterion(seed, (uint64_t)(a + q))
                               : criterion;
             }
-            const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw);
+            const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw, remark3);
             int64_t cap_sum = 0;
             const int64_t used = or_used_bins(bins, nb, B, dense, &cap_sum);
             for (int64_t q = 0; q < k; ++q)
@@ -323,7 +346,7 @@ int oracle_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
                                                   : ((uint64_t)g * OR_FACT12 + (uint64_t)rank) * 16u + (uint64_t)q)
                                   : criterion;
                 }
-                const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw);
+                const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw, remark3);
                 int64_t cap_sum = 0;
                 const int64_t used = or_used_bins(bins, nb, B, dense, &cap_sum);
                 if (best_total < 0 || cap_sum < best_total) {
@@ -351,6 +374,17 @@ int oracle_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
     if (num_bins) *num_bins = bin_offset;
     if (total_capacity) *total_capacity = total;
     return OR_OK;
+}
+
+/* oracle_pack_flags with flags = 0: the readings G1-G12 as stated above. */
+int oracle_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                int32_t preopen, uint64_t seed,
+                int32_t *bin_of_item, int32_t *bin_type,
+                int64_t *num_bins, int64_t *total_capacity)
+{
+    return oracle_pack_flags(w, m, B, n, heuristic, criterion, sublist_size, preopen, seed, 0,
+                             bin_of_item, bin_type, num_bins, total_capacity);
 }
 
 /*

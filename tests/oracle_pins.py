@@ -148,7 +148,7 @@ def pin_hand_examples(lib):
     d = load_golden("hand_examples.json")
     for ex in d["examples"]:
         r = lib.pack(ex["w"], ex["B"], ex["heuristic"], ex["criterion"], ex["sublist_size"],
-                     ex["preopen"], ex["seed"])
+                     ex["preopen"], ex["seed"], ex.get("flags", 0))
         assert r.status == 0, ex["name"]
         assert r.bin_of_item.tolist() == ex["bin_of_item"], ex["name"]
         assert r.bin_type.tolist() == ex["bin_type"], ex["name"]
@@ -295,6 +295,7 @@ def pin_errors(lib):
     assert lib.pack([101, 0], B, 1, 0).status == -2
     assert lib.pack([1], B, 3, 0).status == -1              # heuristic id
     assert lib.pack([1], B, 1, 4).status == -1              # criterion id
+    assert lib.pack([1], B, 1, 0, 0, 0, 0, 2).status == -1  # unknown flag
     assert lib.pack([1], B, 1, 0, -1).status == -1          # sublist size
     assert lib.pack([1], B, 2, 0, 13).status == -1          # H2 sublist <= 12
     assert lib.pack([1], B, 1, 0, 0, 2).status == -1        # preopen flag

@@ -30,6 +30,8 @@ def _lib():
 
 def test_hand_examples_host_api():
     for ex in P.load_golden("hand_examples.json")["examples"]:
+        if ex.get("flags", 0):
+            continue                  # oracle-only reading (Remark 3 condition), not in the library
         r = native.pack(ex["w"], ex["B"], ex["heuristic"], ex["criterion"], ex["sublist_size"],
                         ex["preopen"], ex["seed"])
         assert r.status == 0, ex["name"]

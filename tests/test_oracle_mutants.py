@@ -71,9 +71,13 @@ MUTANTS = {
     "h2_types_of_last_permutation": ("                    best_used = used;\n", "                    best_used = used;\n                }\n                {\n"),
     "rule5_strictly_past_half": ("if (2 * before < cap && cap <= 2 * after) {", "if (2 * before < cap && cap < 2 * after) {"),
     "preopen_all_largest_type": ("bins[nb].type = i;\n            ++nb;", "bins[nb].type = 0;\n            ++nb;"),
-    "h2_preopen_ignored": ("                const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw);\n                int64_t cap_sum = 0;\n                const int64_t used = or_used_bins(bins, nb, B, dense, &cap_sum);\n                if (best_total",
-                           "                const int64_t nb = or_membrane_run(seq, crit, k, B, n, 0, bins, raw);\n                int64_t cap_sum = 0;\n                const int64_t used = or_used_bins(bins, nb, B, dense, &cap_sum);\n                if (best_total"),
+    "h2_preopen_ignored": ("                const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw, remark3);\n                int64_t cap_sum = 0;\n                const int64_t used = or_used_bins(bins, nb, B, dense, &cap_sum);\n                if (best_total",
+                           "                const int64_t nb = or_membrane_run(seq, crit, k, B, n, 0, bins, raw, remark3);\n                int64_t cap_sum = 0;\n                const int64_t used = or_used_bins(bins, nb, B, dense, &cap_sum);\n                if (best_total"),
     "h2_sublist_offset_dropped": ("            bin_offset += best_used;", "            bin_offset += 0;"),
+    "remark3_condition_ignored": ("if (!remark3 || or_type_all_half(bins, nb, B, bins[chosen].type)) {",
+                                  "if (1) {"),
+    "remark3_below_half_strict": ("if (bins[x].type == t && 2 * bins[x].load < (int64_t)B[t])",
+                                  "if (bins[x].type == t && 2 * bins[x].load < (int64_t)B[t] - 1)"),
     "last_partial_sublist_dropped": ("for (int64_t g = 0; g * s < m; ++g) {", "for (int64_t g = 0; (g + 1) * s <= m; ++g) {"),
 }
 
