@@ -74,7 +74,7 @@ def _bind(lib):
     lib.oracle_pack_many.restype = ctypes.c_int
     lib.oracle_pack_many.argtypes = [ctypes.c_int64, i32p, i64p, i32p, i32p,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
-                                     ctypes.c_int32, ctypes.c_uint64,
+                                     ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
                                      i32p, i32p, i64p, i64p, i32p, ctypes.c_int32]
     return lib
 
@@ -155,10 +155,11 @@ class OracleLib:
                                                    _ptr(B, ctypes.c_int32), int(B.shape[0])))
 
     def pack_many(self, w_all, w_off, B_all, B_off, heuristic: int = H1, criterion: int = BF,
-                  sublist_size: int = 0, preopen: int = 0, seed: int = 0,
+                  sublist_size: int = 0, preopen: int = 0, seed: int = 0, flags: int = 0,
                   nthreads: int | None = None) -> BatchResult:
         """Pack N independent instances given in CSR form; one oracle call per
-        instance, spread over ``nthreads`` host threads (default: all cores)."""
+        instance, spread over ``nthreads`` host threads (default: all cores).
+        flags as in ``pack``."""
         w_all = np.ascontiguousarray(w_all, dtype=np.int32)
         w_off = np.ascontiguousarray(w_off, dtype=np.int64)
         B_all = np.ascontiguousarray(B_all, dtype=np.int32)
@@ -177,7 +178,7 @@ class OracleLib:
         rc = self._lib.oracle_pack_many(N, _ptr(wbuf, ctypes.c_int32), _ptr(w_off, ctypes.c_int64),
                                         _ptr(Bbuf, ctypes.c_int32), _ptr(B_off, ctypes.c_int32),
                                         heuristic, criterion, sublist_size, preopen,
-                                        seed & (2**64 - 1),
+                                        seed & (2**64 - 1), flags,
                                         _ptr(boi, ctypes.c_int32), _ptr(bty, ctypes.c_int32),
                                         _ptr(nb, ctypes.c_int64), _ptr(tot, ctypes.c_int64),
                                         _ptr(st, ctypes.c_int32), int(nthreads))
@@ -232,7 +233,7 @@ def opt_bruteforce(w, B) -> int:
 
 
 def pack_many(w_all, w_off, B_all, B_off, heuristic: int = H1, criterion: int = BF,
-              sublist_size: int = 0, preopen: int = 0, seed: int = 0,
+              sublist_size: int = 0, preopen: int = 0, seed: int = 0, flags: int = 0,
               nthreads: int | None = None) -> BatchResult:
     return default().pack_many(w_all, w_off, B_all, B_off, heuristic, criterion,
-                               sublist_size, preopen, seed, nthreads)
+                               sublist_size, preopen, seed, flags, nthreads)

@@ -39,17 +39,21 @@ def test_sublists_equal_independent_packs(oracle_lib):
         assert full.total == tot
 
 
-def test_determinism_and_pack_many(oracle_lib):
+@pytest.mark.parametrize("flags", [0, 1])
+def test_determinism_and_pack_many(oracle_lib, flags):
+    """The threaded batch driver gives each instance exactly the single call's
+    result (flags = 1: the Remark 3 option of Rule 5)."""
     b = I.config3(N=24, m_hi=600)
-    many = oracle_lib.pack_many(b.w_all, b.w_off, b.B_all, b.B_off, 1, 1, nthreads=4)
-    for i in range(b.N):
-        w, B = b.instance(i)
-        r = oracle_lib.pack(w, B, 1, 1)
-        a = int(b.w_off[i])
-        assert many.status[i] == 0
-        assert many.total[i] == r.total
-        assert many.bin_of_item[a:a + len(w)].tolist() == r.bin_of_item.tolist()
-        assert many.bin_type[a:a + r.num_bins].tolist() == r.bin_type.tolist()
+    for crit in ((1,) if flags == 0 else (0, 1, 2)):
+        many = oracle_lib.pack_many(b.w_all, b.w_off, b.B_all, b.B_off, 1, crit, flags=flags, nthreads=4)
+        for i in range(b.N):
+            w, B = b.instance(i)
+            r = oracle_lib.pack(w, B, 1, crit, flags=flags)
+            a = int(b.w_off[i])
+            assert many.status[i] == 0
+            assert many.total[i] == r.total
+            assert many.bin_of_item[a:a + len(w)].tolist() == r.bin_of_item.tolist()
+            assert many.bin_type[a:a + r.num_bins].tolist() == r.bin_type.tolist()
 
 
 def test_group2_fixture_matches_table7_weights():
