@@ -143,7 +143,9 @@ int vsbpp_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
  * on `stream` (a cudaStream_t; NULL = legacy default stream).  The return
  * value only reports host-side argument checks (m, n, p, pointers); the
  * instance's own status (including weight checks) is written to the device
- * word *status when the stream reaches it.
+ * word *status when the stream reaches it.  Library scratch belongs to the
+ * stream and grows in stream order, as for vsbpp_pack_batch below: calls on
+ * different streams never wait for each other on the host.
  */
 int vsbpp_pack_device(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
                       const vsbpp_params *p,
