@@ -17,7 +17,11 @@ mathematics fixes:
   * closed forms: a single item costs min{B_i >= w} (also when w equals a
     capacity); m items of weight B_1 cost m*B_1;
   * the second heuristic equals the cheapest permutation, enumerated here with
-    itertools (Section 6.4);
+    itertools (Section 6.4); with the RANDOM criterion, each permutation's
+    criteria follow from the SplitMix64 stream property (output K of the
+    stream seeded s is output 0 of the stream seeded s + K*gamma), which pins
+    the second heuristic's key layout (reading G12) to the first heuristic's
+    RANDOM packing;
   * invariants of any packing (each item once, no bin over capacity, total =
     sum of used capacities >= sum of weights).
 
@@ -143,6 +147,34 @@ def check_packing(w, B, res, m_expected=None):
     assert np.unique(boi).shape[0] == res.num_bins
 
 
+# ---------------------------------------------------------------- SplitMix64
+# Steele, Lea & Flood (OOPSLA 2014): the state advances by the odd constant
+# gamma (the golden-ratio increment of the published generator), and each
+# output is the state passed through the variant-13 mixer.  Written here
+# independently of the oracle's C copy and checked against the published
+# vectors by pin_h2_random_key.
+SM_GAMMA = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def splitmix64_py(seed: int, key: int) -> int:
+    """Output number `key` (0-based) of the SplitMix64 stream seeded `seed`."""
+    z = (seed + (key + 1) * SM_GAMMA) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+FACT12 = math.factorial(12)
+
+
+def h2_random_key_base(g: int, rank: int, s: int) -> int:
+    """Reading G12: the RANDOM key of step q of permutation `rank` of sublist
+    g is base + q, base = (g*720 + rank)*8 for s <= 6 and (g*12! + rank)*16
+    for the exhaustive search (s = 7..12)."""
+    return (g * 720 + rank) * 8 if s <= 6 else (g * FACT12 + rank) * 16
+
+
 # --------------------------------------------------------------------- pins
 def pin_hand_examples(lib):
     d = load_golden("hand_examples.json")
@@ -266,6 +298,57 @@ def pin_h2_is_best_permutation(lib, trials=60, seed=14):
         assert r2.bin_type.tolist() == best[2]
 
 
+def pin_h2_random_key(lib, seed=17):
+    """The second heuristic with the RANDOM criterion (Rule 3's draw "with
+    equal probabilities", Section 6.4's permutations, reading G12).  Step q of
+    permutation `rank` of sublist g takes criterion SplitMix64(seed, base + q)
+    mod 3, with base as in h2_random_key_base.  SplitMix64 output K of the
+    stream seeded `seed` is output 0 of the stream seeded seed + K*gamma
+    (the state only ever advances by gamma), so that permutation packs
+    exactly as the first heuristic with RANDOM packs the permuted items with
+    seed + base*gamma: the first heuristic's RANDOM is pinned to the published
+    vectors by pin_random_criterion_vectors.  Several sublists (g > 0), the
+    two key layouts (s <= 6 and s = 7) and the switch between them (s = 6 vs
+    7) are all exercised; the cheapest permutation wins, lowest rank on
+    ties, ids offset by the earlier sublists' bins (reading G11)."""
+    d = load_golden("splitmix64_vectors.json")
+    for k, v in enumerate(d["outputs"]):
+        assert splitmix64_py(int(d["seed"]), k) == int(v)
+    # the stream property used below, on the published seed
+    for K in (0, 1, 7, 5765, 2**40 + 3):
+        assert splitmix64_py(int(d["seed"]), K) == splitmix64_py((int(d["seed"]) + K * SM_GAMMA) & _M64, 0)
+    rng = np.random.default_rng(seed)
+    for s, trials in ((3, 6), (5, 3), (6, 2), (7, 1)):
+        for t in range(trials):
+            n = int(rng.integers(2, 4))
+            B = sorted(rng.choice(np.arange(6, 40), size=n, replace=False).tolist(), reverse=True)
+            m = 2 * s + int(rng.integers(1, 3))             # two full sublists and a partial one
+            w = rng.integers(1, B[0] + 1, size=m).tolist()
+            run_seed = int(rng.integers(0, 2**63))
+            want_boi, want_bt, total, off = [], [], 0, 0
+            for g, a in enumerate(range(0, m, s)):
+                sub = w[a:a + s]
+                k = len(sub)
+                best = None
+                for rank, perm in enumerate(itertools.permutations(range(k))):
+                    seed_p = (run_seed + h2_random_key_base(g, rank, s) * SM_GAMMA) & _M64
+                    r = lib.pack([sub[x] for x in perm], B, 1, 3, 0, 0, seed_p)
+                    if best is None or r.total < best[0]:
+                        item_bin = [0] * k
+                        for q, x in enumerate(perm):
+                            item_bin[x] = int(r.bin_of_item[q])
+                        best = (r.total, item_bin, r.bin_type.tolist(), r.num_bins)
+                want_boi += [off + b for b in best[1]]
+                want_bt += best[2]
+                total += best[0]
+                off += best[3]
+            r2 = lib.pack(w, B, 2, 3, s, 0, run_seed)
+            assert r2.status == 0
+            assert r2.bin_of_item.tolist() == want_boi, (s, w, B, run_seed)
+            assert r2.bin_type.tolist() == want_bt, (s, w, B)
+            assert r2.total == total
+
+
 def pin_invariants(lib, trials=200, seed=15):
     rng = np.random.default_rng(seed)
     for t in range(trials):
@@ -330,7 +413,7 @@ def pin_fit_tests(lib, seed=16):
 
 
 ALL_PINS = [pin_hand_examples, pin_splitmix64, pin_random_criterion_vectors, pin_textbook_n1, pin_optimum,
-            pin_closed_forms, pin_h2_is_best_permutation, pin_invariants, pin_errors,
+            pin_closed_forms, pin_h2_is_best_permutation, pin_h2_random_key, pin_invariants, pin_errors,
             pin_fit_tests]
 
 

@@ -78,6 +78,11 @@ MUTANTS = {
                                   "if (1) {"),
     "remark3_below_half_strict": ("if (bins[x].type == t && 2 * bins[x].load < (int64_t)B[t])",
                                   "if (bins[x].type == t && 2 * bins[x].load < (int64_t)B[t] - 1)"),
+    "h2_random_key_720_as_120": ("? (uint64_t)((g * 720 + rank) * 8 + q)", "? (uint64_t)((g * 120 + rank) * 8 + q)"),
+    "h2_random_key_stride_7": ("? (uint64_t)((g * 720 + rank) * 8 + q)", "? (uint64_t)((g * 720 + rank) * 7 + q)"),
+    "h2_random_key_rank_dropped": ("? (uint64_t)((g * 720 + rank) * 8 + q)", "? (uint64_t)((g * 720) * 8 + q)"),
+    "h2x_random_key_stride_8": ("+ (uint64_t)rank) * 16u + (uint64_t)q)", "+ (uint64_t)rank) * 8u + (uint64_t)q)"),
+    "h2_random_layout_switch_off_by_one": ("seed, s <= 6\n", "seed, s <= 5\n"),
     "last_partial_sublist_dropped": ("for (int64_t g = 0; g * s < m; ++g) {", "for (int64_t g = 0; (g + 1) * s <= m; ++g) {"),
 }
 
