@@ -191,13 +191,14 @@ int vsbpp_pack_batch(int64_t N, const int32_t *w_all, const int64_t *w_off,
  * allocate device memory.  (The paper has no counterpart: this is a property
  * of the library, not of the method.)
  *
- * Who needs it: code that runs while a stream is being captured into a CUDA
- * graph in the global capture mode, where cudaMalloc is not permitted; code
- * that owns a fixed memory reservation or runs inside another allocator's
- * arena; latency-critical loops that cannot afford an allocation, or the
- * device-wide synchronisation a cudaFree implies, on their path.  This call
- * allocates nothing: its scratch (about 0.5 MiB) is one static array in the
- * library's device image, shared by every call on a device.
+ * Who needs it: code that owns a fixed device-memory reservation or runs
+ * inside another allocator's arena, where a library allocation would bypass
+ * the owner's accounting; latency-critical loops that cannot afford an
+ * allocation, or the device-wide synchronisation a cudaFree implies, on
+ * their path.  This call allocates nothing: its scratch (about 0.5 MiB) is
+ * one static array in the library's device image, shared by every call on a
+ * device and held by every GPU that loads the library until the process
+ * exits.
  *
  * Arguments and results as vsbpp_pack_batch, restricted to the first
  * heuristic with one membrane system per instance (sublist_size 0 or
@@ -207,10 +208,15 @@ int vsbpp_pack_batch(int64_t N, const int32_t *w_all, const int64_t *w_off,
  * Instances with B_1 > 32767 get status VSBPP_ECAPACITY.
  *
  * The first call on a device looks up the scratch array's device address
- * (with that device current); make that first call before any stream
- * capture begins.  Every call on a device uses the same scratch: calls whose
- * GPU work may overlap in time (for example on two streams) race and must be
- * ordered by the caller.  Each call clears what must start at zero.
+ * (with that device current) and keeps it until the process exits; make that
+ * first call before any stream capture begins, and make no call after a
+ * cudaDeviceReset of that device (the kept address would be stale).
+ * `stream` must belong to the current device (else VSBPP_EINVAL).  Every
+ * call on a device uses the same scratch: calls whose GPU work may overlap
+ * in time (for example on two streams) race and must be ordered by the
+ * caller.  Each call clears what must start at zero.  The work counters
+ * (vsbpp_counters_*) include this call's work; kernel timing
+ * (vsbpp_kernel_timing_*) does not record it.
  */
 #define VSBPP_NOALLOC_MAX_INSTANCES 65536
 #define VSBPP_NOALLOC_MAX_ITEMS 16384

@@ -850,6 +850,11 @@ int time_config(const vsbpp_config& cfg, int64_t N, const int32_t* w_all, const 
 
 }  // namespace
 
+unsigned long long* vsbpp::counters_ptr() {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    return g_counters;
+}
+
 // ================================================================== C ABI
 extern "C" {
 

@@ -14,6 +14,10 @@
 
 namespace vsbpp {
 
+// The device work counters {items, fit tests} while vsbpp_counters_enable is
+// on, else null.
+unsigned long long* counters_ptr();
+
 // Raises a kernel's dynamic shared-memory limit to `smem` bytes on the current
 // device, once per (kernel, device, size) increase.
 cudaError_t ensure_smem_attr(const void* kernel, int smem);

@@ -2,18 +2,18 @@
 // for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the moment they need a packing: code
-// that runs while a stream is being captured into a CUDA graph in the global
-// capture mode (where cudaMalloc is not permitted), code that runs under a
-// fixed memory reservation or inside another allocator's arena, and
-// latency-critical loops that cannot afford an allocation (or the implicit
-// device synchronisation of a cudaFree) on their path.  This entry point
-// takes its scratch from one file-scope __device__ array instead of the
-// library's per-stream scratch, and calls no allocating routine.
+// that runs under a fixed device-memory reservation or inside another
+// allocator's arena (where a library allocation would go around the owner's
+// accounting), and latency-critical loops that cannot afford an allocation,
+// or the device-wide synchronisation of a cudaFree, on their path.  This
+// entry point takes its scratch from one file-scope __device__ array instead
+// of the library's per-stream scratch, and calls no allocating routine.
 //
 // The scratch array is a host-side symbol; host code may not pass its name to
 // a kernel.  Its device address is obtained with cudaGetSymbolAddress once
-// per device, with that device current, by the first call on that device
-// (make that first call before any stream capture begins).  Every call on a
+// per device, with that device current, by the first call on that device,
+// and cached until the process ends: after a cudaDeviceReset the cached
+// address is stale, so calls must not be made after a reset.  Every call on a
 // device shares the array: calls whose GPU work overlaps in time (on
 // different streams) race on it and must be serialised by the caller.
 #include <algorithm>
@@ -71,6 +71,14 @@ extern "C" int vsbpp_pack_batch_noalloc(int64_t N, const int32_t* w_all, const i
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VSBPP_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (st) {
+        // the scratch address and the SM count are the current device's: a
+        // stream of another device would run on the wrong GPU's scratch
+        int sdev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) return VSBPP_ECUDA;
+        if (sdev != dev) return VSBPP_EINVAL;
+    }
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -103,7 +111,6 @@ extern "C" int vsbpp_pack_batch_noalloc(int64_t N, const int32_t* w_all, const i
     const int occ = h1_blocks_per_sm(false, cfg.large_warps, 1, smem);
     if (occ <= 0) return VSBPP_ECUDA;
     const int grid = static_cast<int>(std::min<int64_t>(int64_t(occ) * sms, N));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     BatchView in{N, w_all, w_off, 0, B_all, B_off, 0};
     OutView out{bin_of_item_all, bin_type_all, num_bins, total, status, nullptr, nullptr, nullptr};
@@ -142,6 +149,7 @@ extern "C" int vsbpp_pack_batch_noalloc(int64_t N, const int32_t* w_all, const i
     hp.chunk = cfg.chunk;
     hp.slot_cap = slot_cap;
     hp.group_bytes = smem;
+    hp.counters = counters_ptr();       // work counters, when enabled
     if (h1_launch(false, hp, cfg.large_warps, 1, grid, smem, st) != cudaSuccess) return VSBPP_ECUDA;
     return VSBPP_OK;
 }

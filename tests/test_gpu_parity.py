@@ -81,10 +81,6 @@ def test_config3_full_batch(crit):
     assert_same(b, run_batch(b, 1, crit, seed=3), run_oracle(b, 1, crit, seed=3), f"cfg3 H1 c{crit}")
 
 
-def test_config3_h2_sample():
-    b = I.config3().subset(range(0, 4096, 16))
-    assert_same(b, run_batch(b, 2, native.BF, 5), run_oracle(b, 2, native.BF, 5), "cfg3 H2")
-
 
 def _fuzz_batch(seed, N=300, m_hi=400, cap_choices=(20, 100, 1000, 32767, 40000, 2**31 - 1)):
     rng = np.random.default_rng(seed)
