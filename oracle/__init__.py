@@ -33,6 +33,7 @@ FF, BF, WF, RANDOM = 0, 1, 2, 3
 H1, H2 = 1, 2
 OK, EINVAL, ETOOBIG = 0, -1, -2
 REMARK3 = 1        # flag: Rule 5 with Remark 3's per-type condition (reading in vsbpp_oracle.c, G7)
+PRESORT = 2        # flag: items packed in non-increasing weight order, ties in list order (G16)
 
 
 def build(force: bool = False) -> str:
@@ -66,6 +67,15 @@ def _bind(lib):
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                       ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
                                       i32p, i32p, i64p, i64p]
+    lib.oracle_pack_ext.restype = ctypes.c_int
+    lib.oracle_pack_ext.argtypes = [i32p, ctypes.c_int64, i32p, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                    ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64,
+                                    i32p, i32p, i64p, i64p]
+    lib.oracle_fit_tests_ext.restype = ctypes.c_uint64
+    lib.oracle_fit_tests_ext.argtypes = [i32p, ctypes.c_int64, i32p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                         ctypes.c_int32, ctypes.c_int64]
     lib.oracle_opt_bruteforce.restype = ctypes.c_int64
     lib.oracle_opt_bruteforce.argtypes = [i32p, ctypes.c_int32, i32p, ctypes.c_int32]
     lib.oracle_fit_tests.restype = ctypes.c_uint64
@@ -74,7 +84,7 @@ def _bind(lib):
     lib.oracle_pack_many.restype = ctypes.c_int
     lib.oracle_pack_many.argtypes = [ctypes.c_int64, i32p, i64p, i32p, i32p,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
-                                     ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64,
                                      i32p, i32p, i64p, i64p, i32p, ctypes.c_int32]
     return lib
 
@@ -115,10 +125,12 @@ class OracleLib:
         return int(self._lib.oracle_splitmix64(seed & (2**64 - 1), key & (2**64 - 1)))
 
     def pack(self, w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
-             preopen: int = 0, seed: int = 0, flags: int = 0) -> PackResult:
+             preopen: int = 0, seed: int = 0, flags: int = 0, max_open: int = 0) -> PackResult:
         """Pack one instance with the hybrid P system (Sections 6.3 / 6.4).
-        flags: 0, or REMARK3 (Rule 5 divides only when every bin of the type
-        then holds at least half its capacity, Remark 3 of Section 6.3)."""
+        flags: REMARK3 (Rule 5 divides only when every bin of the type then
+        holds at least half its capacity, Remark 3 of Section 6.3) and/or
+        PRESORT (non-increasing weight order first, reading G16).  max_open:
+        0, or K >= 1 for the bounded-space variant (reading G15)."""
         w = np.ascontiguousarray(w, dtype=np.int32)
         B = np.ascontiguousarray(B, dtype=np.int32)
         m = int(w.shape[0])
@@ -128,23 +140,25 @@ class OracleLib:
         tot = np.zeros(1, dtype=np.int64)
         wbuf = w if m > 0 else np.zeros(1, dtype=np.int32)
         Bbuf = B if B.shape[0] > 0 else np.zeros(1, dtype=np.int32)
-        rc = self._lib.oracle_pack_flags(_ptr(wbuf, ctypes.c_int32), m, _ptr(Bbuf, ctypes.c_int32),
-                                         int(B.shape[0]), heuristic, criterion, sublist_size, preopen,
-                                         seed & (2**64 - 1), flags,
-                                         _ptr(bin_of_item, ctypes.c_int32), _ptr(bin_type, ctypes.c_int32),
-                                         _ptr(nb, ctypes.c_int64), _ptr(tot, ctypes.c_int64))
+        rc = self._lib.oracle_pack_ext(_ptr(wbuf, ctypes.c_int32), m, _ptr(Bbuf, ctypes.c_int32),
+                                       int(B.shape[0]), heuristic, criterion, sublist_size, preopen,
+                                       seed & (2**64 - 1), flags, max_open,
+                                       _ptr(bin_of_item, ctypes.c_int32), _ptr(bin_type, ctypes.c_int32),
+                                       _ptr(nb, ctypes.c_int64), _ptr(tot, ctypes.c_int64))
         k = int(nb[0])
         return PackResult(int(rc), bin_of_item[:m].copy(), bin_type[:k].copy(), k, int(tot[0]))
 
     def fit_tests(self, w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
-                  preopen: int = 0, seed: int = 0) -> int:
-        """Rule 4 fit tests oracle_pack performs on this instance."""
+                  preopen: int = 0, seed: int = 0, flags: int = 0, max_open: int = 0) -> int:
+        """Rule 4 fit tests the oracle performs on this instance (one per
+        bin membrane that is open when an item arrives)."""
         w = np.ascontiguousarray(w, dtype=np.int32)
         B = np.ascontiguousarray(B, dtype=np.int32)
         wbuf = w if w.shape[0] > 0 else np.zeros(1, dtype=np.int32)
-        return int(self._lib.oracle_fit_tests(_ptr(wbuf, ctypes.c_int32), int(w.shape[0]),
-                                              _ptr(B, ctypes.c_int32), int(B.shape[0]), heuristic, criterion,
-                                              sublist_size, preopen, seed & (2**64 - 1)))
+        return int(self._lib.oracle_fit_tests_ext(_ptr(wbuf, ctypes.c_int32), int(w.shape[0]),
+                                                  _ptr(B, ctypes.c_int32), int(B.shape[0]), heuristic,
+                                                  criterion, sublist_size, preopen, seed & (2**64 - 1),
+                                                  flags, max_open))
 
     def opt_bruteforce(self, w, B) -> int:
         """Exact VSBPP optimum by subset DP (m <= 20); -1 if infeasible/invalid."""
@@ -156,7 +170,7 @@ class OracleLib:
 
     def pack_many(self, w_all, w_off, B_all, B_off, heuristic: int = H1, criterion: int = BF,
                   sublist_size: int = 0, preopen: int = 0, seed: int = 0, flags: int = 0,
-                  nthreads: int | None = None) -> BatchResult:
+                  nthreads: int | None = None, max_open: int = 0) -> BatchResult:
         """Pack N independent instances given in CSR form; one oracle call per
         instance, spread over ``nthreads`` host threads (default: all cores).
         flags as in ``pack``."""
@@ -167,7 +181,7 @@ class OracleLib:
         N = int(w_off.shape[0]) - 1
         tot_m = int(w_off[-1]) if N > 0 else 0
         if nthreads is None:
-            nthreads = os.cpu_count() or 1
+            nthreads = host_cores()
         boi = np.full(max(tot_m, 1), -1, dtype=np.int32)
         bty = np.full(max(tot_m, 1), -1, dtype=np.int32)
         nb = np.zeros(max(N, 1), dtype=np.int64)
@@ -178,7 +192,7 @@ class OracleLib:
         rc = self._lib.oracle_pack_many(N, _ptr(wbuf, ctypes.c_int32), _ptr(w_off, ctypes.c_int64),
                                         _ptr(Bbuf, ctypes.c_int32), _ptr(B_off, ctypes.c_int32),
                                         heuristic, criterion, sublist_size, preopen,
-                                        seed & (2**64 - 1), flags,
+                                        seed & (2**64 - 1), flags, max_open,
                                         _ptr(boi, ctypes.c_int32), _ptr(bty, ctypes.c_int32),
                                         _ptr(nb, ctypes.c_int64), _ptr(tot, ctypes.c_int64),
                                         _ptr(st, ctypes.c_int32), int(nthreads))
@@ -186,6 +200,14 @@ class OracleLib:
             raise RuntimeError(f"oracle_pack_many failed: {rc}")
         return BatchResult(st[:N].copy(), boi[:tot_m].copy(), bty[:tot_m].copy(),
                            nb[:N].copy(), tot[:N].copy())
+
+
+def host_cores() -> int:
+    """Host cores this process may run on (its CPU affinity set)."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 def compile_variant(source_text: str, out_path: str) -> str:
@@ -219,13 +241,13 @@ def splitmix64(seed: int, key: int) -> int:
 
 
 def pack(w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
-         preopen: int = 0, seed: int = 0, flags: int = 0) -> PackResult:
-    return default().pack(w, B, heuristic, criterion, sublist_size, preopen, seed, flags)
+         preopen: int = 0, seed: int = 0, flags: int = 0, max_open: int = 0) -> PackResult:
+    return default().pack(w, B, heuristic, criterion, sublist_size, preopen, seed, flags, max_open)
 
 
 def fit_tests(w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
-              preopen: int = 0, seed: int = 0) -> int:
-    return default().fit_tests(w, B, heuristic, criterion, sublist_size, preopen, seed)
+              preopen: int = 0, seed: int = 0, flags: int = 0, max_open: int = 0) -> int:
+    return default().fit_tests(w, B, heuristic, criterion, sublist_size, preopen, seed, flags, max_open)
 
 
 def opt_bruteforce(w, B) -> int:
@@ -234,6 +256,6 @@ def opt_bruteforce(w, B) -> int:
 
 def pack_many(w_all, w_off, B_all, B_off, heuristic: int = H1, criterion: int = BF,
               sublist_size: int = 0, preopen: int = 0, seed: int = 0, flags: int = 0,
-              nthreads: int | None = None) -> BatchResult:
+              nthreads: int | None = None, max_open: int = 0) -> BatchResult:
     return default().pack_many(w_all, w_off, B_all, B_off, heuristic, criterion,
-                               sublist_size, preopen, seed, flags, nthreads)
+                               sublist_size, preopen, seed, flags, nthreads, max_open)

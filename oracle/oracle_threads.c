@@ -4,7 +4,7 @@
  *
  * TEST INFRASTRUCTURE ONLY (parity tests and the CPU-baseline timing).  It
  * adds no arithmetic of its own: each instance is one plain call of
- * oracle_pack_flags; threads only take the next instance index from a shared
+ * oracle_pack_ext; threads only take the next instance index from a shared
  * counter.  Instances are independent problems (Section 6.1), so the result
  * does not depend on the thread count.
  */
@@ -12,11 +12,11 @@
 #include <stdint.h>
 #include <stdlib.h>
 
-int oracle_pack_flags(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
-                      int32_t heuristic, int32_t criterion, int64_t sublist_size,
-                      int32_t preopen, uint64_t seed, int32_t flags,
-                      int32_t *bin_of_item, int32_t *bin_type,
-                      int64_t *num_bins, int64_t *total_capacity);
+int oracle_pack_ext(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                    int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                    int32_t preopen, uint64_t seed, int32_t flags, int64_t max_open,
+                    int32_t *bin_of_item, int32_t *bin_type,
+                    int64_t *num_bins, int64_t *total_capacity);
 
 typedef struct {
     int64_t N;
@@ -26,6 +26,7 @@ typedef struct {
     const int32_t *B_off;
     int32_t heuristic, criterion, preopen, flags;
     int64_t sublist_size;
+    int64_t max_open;
     uint64_t seed;
     int32_t *bin_of_item_all;
     int32_t *bin_type_all;
@@ -49,10 +50,11 @@ static void *or_many_worker(void *arg)
         const int64_t m = job->w_off[i + 1] - a;
         const int32_t b0 = job->B_off[i];
         const int32_t n = job->B_off[i + 1] - b0;
-        job->status[i] = oracle_pack_flags(job->w_all + a, m, job->B_all + b0, n,
-                                           job->heuristic, job->criterion,
-                                           job->sublist_size, job->preopen, job->seed, job->flags,
-                                           job->bin_of_item_all + a,
+        job->status[i] = oracle_pack_ext(job->w_all + a, m, job->B_all + b0, n,
+                                         job->heuristic, job->criterion,
+                                         job->sublist_size, job->preopen, job->seed, job->flags,
+                                         job->max_open,
+                                         job->bin_of_item_all + a,
                                            job->bin_type_all + a,
                                            &job->num_bins[i], &job->total[i]);
     }
@@ -62,7 +64,7 @@ static void *or_many_worker(void *arg)
 int oracle_pack_many(int64_t N, const int32_t *w_all, const int64_t *w_off,
                      const int32_t *B_all, const int32_t *B_off,
                      int32_t heuristic, int32_t criterion, int64_t sublist_size,
-                     int32_t preopen, uint64_t seed, int32_t flags,
+                     int32_t preopen, uint64_t seed, int32_t flags, int64_t max_open,
                      int32_t *bin_of_item_all, int32_t *bin_type_all,
                      int64_t *num_bins, int64_t *total, int32_t *status,
                      int32_t nthreads)
@@ -74,7 +76,7 @@ int oracle_pack_many(int64_t N, const int32_t *w_all, const int64_t *w_off,
     job.w_all = w_all; job.w_off = w_off;
     job.B_all = B_all; job.B_off = B_off;
     job.heuristic = heuristic; job.criterion = criterion; job.preopen = preopen; job.flags = flags;
-    job.sublist_size = sublist_size; job.seed = seed;
+    job.sublist_size = sublist_size; job.seed = seed; job.max_open = max_open;
     job.bin_of_item_all = bin_of_item_all; job.bin_type_all = bin_type_all;
     job.num_bins = num_bins; job.total = total; job.status = status;
     job.next = 0;

@@ -45,6 +45,22 @@
  *   G9  permutations are enumerated in lexicographic order of positions,
  *       rank 0 = identity;
  *   G10 ties between permutations go to the lowest rank;
+ *   G15 (bounded-space variant, Section 1: FF / BF / WF keep a given number
+ *       of bins active, and a bin is closed when it is completely filled)
+ *       with max_open = K >= 1: only active (open) bin membranes take part
+ *       in Rule 4's fit test; a bin closes as soon as its residual reaches
+ *       0; whenever a bin must be created (an item that fits no open bin,
+ *       a Rule 5 division, or a Rule 2 bin) while K bins are open, the open
+ *       bin with the lowest creation index closes first.  Closed bins keep
+ *       their items and still count toward the objective.  K = 0 means no
+ *       bound (the method as above, nothing ever closes).  First heuristic
+ *       only; not combined with Remark 3;
+ *   G16 (offline pre-sort, the decreasing order of FFD/BFD that Section 5's
+ *       prior work uses) with flag ORACLE_PRESORT: the item list is sorted
+ *       by non-increasing weight, ties kept in list order, before Rule 1;
+ *       the sorted list is then packed exactly as a caller-given list would
+ *       be (RANDOM keys are sorted positions), and each item's bin id is
+ *       reported at the item's original position;
  *   G12 the RANDOM criterion draws c = SplitMix64(seed, key) mod 3 with
  *       0=FF, 1=BF, 2=WF; key = item index (first heuristic) or
  *       (sublist*720 + rank)*8 + step (second heuristic, s <= 6), or
@@ -71,8 +87,9 @@
 #define OR_H1 1
 #define OR_H2 2
 
-/* flags of oracle_pack_flags */
+/* flags of oracle_pack_flags / oracle_pack_ext */
 #define ORACLE_REMARK3 1       /* G7 with Remark 3's per-type condition */
+#define ORACLE_PRESORT 2       /* G16: non-increasing weight order before packing */
 
 #define OR_H2_DEFAULT_SUBLIST 5
 #define OR_H2_MAX_SUBLIST 12   /* s <= 6: Section 6.4; up to 12: Section 7's exhaustive search */
@@ -190,6 +207,103 @@ static int64_t or_membrane_run(const int32_t *seq, const int32_t *crit, int64_t 
     return nb;
 }
 
+/* G15: open bin number `at` of the list (creation order) closes. */
+static void or_close_at(int64_t *active, int64_t *na, int64_t at)
+{
+    for (int64_t a = at + 1; a < *na; ++a)
+        active[a - 1] = active[a];
+    --*na;
+}
+
+/* G15: before a bin is created while max_open bins are open, the open bin
+ * with the lowest creation index (the first of the list) closes. */
+static void or_make_room(int64_t *active, int64_t *na, int64_t max_open)
+{
+    if (*na >= max_open)
+        or_close_at(active, na, 0);
+}
+
+/*
+ * The bounded-space variant of one membrane system (reading G15): at most
+ * max_open bin membranes are active at a time.  active[0..na) lists the open
+ * bins by creation index (new bins are appended, so the list stays in
+ * creation order and its first entry is the oldest open bin).  Same
+ * arguments and result as or_membrane_run; active needs room for max_open
+ * entries.
+ */
+static int64_t or_membrane_run_bounded(const int32_t *seq, const int32_t *crit, int64_t k,
+                                       const int32_t *B, int32_t n, int32_t preopen,
+                                       or_bin *bins, int64_t *raw, int64_t max_open,
+                                       int64_t *active)
+{
+    int64_t nb = 0, na = 0;
+    if (preopen) {                         /* Rule 2 taken literally (G3) */
+        for (int32_t i = 0; i < n; ++i) {
+            or_make_room(active, &na, max_open);
+            bins[nb].load = 0;
+            bins[nb].type = i;
+            active[na++] = nb;
+            ++nb;
+        }
+    }
+    for (int64_t q = 0; q < k; ++q) {      /* Rule 3: one item per step (G2) */
+        const int64_t w = seq[q];
+        const int32_t c = crit[q];
+        int64_t chosen = -1, chosen_at = -1;
+        int64_t chosen_res = 0;
+        /* Rule 4 over the open bins only, in creation order (G5, G6) */
+        or_fit_tests += (uint64_t)na;
+        for (int64_t a = 0; a < na; ++a) {
+            const int64_t x = active[a];
+            const int64_t res = (int64_t)B[bins[x].type] - bins[x].load;
+            if (res < w)
+                continue;
+            if (chosen < 0 ||
+                (c == OR_BF && res < chosen_res) ||
+                (c == OR_WF && res > chosen_res)) {
+                chosen = x;
+                chosen_at = a;
+                chosen_res = res;
+            }
+            if (c == OR_FF)
+                break;
+        }
+        if (chosen < 0) {
+            /* G4: a bin of the smallest type that holds w, after closing the
+             * oldest open bin if max_open are open */
+            int32_t t = 0;
+            for (int32_t i = 0; i < n; ++i)
+                if (B[i] >= w)
+                    t = i;
+            or_make_room(active, &na, max_open);
+            bins[nb].load = 0;
+            bins[nb].type = t;
+            chosen = nb;
+            chosen_at = na;
+            active[na++] = nb;
+            ++nb;
+        }
+        {
+            const int64_t cap = B[bins[chosen].type];
+            const int64_t before = bins[chosen].load;
+            const int64_t after = before + w;
+            bins[chosen].load = after;     /* Rule 4: polarity k -> k + w */
+            if (after == cap)              /* completely filled: the bin closes */
+                or_close_at(active, &na, chosen_at);
+            /* Rule 5 (G7), after a full bin has closed */
+            if (2 * before < cap && cap <= 2 * after) {
+                or_make_room(active, &na, max_open);
+                bins[nb].load = 0;
+                bins[nb].type = bins[chosen].type;
+                active[na++] = nb;
+                ++nb;
+            }
+        }
+        raw[q] = chosen;
+    }
+    return nb;
+}
+
 /*
  * Objective of Section 1 over one membrane system (G8): dense[x] receives the
  * rank of bin x among used bins in creation order (or -1 when unused).
@@ -262,27 +376,73 @@ static int or_validate(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
     return OR_OK;
 }
 
+/* G16: one item of the pre-sort, its weight and its position in the list. */
+typedef struct {
+    int32_t w;
+    int64_t pos;
+} or_sort_item;
+
+/* Non-increasing weight; equal weights keep their list order. */
+static int or_sort_cmp(const void *a, const void *b)
+{
+    const or_sort_item *x = (const or_sort_item *)a, *y = (const or_sort_item *)b;
+    if (x->w != y->w)
+        return x->w > y->w ? -1 : 1;
+    return x->pos < y->pos ? -1 : (x->pos > y->pos ? 1 : 0);
+}
+
 /*
  * Pack one instance.  bin_of_item[m] receives dense bin ids, bin_type[<= m]
  * receives the 0-based type of each used bin (0 = largest capacity).
- * flags: 0, or ORACLE_REMARK3 (reading G7 with Remark 3's condition).
+ * flags: ORACLE_REMARK3 (reading G7 with Remark 3's condition) and/or
+ * ORACLE_PRESORT (reading G16).  max_open: 0, or the bound K of the
+ * bounded-space variant (reading G15; first heuristic, without Remark 3).
  */
-int oracle_pack_flags(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
-                      int32_t heuristic, int32_t criterion, int64_t sublist_size,
-                      int32_t preopen, uint64_t seed, int32_t flags,
-                      int32_t *bin_of_item, int32_t *bin_type,
-                      int64_t *num_bins, int64_t *total_capacity)
+int oracle_pack_ext(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                    int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                    int32_t preopen, uint64_t seed, int32_t flags, int64_t max_open,
+                    int32_t *bin_of_item, int32_t *bin_type,
+                    int64_t *num_bins, int64_t *total_capacity)
 {
     if (num_bins) *num_bins = 0;
     if (total_capacity) *total_capacity = 0;
     int rc = or_validate(w, m, B, n, heuristic, criterion, sublist_size, preopen);
     if (rc != OR_OK)
         return rc;
-    if (flags & ~ORACLE_REMARK3)
+    if (flags & ~(ORACLE_REMARK3 | ORACLE_PRESORT))
         return OR_EINVAL;
     const int32_t remark3 = (flags & ORACLE_REMARK3) ? 1 : 0;
+    if (max_open < 0 || (max_open > 0 && (heuristic != OR_H1 || remark3)))
+        return OR_EINVAL;
     if (m == 0)
         return OR_OK;
+
+    if (flags & ORACLE_PRESORT) {
+        /* G16: pack the list sorted by non-increasing weight (stable), then
+         * report each item's bin at its original position */
+        or_sort_item *it = (or_sort_item *)malloc(sizeof(or_sort_item) * (size_t)m);
+        int32_t *ws = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+        int32_t *bs = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+        if (!it || !ws || !bs) {
+            free(it); free(ws); free(bs);
+            return OR_ENOMEM;
+        }
+        for (int64_t j = 0; j < m; ++j) {
+            it[j].w = w[j];
+            it[j].pos = j;
+        }
+        qsort(it, (size_t)m, sizeof(or_sort_item), or_sort_cmp);
+        for (int64_t j = 0; j < m; ++j)
+            ws[j] = it[j].w;
+        rc = oracle_pack_ext(ws, m, B, n, heuristic, criterion, sublist_size, preopen, seed,
+                             flags & ~ORACLE_PRESORT, max_open, bs, bin_type, num_bins,
+                             total_capacity);
+        if (rc == OR_OK)
+            for (int64_t j = 0; j < m; ++j)
+                bin_of_item[it[j].pos] = bs[j];
+        free(it); free(ws); free(bs);
+        return rc;
+    }
 
     int64_t s;
     if (heuristic == OR_H1)
@@ -300,9 +460,11 @@ int oracle_pack_flags(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
     int32_t *crit = (int32_t *)malloc(sizeof(int32_t) * (size_t)s);
     int64_t *best_item_bin = (int64_t *)malloc(sizeof(int64_t) * (size_t)s);
     int32_t *best_types = (int32_t *)malloc(sizeof(int32_t) * (size_t)bin_room);
-    if (!bins || !raw || !dense || !seq || !crit || !best_item_bin || !best_types) {
+    int64_t *active = max_open > 0 ? (int64_t *)malloc(sizeof(int64_t) * (size_t)max_open) : NULL;
+    if (!bins || !raw || !dense || !seq || !crit || !best_item_bin || !best_types ||
+        (max_open > 0 && !active)) {
         free(bins); free(raw); free(dense); free(seq); free(crit);
-        free(best_item_bin); free(best_types);
+        free(best_item_bin); free(best_types); free(active);
         return OR_ENOMEM;
     }
 
@@ -318,7 +480,9 @@ int oracle_pack_flags(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
                               ? or_random_criterion(seed, (uint64_t)(a + q))
                               : criterion;
             }
-            const int64_t nb = or_membrane_run(seq, crit, k, B, n, preopen, bins, raw, remark3);
+            const int64_t nb = max_open > 0
+                ? or_membrane_run_bounded(seq, crit, k, B, n, preopen, bins, raw, max_open, active)
+                : or_membrane_run(seq, crit, k, B, n, preopen, bins, raw, remark3);
             int64_t cap_sum = 0;
             const int64_t used = or_used_bins(bins, nb, B, dense, &cap_sum);
             for (int64_t q = 0; q < k; ++q)
@@ -370,10 +534,21 @@ int oracle_pack_flags(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
     }
 
     free(bins); free(raw); free(dense); free(seq); free(crit);
-    free(best_item_bin); free(best_types);
+    free(best_item_bin); free(best_types); free(active);
     if (num_bins) *num_bins = bin_offset;
     if (total_capacity) *total_capacity = total;
     return OR_OK;
+}
+
+/* oracle_pack_ext without the bounded-space variant (max_open = 0). */
+int oracle_pack_flags(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                      int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                      int32_t preopen, uint64_t seed, int32_t flags,
+                      int32_t *bin_of_item, int32_t *bin_type,
+                      int64_t *num_bins, int64_t *total_capacity)
+{
+    return oracle_pack_ext(w, m, B, n, heuristic, criterion, sublist_size, preopen, seed, flags, 0,
+                           bin_of_item, bin_type, num_bins, total_capacity);
 }
 
 /* oracle_pack_flags with flags = 0: the readings G1-G12 as stated above. */
@@ -392,9 +567,9 @@ int oracle_pack(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
  * arrives; every permutation counted for the second heuristic) that
  * oracle_pack performs for this instance.  Returns 0 on invalid input.
  */
-uint64_t oracle_fit_tests(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
-                          int32_t heuristic, int32_t criterion, int64_t sublist_size,
-                          int32_t preopen, uint64_t seed)
+uint64_t oracle_fit_tests_ext(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                              int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                              int32_t preopen, uint64_t seed, int32_t flags, int64_t max_open)
 {
     int32_t *boi = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
     int32_t *bt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
@@ -404,10 +579,17 @@ uint64_t oracle_fit_tests(const int32_t *w, int64_t m, const int32_t *B, int32_t
     }
     or_fit_tests = 0;
     int64_t nb = 0, tot = 0;
-    const int rc = oracle_pack(w, m, B, n, heuristic, criterion, sublist_size, preopen, seed,
-                               boi, bt, &nb, &tot);
+    const int rc = oracle_pack_ext(w, m, B, n, heuristic, criterion, sublist_size, preopen, seed,
+                                   flags, max_open, boi, bt, &nb, &tot);
     free(boi); free(bt);
     return rc == OR_OK ? or_fit_tests : 0;
+}
+
+uint64_t oracle_fit_tests(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
+                          int32_t heuristic, int32_t criterion, int64_t sublist_size,
+                          int32_t preopen, uint64_t seed)
+{
+    return oracle_fit_tests_ext(w, m, B, n, heuristic, criterion, sublist_size, preopen, seed, 0, 0);
 }
 
 /*

@@ -23,7 +23,13 @@ mathematics fixes:
     the second heuristic's key layout (reading G12) to the first heuristic's
     RANDOM packing;
   * invariants of any packing (each item once, no bin over capacity, total =
-    sum of used capacities >= sum of weights).
+    sum of used capacities >= sum of weights);
+  * the bounded-space variant (reading G15): a bound no packing can reach
+    gives the unbounded packing, one open bin makes FF, BF and WF identical,
+    and no step ever meets more open bins than the bound;
+  * the offline pre-sort (reading G16): with one bin type FF and BF in
+    decreasing order are the textbook FFD and BFD, and a list already in
+    non-increasing order is packed as it stands.
 
 The same functions run against copies of the oracle with planted mistakes
 (tests/test_oracle_mutants.py) to show that each plausible slip is caught.
@@ -180,7 +186,7 @@ def pin_hand_examples(lib):
     d = load_golden("hand_examples.json")
     for ex in d["examples"]:
         r = lib.pack(ex["w"], ex["B"], ex["heuristic"], ex["criterion"], ex["sublist_size"],
-                     ex["preopen"], ex["seed"], ex.get("flags", 0))
+                     ex["preopen"], ex["seed"], ex.get("flags", 0), ex.get("max_open", 0))
         assert r.status == 0, ex["name"]
         assert r.bin_of_item.tolist() == ex["bin_of_item"], ex["name"]
         assert r.bin_type.tolist() == ex["bin_type"], ex["name"]
@@ -378,7 +384,12 @@ def pin_errors(lib):
     assert lib.pack([101, 0], B, 1, 0).status == -2
     assert lib.pack([1], B, 3, 0).status == -1              # heuristic id
     assert lib.pack([1], B, 1, 4).status == -1              # criterion id
-    assert lib.pack([1], B, 1, 0, 0, 0, 0, 2).status == -1  # unknown flag
+    assert lib.pack([1], B, 1, 0, 0, 0, 0, 4).status == -1  # unknown flag
+    assert lib.pack([1], B, 1, 0, max_open=-1).status == -1            # bound >= 0
+    assert lib.pack([1], B, 2, 0, 5, max_open=3).status == -1          # bounded: first heuristic only
+    assert lib.pack([1], B, 1, 0, 0, 0, 0, 1, max_open=3).status == -1  # not with Remark 3
+    assert lib.pack([0, 2], B, 1, 0, 0, 0, 0, 2).status == -1           # pre-sort: list order decides
+    assert lib.pack([101, 0], B, 1, 0, 0, 0, 0, 2).status == -2
     assert lib.pack([1], B, 1, 0, -1).status == -1          # sublist size
     assert lib.pack([1], B, 2, 0, 13).status == -1          # H2 sublist <= 12
     assert lib.pack([1], B, 1, 0, 0, 2).status == -1        # preopen flag
@@ -412,9 +423,84 @@ def pin_fit_tests(lib, seed=16):
     assert lib.fit_tests([5], [5, 3], 1, 1, 0, 1) == 2
 
 
+def pin_bounded_space(lib, seed=18):
+    """Reading G15 (Section 1's bounded-space FF / BF / WF).  (a) A bound of
+    2m + n open bins is never reached, and closing a full bin never changes a
+    later choice (a full bin holds no further item), so the packing is the
+    unbounded one.  (b) With one open bin at a time there is nothing to
+    choose: FF, BF and WF pack alike.  (c) The fit tests per item are the open
+    bins, so a run never makes more than K per item; when every weight is B_1
+    each bin fills and closes at once and only the empty bin it divided off
+    is open for the next item: m - 1 fit tests (unbounded: (m-1)(m+2)/2).
+    Plus the invariants of any packing."""
+    rng = np.random.default_rng(seed)
+    for t in range(60):
+        m = int(rng.integers(0, 50))
+        n = int(rng.integers(1, 5))
+        B = sorted(rng.choice(np.arange(2, 60), size=n, replace=False).tolist(), reverse=True)
+        w = rng.integers(1, B[0] + 1, size=m).tolist()
+        pre = int(rng.integers(0, 2))
+        for crit in (0, 1, 2, 3):
+            ref = lib.pack(w, B, 1, crit, 0, pre, t)
+            big = lib.pack(w, B, 1, crit, 0, pre, t, max_open=2 * m + n)
+            assert big.bin_of_item.tolist() == ref.bin_of_item.tolist(), (w, B, crit, pre)
+            assert big.bin_type.tolist() == ref.bin_type.tolist() and big.total == ref.total
+        one = [lib.pack(w, B, 1, crit, 0, pre, max_open=1) for crit in (0, 1, 2)]
+        assert one[0].bin_of_item.tolist() == one[1].bin_of_item.tolist() == one[2].bin_of_item.tolist(), (w, B)
+        for K in (1, 2, 3, 7):
+            crit = int(rng.integers(0, 4))
+            r = lib.pack(w, B, 1, crit, 0, pre, t, max_open=K)
+            check_packing(w, B, r)
+            ft = lib.fit_tests(w, B, 1, crit, 0, pre, t, max_open=K)
+            assert ft <= K * m, (w, B, K)
+            if m > 0:
+                assert lib.fit_tests([B[0]] * m, B, 1, crit, 0, 0, t, max_open=K) == m - 1
+
+
+def textbook_decreasing(w, C, fit):
+    """FFD / BFD: sort by non-increasing weight (stable), then the textbook
+    first-fit or best-fit; bins reported per original item."""
+    order = sorted(range(len(w)), key=lambda j: -w[j])
+    idx, nb = fit([w[j] for j in order], C)
+    out = [0] * len(w)
+    for pos, j in enumerate(order):
+        out[j] = idx[pos]
+    return out, nb
+
+
+def pin_presort(lib, trials=120, seed=19):
+    """Reading G16.  With one bin type, FF and BF on the list sorted by
+    non-increasing weight are the textbook First-Fit-Decreasing and
+    Best-Fit-Decreasing (the n = 1 reduction of pin_textbook_n1 applied to
+    the sorted list); a list that is already non-increasing packs exactly as
+    without the flag; any pre-sorted packing satisfies the invariants."""
+    rng = np.random.default_rng(seed)
+    for t in range(trials):
+        C = int(rng.integers(1, 60))
+        m = int(rng.integers(0, 40))
+        w = rng.integers(1, C + 1, size=m).tolist()
+        for crit, ref in ((0, textbook_first_fit), (1, textbook_best_fit)):
+            r = lib.pack(w, [C], 1, crit, 0, 0, 0, 2)
+            idx, nbins = textbook_decreasing(w, C, ref)
+            assert r.status == 0
+            assert r.bin_of_item.tolist() == idx, (crit, C, w)
+            assert r.num_bins == nbins and r.total == nbins * C
+        n = int(rng.integers(1, 5))
+        B = sorted(rng.choice(np.arange(2, 80), size=n, replace=False).tolist(), reverse=True)
+        w = sorted(rng.integers(1, B[0] + 1, size=m).tolist(), reverse=True)
+        h = int(rng.integers(1, 3))
+        s = int(rng.integers(0, 6)) if h == 2 else 0
+        crit = int(rng.integers(0, 4))
+        a = lib.pack(w, B, h, crit, s, 0, t)
+        b = lib.pack(w, B, h, crit, s, 0, t, 2)
+        assert a.bin_of_item.tolist() == b.bin_of_item.tolist() and a.total == b.total, (w, B, h, crit)
+        rng.shuffle(w)
+        check_packing(w, B, lib.pack(w, B, h, crit, s, int(rng.integers(0, 2)), t, 2))
+
+
 ALL_PINS = [pin_hand_examples, pin_splitmix64, pin_random_criterion_vectors, pin_textbook_n1, pin_optimum,
             pin_closed_forms, pin_h2_is_best_permutation, pin_h2_random_key, pin_invariants, pin_errors,
-            pin_fit_tests]
+            pin_fit_tests, pin_bounded_space, pin_presort]
 
 
 def failing_pins(lib):

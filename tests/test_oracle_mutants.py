@@ -83,18 +83,46 @@ MUTANTS = {
     "h2_random_key_rank_dropped": ("? (uint64_t)((g * 720 + rank) * 8 + q)", "? (uint64_t)((g * 720) * 8 + q)"),
     "h2x_random_key_stride_8": ("+ (uint64_t)rank) * 16u + (uint64_t)q)", "+ (uint64_t)rank) * 8u + (uint64_t)q)"),
     "h2_random_layout_switch_off_by_one": ("seed, s <= 6\n", "seed, s <= 5\n"),
+    "bounded_newest_closes": ("        or_close_at(active, na, 0);", "        or_close_at(active, na, *na - 1);"),
+    "bounded_limit_off_by_one": ("    if (*na >= max_open)\n        or_close_at", "    if (*na > max_open)\n        or_close_at"),
+    "bounded_full_bins_stay_open": ("            if (after == cap)              /* completely filled: the bin closes */\n                or_close_at(active, &na, chosen_at);",
+                                    "            if (0)\n                or_close_at(active, &na, chosen_at);"),
+    "bounded_division_unbounded": ("            if (2 * before < cap && cap <= 2 * after) {\n                or_make_room(active, &na, max_open);",
+                                   "            if (2 * before < cap && cap <= 2 * after) {\n                if (na >= max_open) { bins[nb].load = 0; bins[nb].type = bins[chosen].type; ++nb; raw[q] = chosen; continue; }"),
+    "presort_ascending": ("        return x->w > y->w ? -1 : 1;", "        return x->w < y->w ? -1 : 1;"),
+    "presort_ties_reversed": ("    return x->pos < y->pos ? -1 : (x->pos > y->pos ? 1 : 0);", "    return x->pos > y->pos ? -1 : (x->pos < y->pos ? 1 : 0);"),
+    "presort_bins_not_mapped_back": ("                bin_of_item[it[j].pos] = bs[j];", "                bin_of_item[j] = bs[j];"),
     "last_partial_sublist_dropped": ("for (int64_t g = 0; g * s < m; ++g) {", "for (int64_t g = 0; (g + 1) * s <= m; ++g) {"),
 }
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_planted_mistake_is_caught(name, tmp_path):
+    """The mistake planted at every place its anchor occurs."""
     old, new = MUTANTS[name]
     src = oracle.source_text()
-    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
     path = oracle.compile_variant(src.replace(old, new), str(tmp_path / f"mut_{name}.so"))
     bad = failing_pins_isolated(path)
     assert bad, f"planted mistake {name} passed every pin"
+
+
+# Anchors shared by the unbounded membrane run and the bounded-space run
+# (reading G15), which follows it in the source: the same slip planted in the
+# bounded run alone must be caught too.
+SHARED = sorted(k for k, (old, _) in MUTANTS.items() if oracle.source_text().count(old) == 2)
+
+
+@pytest.mark.parametrize("name", SHARED)
+def test_planted_mistake_in_bounded_run_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = oracle.source_text()
+    cut = src.index("static int64_t or_membrane_run_bounded(")
+    head, tail = src[:cut], src[cut:]
+    assert head.count(old) == 1 and tail.count(old) == 1, name
+    path = oracle.compile_variant(head + tail.replace(old, new), str(tmp_path / f"mutb_{name}.so"))
+    bad = failing_pins_isolated(path)
+    assert bad, f"planted mistake {name} (bounded run only) passed every pin"
 
 
 def test_unmodified_copy_passes(tmp_path):
