@@ -248,6 +248,104 @@ def exhaustive_search(native, I, dev, stream):
     return res
 
 
+def latency_roof(native, batch, dev, stream, flush, name, kernel_ms, sm_mhz, reps):
+    """The bound that binds the batched first heuristic: each membrane
+    system is a chain of dependent item steps (Rule 3 takes one item per
+    step), so a pass cannot end before its largest system, packed alone.
+    Reported: that system's solo kernel time (CUDA events on the launching
+    stream, L2 flushed), its cycles per item at the sampled SM clock, and the
+    batched kernel's time over it."""
+    import torch
+    from paper_1602_08735_gb300 import instances as I
+    h, c, s_ = dict((p[0], p[1:]) for p in PASSES)[name]
+    big = int(np.argmax(np.diff(batch.w_off)))
+    one = I.from_instances([batch.instance(big)])
+    db1 = native.DeviceBatch.from_host(one, device=dev)
+    out1 = native.DeviceResult.empty(1, db1.total_items, device=dev)
+    assert native.pack_batch(db1, out1, h, c, s_, stream=stream) == 0
+    native.kernel_timing_enable(True)
+    native.kernel_timing_read()
+    for _ in range(reps):
+        flush.zero_()
+        assert native.pack_batch(db1, out1, h, c, s_, stream=stream) == 0
+    t = native.kernel_timing_read()
+    native.kernel_timing_enable(False)
+    solo = float(np.mean(t))
+    m = db1.total_items
+    return {"bound": "per-system dependent chain (largest system packed alone)", "pass": name,
+            "largest_m": m, "solo_kernel_ms": solo, "sm_mhz": sm_mhz,
+            "chain_cycles_per_item": solo * 1e-3 * sm_mhz * 1e6 / m,
+            "batched_kernel_ms": kernel_ms, "kernel_over_solo": kernel_ms / solo if solo else None}
+
+
+def serve_stream(native, reqs, rate):
+    """Submit reqs at their arrival times (rate None: all at once) and poll
+    them all; returns the server's stats and the wall time."""
+    items = sum(len(w) for (_, w, _) in reqs)
+    with native.Server(device_mem_budget=8 << 30, max_slots=64, lanes=32) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for (t_arr, w, B) in reqs:
+            if rate is not None:
+                now = time.perf_counter() - t0
+                if t_arr > now:
+                    time.sleep(t_arr - now)
+            tickets.append(srv.submit(w, B, 1, 1))
+        bad = 0
+        for t in tickets:
+            rc, _ = srv.poll(t)
+            bad += rc != 0
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    return {"rate_per_s": rate, "requests": len(reqs), "items": items, "failed": bad,
+            "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
+            "wait_p50_ms": st["wait_p50_us"] / 1e3, "wait_p99_ms": st["wait_p99_us"] / 1e3,
+            "service_p50_ms": st["service_p50_us"] / 1e3, "service_p99_ms": st["service_p99_us"] / 1e3,
+            "items_per_s": items / wall, "requests_per_s": len(reqs) / wall, "wall_s": wall,
+            "busy_s": st["busy_s"]}
+
+
+def serving_sweep(native, I, n_req):
+    """Config 5 through the continuous-batching server: capacity with every
+    request queued at once (requests/s over the server's busy time), then
+    Poisson arrivals at 50 %, 90 % and 110 % of that capacity."""
+    sat = serve_stream(native, I.config5(seed=5, num_requests=n_req, rate_per_s=1e9), None)
+    cap = sat["requests"] / max(sat["busy_s"], 1e-9)
+    points = []
+    for frac in (0.5, 0.9, 1.1):
+        rate = frac * cap
+        pt = serve_stream(native, I.config5(seed=5, num_requests=n_req, rate_per_s=rate), rate)
+        pt["fraction_of_capacity"] = frac
+        points.append(pt)
+    return {"pass": "H1-BF per request", "m": "log-uniform [100, 1e5]", "capacity_requests_per_s": cap,
+            "capacity_items_per_s": sat["items"] / max(sat["busy_s"], 1e-9), "saturated": sat,
+            "points": points}
+
+
+def variants_side(native, db, dev, stream, flush):
+    """One config-3 first-heuristic BF pass with each option (event-timed
+    call of the batched entry point, L2 flushed)."""
+    import torch
+    out = native.DeviceResult.empty(db.N, db.total_items, device=dev)
+    res = {}
+    for label, kw in (("plain_method", {}), ("presort", dict(flags=native.PRESORT)),
+                      ("remark3", dict(flags=native.REMARK3)), ("bounded_K8", dict(max_open=8)),
+                      ("bounded_K32", dict(max_open=32))):
+        assert native.pack_batch(db, out, 1, 1, stream=stream, **kw) == 0
+        e0, e1 = _events(torch)
+        ms = 0.0
+        for _ in range(3):
+            flush.zero_()
+            e0.record(stream)
+            assert native.pack_batch(db, out, 1, 1, stream=stream, **kw) == 0
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1) / 3
+        res[label] = {"ms": ms, "items_per_s": db.total_items / (ms / 1e3),
+                      "total_capacity": int(out.total[:db.N].sum().item())}
+    return res
+
+
 def serving_run(native, I, rate, n_req):
     """Config 5: Poisson arrivals through the continuous-batching server."""
     reqs = I.config5(seed=5, num_requests=n_req, rate_per_s=rate)
@@ -342,7 +440,7 @@ def cpu_baseline(batch, sample_n: int, seed: int = 123):
     rng = np.random.default_rng(seed)
     idx = np.sort(rng.choice(batch.N, size=min(sample_n, batch.N), replace=False))
     sub = batch.subset(idx)
-    cores = os.cpu_count() or 1
+    cores = oracle.host_cores()                   # the process's CPU affinity set
     t0 = time.perf_counter()
     for (_, h, c, s) in PASSES:
         oracle.pack_many(sub.w_all, sub.w_off, sub.B_all, sub.B_off, h, c, s, 0, 0, nthreads=cores)
@@ -355,6 +453,7 @@ def cpu_baseline(batch, sample_n: int, seed: int = 123):
         oracle.pack_many(one.w_all, one.w_off, one.B_all, one.B_off, h, c, s, 0, 0, nthreads=1)
     dt1 = time.perf_counter() - t1
     return {"value": items / dt, "unit": "items/s", "cores": cores, "kind": "oracle",
+            "nproc": cores, "os_cpu_count": os.cpu_count(),
             "sample": f"{len(idx)} of {batch.N} instances ({sub.total_items} items) x 4 passes "
                       f"(H1 FF/BF/WF, H2 BF), {dt:.2f} s wall",
             "one_core": {"value": 4 * one.total_items / dt1, "unit": "items/s", "cores": 1,
@@ -370,6 +469,7 @@ def run_reference(args, ws, rank):
     sample_n = min(args.cpu_sample, batch.N)
     import oracle
     oracle.build()
+    cores = oracle.host_cores()
     rng = np.random.default_rng(7)
     times, items = [], 0
     for k in range(args.warmup + args.steps):
@@ -377,13 +477,12 @@ def run_reference(args, ws, rank):
         sub = batch.subset(idx)
         t0 = time.perf_counter()
         for (_, h, c, s) in PASSES:
-            oracle.pack_many(sub.w_all, sub.w_off, sub.B_all, sub.B_off, h, c, s, 0, 0)
+            oracle.pack_many(sub.w_all, sub.w_off, sub.B_all, sub.B_off, h, c, s, 0, 0, nthreads=cores)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
             items += 4 * sub.total_items
     value = items / sum(times)
-    cores = os.cpu_count() or 1
     line = {
         "impl": "reference", "metric": "items packed/s", "value": value, "unit": "items/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -392,6 +491,7 @@ def run_reference(args, ws, rank):
         "config": {"workload": WORKLOAD, "instances": batch.N, "sample_instances_per_step": sample_n,
                    "passes": [p[0] for p in PASSES]},
         "cpu_baseline": {"value": value, "unit": "items/s", "cores": cores, "kind": "oracle",
+                         "nproc": cores, "os_cpu_count": os.cpu_count(),
                          "sample": f"{sample_n} random instances of {batch.N} per step x 4 passes"},
         "e2e": {"value": value, "unit": "items/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -514,30 +614,33 @@ def run_ours(args, ws, rank, local):
     value = items_per_step / (step_ms / 1e3)
     clocks = clk.summary()
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the C ABI with host buffers: vsbpp_pack_batch_host
+    # takes pinned host CSR arrays, copies them to the device, packs and
+    # copies every output back inside the call (one call per pass, serial on
+    # the library's stream); host wall clock around the synchronous calls
     pin = lambda t: t.cpu().pin_memory()
     h_in = [pin(db.w_all), pin(db.w_off), pin(db.B_all), pin(db.B_off)]
-    h_out = [[torch.empty_like(x, device="cpu").pin_memory() for x in
-              (o.bin_of_item, o.bin_type, o.num_bins, o.total, o.status)] for o in outs]
-    h2d = sum(int(x.numel() * x.element_size()) for x in h_in)
-    d2h = sum(int(x.numel() * x.element_size()) for row in h_out for x in row)
+    h_out = [native.HostResult(*(torch.empty_like(x, device="cpu").pin_memory() for x in
+                                 (o.status, o.bin_of_item, o.bin_type, o.num_bins, o.total))) for o in outs]
+    h2d = len(PASSES) * sum(int(x.numel() * x.element_size()) for x in h_in)
+    d2h = sum(int(x.numel() * x.element_size()) for o in h_out
+              for x in (o.status, o.bin_of_item, o.bin_type, o.num_bins, o.total))
     e2e_steps = max(1, min(args.steps, 5))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for (name, h, c, s_), o in zip(PASSES, h_out):          # warm-up: library buffers sized
+        assert native.pack_batch_host(*h_in, o, h, c, s_, max_m=db.max_m) == 0, name
     e2e_ms = 0.0
     for k in range(e2e_steps):
         flush.zero_()
-        e0.record(stream)
-        for dst, src in zip((db.w_all, db.w_off, db.B_all, db.B_off), h_in):
-            dst.copy_(src, non_blocking=True)
-        step()
-        for o, row in zip(outs, h_out):
-            for src, dst in zip((o.bin_of_item, o.bin_type, o.num_bins, o.total, o.status), row):
-                dst.copy_(src, non_blocking=True)
-        e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
+        t0 = time.perf_counter()
+        for (name, h, c, s_), o in zip(PASSES, h_out):
+            rc = native.pack_batch_host(*h_in, o, h, c, s_, max_m=db.max_m)
+            assert rc == 0, (name, native.strerror(rc))
+        e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_ms = max_over_ranks(e2e_ms / e2e_steps, ws)
     e2e_value = items_per_step / (e2e_ms / 1e3)
+    for o, d in zip(h_out, outs):                            # the host call's results = the device path's
+        assert torch.equal(o.total[:db.N], d.total[:db.N].cpu())
 
     # ---- plain path: one launch per instance, one step
     plain = None
@@ -570,6 +673,10 @@ def run_ours(args, ws, rank, local):
         kernel_ms[name] = float(np.mean(t)) if t else None
     native.kernel_timing_enable(False)
     roofline = roofline_of(torch, dev, kernel_ms, fit_tests)
+    if roofline:
+        roofline["latency"] = latency_roof(native, batch, dev, stream, flush, roofline["pass"],
+                                           roofline["kernel_ms"], clocks.get("sm_mhz") or 2070.0,
+                                           max(args.steps, 3))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -579,7 +686,8 @@ def run_ours(args, ws, rank, local):
     if not args.no_side:
         side["single_instance"] = single_instance_latency(native, I, dev, stream)
         side["config4"] = config4_pass(native, I, dev, stream, args.config4_instances, args.config4_m)
-        side["serving"] = serving_run(native, I, args.serve_rate, args.serve_requests)
+        side["serving"] = serving_sweep(native, I, args.serve_requests)
+        side["variants"] = variants_side(native, db, dev, stream, flush)
         side["exhaustive"] = exhaustive_search(native, I, dev, stream)
 
     if rank == 0:
@@ -598,7 +706,9 @@ def run_ours(args, ws, rank, local):
             "passes_ms": {p[0]: float(t) for p, t in zip(PASSES, pass_ms)},
             "schedule": "H1 FF, BF, WF back to back on one stream; H2 BF on a second stream beside them",
             "serial_ms_per_step": serial_ms,
-            "e2e": {"value": e2e_value, "unit": "items/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": "items/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "call": "vsbpp_pack_batch_host (pinned host CSR in, host outputs back), one call per pass",
+                    "ms_per_step": e2e_ms},
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "plain": plain,
             "roofline": roofline,

@@ -44,6 +44,9 @@
  * Threading: every entry point may be called from any host thread; calls are
  * serialised internally per process.  Device entry points are asynchronous
  * with respect to the host and ordered on the caller's stream.
+ *
+ * Parameter layout changed in 1.1.0: `reserved` became `flags` and `max_open`
+ * was appended (struct size 40 bytes).
  */
 #ifndef VSBPP_H
 #define VSBPP_H
@@ -55,8 +58,21 @@
 extern "C" {
 #endif
 
-#define VSBPP_VERSION 10000          /* 1.0.0 */
+#define VSBPP_VERSION 10100          /* 1.1.0 */
 #define VSBPP_MAX_TYPES 32           /* bin types per instance */
+#define VSBPP_MAX_OPEN 32            /* largest bound of the bounded-space variant */
+
+/* Option flags (vsbpp_params.flags). */
+#define VSBPP_REMARK3 1   /* Rule 5 with Remark 3 of Section 6.3 read as a condition: a bin of a
+                             type divides off a new one only if every bin of that type then
+                             holds at least half its capacity (a consequence of Rule 5 under the
+                             literal Rule 2, not once a bin can open below half)               */
+#define VSBPP_PRESORT 2   /* offline pre-sort: the list is packed in non-increasing weight order
+                             (equal weights keep their list order), as the decreasing-order
+                             heuristics of the prior work in Section 5 do; bin_of_item is still
+                             reported per item at its original position, RANDOM keys are the
+                             sorted positions, and validation still reports the first
+                             offending item in the caller's order                               */
 #define VSBPP_H2_MAX_SUBLIST 12      /* s <= 6: Section 6.4 (s! <= 720); 7..12: exhaustive search */
 
 /* Selection criterion of Rule 3 / Rule 4 (Section 1 defines FF, BF, WF). */
@@ -65,8 +81,9 @@ typedef enum {
     VSBPP_BF = 1,      /* bin with the least room left that fits; lowest index */
     VSBPP_WF = 2,      /* bin with the most room left; lowest index            */
     VSBPP_RANDOM = 3   /* per item, c = SplitMix64(seed, key) mod 3 (0=FF,1=BF,2=WF);
-                          key = item index within the instance (first heuristic)
-                          or (sublist*720 + permutation rank)*8 + step (second) */
+                          key = item index within the instance (first heuristic),
+                          (sublist*720 + permutation rank)*8 + step (second, s <= 6)
+                          or (sublist*12! + rank)*16 + step (second, s = 7..12) */
 } vsbpp_criterion;
 
 /* The two heuristics of Section 6. */
@@ -89,8 +106,21 @@ typedef struct {
     int32_t  preopen;       /* 0: no bin open at the start (a bin opens when nothing
                                fits).  1: literal Rule 2, one empty bin of every type,
                                types in order, before the first item.                    */
-    int32_t  reserved;      /* must be 0                                                 */
+    int32_t  flags;         /* VSBPP_REMARK3 | VSBPP_PRESORT, or 0; other bits: EINVAL.
+                               VSBPP_REMARK3 with sublists of 7..12 items: EINVAL         */
     uint64_t seed;          /* used by VSBPP_RANDOM only                                 */
+    int64_t  max_open;      /* 0: no bound (the method as the paper states it).  K >= 1:
+                               the bounded-space variant of Section 1's FF / BF / WF
+                               ("keeps only a specific number of bins open"): only the K or
+                               fewer open bins take part in Rule 4's fit test, a bin
+                               closes as soon as it is completely filled, and before a bin
+                               is created (no open bin holds the item, a Rule 5 division,
+                               a Rule 2 bin) while K are open, the open bin with the lowest
+                               creation index closes.  Closed bins keep their items and
+                               count in the objective.  First heuristic with one membrane
+                               system per instance (sublist_size 0 or >= every m), without
+                               VSBPP_REMARK3, else EINVAL; K <= VSBPP_MAX_OPEN, else
+                               VSBPP_ECAPACITY; K < 0: EINVAL.                           */
 } vsbpp_params;
 
 /* Status codes. */
@@ -187,6 +217,24 @@ int vsbpp_pack_batch(int64_t N, const int32_t *w_all, const int64_t *w_off,
                      void *stream);
 
 /*
+ * vsbpp_pack_batch_host -- vsbpp_pack_batch for a batch held in HOST memory;
+ * synchronous.  Same CSR arguments and results as vsbpp_pack_batch, but every
+ * array is a host pointer (pinned, e.g. from cudaHostAlloc, or pageable).
+ * The library copies the inputs to device buffers it owns on the current
+ * device, packs them with the same kernels on its own stream for that device,
+ * copies the results back and returns when they are in place: the whole
+ * host-to-host path in one call.  Pinned buffers are copied directly;
+ * pageable ones are staged through the library's pinned buffers.  max_m: as
+ * for vsbpp_pack_batch (0 lets the library read it off w_off).  Returns a
+ * host-side status; per-instance codes are in status[].
+ */
+int vsbpp_pack_batch_host(int64_t N, const int32_t *w_all, const int64_t *w_off,
+                          const int32_t *B_all, const int32_t *B_off, int64_t max_m,
+                          const vsbpp_params *p,
+                          int32_t *bin_of_item_all, int32_t *bin_type_all,
+                          int64_t *num_bins, int64_t *total, int32_t *status);
+
+/*
  * vsbpp_pack_batch_noalloc -- vsbpp_pack_batch for callers that cannot
  * allocate device memory.  (The paper has no counterpart: this is a property
  * of the library, not of the method.)
@@ -202,7 +250,8 @@ int vsbpp_pack_batch(int64_t N, const int32_t *w_all, const int64_t *w_off,
  *
  * Arguments and results as vsbpp_pack_batch, restricted to the first
  * heuristic with one membrane system per instance (sublist_size 0 or
- * >= max_m): N <= VSBPP_NOALLOC_MAX_INSTANCES and max_m <=
+ * >= max_m), without option flags or a bound (flags = max_open = 0, else
+ * VSBPP_EINVAL): N <= VSBPP_NOALLOC_MAX_INSTANCES and max_m <=
  * VSBPP_NOALLOC_MAX_ITEMS, else VSBPP_ECAPACITY; other parameters as in
  * vsbpp_pack_batch, a second-heuristic request gives VSBPP_EINVAL.
  * Instances with B_1 > 32767 get status VSBPP_ECAPACITY.
@@ -352,14 +401,18 @@ int vsbpp_tune_load(const char *path);
  *     host buffers; VSBPP_ETIMEDOUT if it is not finished in time.  A ticket
  *     is released by the poll that returns its result.
  *   vsbpp_server_stats reports completed requests and latency percentiles
- *     (submit to completion, microseconds) over the last completed requests.
+ *     over the last completed requests, in microseconds: submit to
+ *     completion, and its two parts -- the wait in the host queue (submit to
+ *     admission) and the service time (admission to completion).
  */
 typedef struct vsbpp_server vsbpp_server;
 typedef struct {
     int64_t completed;
     int64_t items_packed;
-    double  p50_us, p99_us, max_us;
+    double  p50_us, p99_us, max_us;        /* submit to completion                          */
     double  busy_s;          /* seconds from the first admission to the last completion */
+    double  wait_p50_us, wait_p99_us;      /* submit to admission (queueing)                */
+    double  service_p50_us, service_p99_us;  /* admission to completion (copies + packing)  */
 } vsbpp_server_stats_t;
 
 int vsbpp_server_create(size_t device_mem_budget, int32_t max_slots, int32_t lanes,

@@ -173,6 +173,19 @@ struct Scratch {
     int32_t* spill_list = nullptr; int64_t cap_spill_list = 0;  // systems to repack at full size
     int32_t* spill_list2 = nullptr; int64_t cap_spill_list2 = 0;  // ... and those beyond it (global memory)
     unsigned long long* h2x_best = nullptr; int64_t cap_h2x_best = 0;  // exhaustive search: best key per sublist
+    // offline pre-sort: sorted weights, permutation, radix buffer, sorted-order bin ids, caller-order status
+    int32_t* ps_w = nullptr;    int64_t cap_ps_w = 0;
+    int32_t* ps_perm = nullptr; int64_t cap_ps_perm = 0;
+    int32_t* ps_tmp = nullptr;  int64_t cap_ps_tmp = 0;
+    int32_t* ps_boi = nullptr;  int64_t cap_ps_boi = 0;
+    int32_t* ps_stat = nullptr; int64_t cap_ps_stat = 0;
+    int32_t* bk_rec = nullptr;  int64_t cap_bk_rec = 0;     // bounded space: per-bin records
+    // host-memory batch call: device copies of the CSR offsets and the per-instance outputs
+    int64_t* hb_woff = nullptr; int64_t cap_hb_woff = 0;
+    int32_t* hb_Boff = nullptr; int64_t cap_hb_Boff = 0;
+    int64_t* hb_nb = nullptr;   int64_t cap_hb_nb = 0;
+    int64_t* hb_tot = nullptr;  int64_t cap_hb_tot = 0;
+    int32_t* hb_st = nullptr;   int64_t cap_hb_st = 0;
 
     uint32_t* hist() const { return reinterpret_cast<uint32_t*>(fixed); }
     int64_t* cursor() const { return reinterpret_cast<int64_t*>(fixed + kClasses * kBuckets * 4); }
@@ -252,7 +265,9 @@ struct Scratch {
 
     void release() {
         void* bufs[] = {cls, order, nu, unit_base, unit_count, unit_total, local_types, fixed, kc_slots,
-                        spill_list, spill_list2, h2x_best, h_w, h_B, h_boi, h_bt, h_small};
+                        spill_list, spill_list2, h2x_best, h_w, h_B, h_boi, h_bt, h_small,
+                        ps_w, ps_perm, ps_tmp, ps_boi, ps_stat, bk_rec, hb_woff, hb_Boff, hb_nb,
+                        hb_tot, hb_st};
         for (void* q : bufs) free_buf(q);
         for (void* q : retired) free_buf(q);
         *this = Scratch();
@@ -274,6 +289,79 @@ Scratch& scratch_for(cudaStream_t st) {
         it->second.ord = st;
     }
     return it->second;
+}
+
+// The library's own stream and pinned staging on one device, for the calls
+// that take host buffers (vsbpp_pack, vsbpp_pack_batch_host).  Pageable host
+// memory is copied through two pinned chunks, so the host copy of one chunk
+// overlaps the transfer of the other.
+struct HostCtx {
+    static constexpr size_t kChunk = size_t(8) << 20;
+    cudaStream_t st = nullptr;
+    void* pin[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+
+    int init() {
+        if (st) return VSBPP_OK;
+        VS_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            VS_TRY(cudaHostAlloc(&pin[k], kChunk, cudaHostAllocDefault));
+            VS_TRY(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
+        }
+        return VSBPP_OK;
+    }
+    static bool pinned(const void* p) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return a.type == cudaMemoryTypeHost;
+    }
+    // host -> device, enqueued on st (pageable sources go through the chunks)
+    int to_device(void* dst, const void* src, size_t bytes) {
+        if (bytes == 0) return VSBPP_OK;
+        if (pinned(src)) return record(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+        int k = 0;
+        for (size_t off = 0; off < bytes; off += kChunk, k ^= 1) {
+            const size_t n = std::min(kChunk, bytes - off);
+            VS_TRY(cudaEventSynchronize(ev[k]));          // the chunk's previous transfer is done
+            std::memcpy(pin[k], static_cast<const char*>(src) + off, n);
+            VS_TRY(cudaMemcpyAsync(static_cast<char*>(dst) + off, pin[k], n, cudaMemcpyHostToDevice, st));
+            VS_TRY(cudaEventRecord(ev[k], st));
+        }
+        return VSBPP_OK;
+    }
+    // device -> host after the work enqueued on st; returns when the copy is done
+    int to_host(void* dst, const void* src, size_t bytes) {
+        if (bytes == 0) return VSBPP_OK;
+        if (pinned(dst)) return record(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+        int k = 0;
+        size_t prev_off = 0, prev_n = 0;
+        for (size_t off = 0; off < bytes; off += kChunk, k ^= 1) {
+            const size_t n = std::min(kChunk, bytes - off);
+            VS_TRY(cudaMemcpyAsync(pin[k], static_cast<const char*>(src) + off, n, cudaMemcpyDeviceToHost, st));
+            VS_TRY(cudaEventRecord(ev[k], st));
+            if (prev_n) {                                  // the other chunk, copied while this one moves
+                VS_TRY(cudaEventSynchronize(ev[k ^ 1]));
+                std::memcpy(static_cast<char*>(dst) + prev_off, pin[k ^ 1], prev_n);
+            }
+            prev_off = off;
+            prev_n = n;
+        }
+        VS_TRY(cudaEventSynchronize(ev[k ^ 1]));
+        std::memcpy(static_cast<char*>(dst) + prev_off, pin[k ^ 1], prev_n);
+        return VSBPP_OK;
+    }
+};
+
+// The host context of the current device (created on first use there).
+HostCtx* host_ctx() {
+    static std::map<int, HostCtx> ctx;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    HostCtx& c = ctx[dev];
+    return c.init() == VSBPP_OK ? &c : nullptr;
 }
 
 // ------------------------------------------------------------ launch plan
@@ -314,6 +402,11 @@ struct LaunchPlan {
     KCShape kc{};
     int h2_threads = 0, h2_smem = 0, h2_grid = 0, h2_max_bins = 0;
     bool h2x = false;     // sublists of 7..12 items: the exhaustive search
+    bool h2_generic = false;   // second heuristic in the one-thread-per-permutation kernel
+    bool presort = false;      // VSBPP_PRESORT: sort, pack the sorted copy, scatter back
+    bool remark3 = false;      // VSBPP_REMARK3
+    bool bounded = false;      // max_open > 0: the bounded-space kernel
+    int bk_grid = 0;
     int prep_grid = 0;
 };
 
@@ -321,20 +414,21 @@ int round4(int64_t x) { return static_cast<int>((x + 3) & ~int64_t(3)); }
 // Shared-memory kernels read whole 128-bin segments.
 int round128(int64_t x) { return static_cast<int>((x + 127) & ~int64_t(127)); }
 
-// Shared memory of one group: the one-warp kernel's layout where it applies.
-int group_bytes(bool wide, int G, int slot_cap, int chunk, int bf_index) {
-    if (!wide && G == 1 && h1w_supported(slot_cap)) return h1w_bytes(slot_cap, bf_index);
+// Shared memory of one group: the one-warp kernel's layout where it applies
+// (h1w_ok: the one-warp kernel may be used; not with VSBPP_REMARK3).
+int group_bytes(bool wide, int G, int slot_cap, int chunk, int bf_index, bool h1w_ok) {
+    if (h1w_ok && !wide && G == 1 && h1w_supported(slot_cap)) return h1w_bytes(slot_cap, bf_index);
     return h1_group_bytes(slot_cap, chunk, wide ? 8 : 4, G, bf_index);
 }
 
 // Largest m whose group footprint fits `budget` bytes (slot_cap = 2m + 32).
-int64_t cap_for_budget(int budget, bool wide, int chunk, int G, int bf_index) {
+int64_t cap_for_budget(int budget, bool wide, int chunk, int G, int bf_index, bool h1w_ok) {
     int64_t lo = 0, hi = 1 << 22;
     while (hi - lo > 1) {
         const int64_t mid = (lo + hi) / 2;
         const int64_t sc = round128(2 * mid + kMaxTypes);
         const int64_t bytes = group_bytes(wide, G, static_cast<int>(std::min<int64_t>(sc, 1 << 26)), chunk,
-                                          bf_index);
+                                          bf_index, h1w_ok);
         if (bytes <= budget) lo = mid; else hi = mid;
     }
     return lo;
@@ -343,11 +437,12 @@ int64_t cap_for_budget(int budget, bool wide, int chunk, int G, int bf_index) {
 // cap_m = the largest system whose worst case (2m + 32 slots) the shape could
 // hold; slot_cap = pct% of that plus 64 (never above the worst case).
 int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int chunk, int smem_max,
-               int sms, int64_t hard_cap, int pct, int bf_index, int criterion, bool spills = false) {
+               int sms, int64_t hard_cap, int pct, int bf_index, int criterion, bool spills = false,
+               bool h1w_ok = true) {
     sh.chunk = chunk;
     sh.bf_index = bf_index;
-    int64_t cap = std::min<int64_t>(want_m, cap_for_budget(smem_max / groups, wide, chunk, G, bf_index));
-    if (spills && !wide && G == 1) {
+    int64_t cap = std::min<int64_t>(want_m, cap_for_budget(smem_max / groups, wide, chunk, G, bf_index, h1w_ok));
+    if (spills && h1w_ok && !wide && G == 1) {
         // The one-warp kernel spills a system that outgrows its slots (it is
         // packed again by the worst-case shape, or in global memory), so its
         // reach is set by the pct estimate rather than the worst case.
@@ -356,7 +451,7 @@ int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int ch
             const int64_t mid = (lo + hi) / 2;
             const int64_t sc = round128(mid * pct / 100 + 64);
             const bool fits = h1w_supported(static_cast<int>(std::min<int64_t>(sc, 1 << 30))) &&
-                              group_bytes(false, 1, static_cast<int>(sc), chunk, bf_index) <=
+                              group_bytes(false, 1, static_cast<int>(sc), chunk, bf_index, true) <=
                                                          smem_max / groups;
             if (fits) lo = mid; else hi = mid;
         }
@@ -368,8 +463,8 @@ int make_shape(H1Shape& sh, bool wide, int G, int groups, int64_t want_m, int ch
     sh.groups = groups;
     sh.cap_m = cap;
     sh.slot_cap = std::min(round128(2 * cap + kMaxTypes), round128(cap * pct / 100 + 64));
-    sh.warp_kernel = !wide && G == 1 && h1w_supported(sh.slot_cap);
-    sh.smem = group_bytes(wide, G, sh.slot_cap, chunk, bf_index) * groups;
+    sh.warp_kernel = h1w_ok && !wide && G == 1 && h1w_supported(sh.slot_cap);
+    sh.smem = group_bytes(wide, G, sh.slot_cap, chunk, bf_index, h1w_ok) * groups;
     if (sh.smem > smem_max) return VSBPP_ECAPACITY;
     const int occ = sh.warp_kernel ? h1w_blocks_per_sm(sh.slot_cap, criterion, groups, sh.smem)
                                    : h1_blocks_per_sm(wide, G, groups, sh.smem);
@@ -385,16 +480,7 @@ cudaError_t launch_shape(const H1Shape& sh, bool wide, const H1Params& p, int gr
     return h1_launch(wide, p, sh.G, groups, grid, sh.smem, st);
 }
 
-int check_params(const vsbpp_params* p) {
-    if (!p) return VSBPP_OK;
-    if (p->heuristic != VSBPP_H1 && p->heuristic != VSBPP_H2) return VSBPP_EINVAL;
-    if (p->criterion < VSBPP_FF || p->criterion > VSBPP_RANDOM) return VSBPP_EINVAL;
-    if (p->preopen != 0 && p->preopen != 1) return VSBPP_EINVAL;
-    if (p->reserved != 0) return VSBPP_EINVAL;
-    if (p->sublist_size < 0) return VSBPP_EINVAL;
-    if (p->heuristic == VSBPP_H2 && p->sublist_size > VSBPP_H2_MAX_SUBLIST) return VSBPP_EINVAL;
-    return VSBPP_OK;
-}
+int check_params(const vsbpp_params* p) { return check_params_public(p); }
 
 vsbpp_params defaults(const vsbpp_params* p) {
     vsbpp_params q;
@@ -419,6 +505,8 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
     const int smax = di.max_smem_optin;
     max_m = std::max<int64_t>(max_m, 1);
     lp.prep_grid = di.sms * 8;
+    lp.presort = (prm.flags & VSBPP_PRESORT) != 0;
+    lp.remark3 = (prm.flags & VSBPP_REMARK3) != 0;
     if (prm.heuristic == VSBPP_H2) {
         const int s = static_cast<int>(prm.sublist_size == 0 ? 5 : prm.sublist_size);
         lp.mode = {VSBPP_H2, 1, s};
@@ -434,13 +522,15 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         }
         int f = 1;
         for (int x = 2; x <= s; ++x) f *= x;
-        // literal Rule 2 start: one thread per permutation (shared-memory
-        // bins); otherwise four warps per block, one sublist per warp
-        lp.h2_threads = prm.preopen ? std::max(32, (f + 31) / 32 * 32) : 128;
+        // literal Rule 2 start or Remark 3: one thread per permutation
+        // (shared-memory bins); otherwise four warps per block, one sublist
+        // per warp, bins in registers
+        lp.h2_generic = prm.preopen || lp.remark3;
+        lp.h2_threads = lp.h2_generic ? std::max(32, (f + 31) / 32 * 32) : 128;
         lp.h2_max_bins = 2 * s + (prm.preopen ? kMaxTypes : 0);
         lp.h2_smem = h2_smem_bytes(lp.h2_threads, lp.h2_max_bins);
-        int occ = prm.preopen ? h2_blocks_per_sm(lp.h2_threads, lp.h2_smem)
-                              : h2_blocks_per_sm_reg(lp.h2_threads, s, prm.criterion);
+        int occ = lp.h2_generic ? h2_blocks_per_sm(lp.h2_threads, lp.h2_smem)
+                                : h2_blocks_per_sm_reg(lp.h2_threads, s, prm.criterion);
         if (lp.cfg.h2_blocks_per_sm > 0) occ = std::min(occ, lp.cfg.h2_blocks_per_sm);
         if (occ <= 0) return record(cudaErrorInvalidConfiguration);
         lp.h2_grid = occ * di.sms;
@@ -449,6 +539,18 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         return VSBPP_OK;
     }
     const int64_t s = prm.sublist_size;
+    if (prm.max_open > 0) {
+        // bounded space: one membrane system per instance, one warp each,
+        // the open bins in registers
+        if (s > 0 && s < max_m) return VSBPP_EINVAL;
+        lp.mode = {VSBPP_H1, 0, 0};
+        lp.bounded = true;
+        const int occ = bk_blocks_per_sm();
+        if (occ <= 0) return record(cudaErrorInvalidConfiguration);
+        lp.bk_grid = static_cast<int>(std::max<int64_t>(
+            1, std::min<int64_t>(int64_t(occ) * di.sms, (N + kBKWarpsPerBlock - 1) / kBKWarpsPerBlock)));
+        return VSBPP_OK;
+    }
     if (s > 0 && s < max_m) {
         lp.mode = {VSBPP_H1, 1, s};
         const bool one_warp = s <= lp.cfg.small_m;
@@ -466,15 +568,18 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
     lp.mode = {VSBPP_H1, 0, 0};
     // the BF residual index is laid out when BF items can occur
     const int bfi = prm.criterion == VSBPP_BF || prm.criterion == VSBPP_RANDOM;
+    // Remark 3 runs in the group kernel (the one-warp kernel has no per-type
+    // count of bins below half)
+    const bool h1w_ok = !lp.remark3;
     int rc = make_shape(lp.full, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752, 200, bfi,
-                        prm.criterion);
+                        prm.criterion, false, h1w_ok);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.large, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30,
-                    lp.cfg.slot_pct, bfi, prm.criterion, true);
+                    lp.cfg.slot_pct, bfi, prm.criterion, true, h1w_ok);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.small, false, 1, lp.cfg.small_warps_per_block,
                     std::min<int64_t>(max_m, std::max(1, lp.cfg.small_m)), std::min(chunk, 256), smax,
-                    di.sms, 32752, lp.cfg.slot_pct, bfi, prm.criterion, true);
+                    di.sms, 32752, lp.cfg.slot_pct, bfi, prm.criterion, true, h1w_ok);
     if (rc != VSBPP_OK) return rc;
     rc = make_shape(lp.wide, true, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 1 << 30, 200, bfi,
                     prm.criterion);
@@ -530,7 +635,16 @@ int ensure_scratch(Scratch& sc, const LaunchPlan& lp, int64_t N, int64_t total_m
     int rc = sc.ensure_fixed();
     if (rc) return rc;
     if ((rc = sc.grow(sc.cls, sc.cap_cls, N))) return rc;
+    if (lp.presort) {
+        if ((rc = sc.grow(sc.ps_w, sc.cap_ps_w, total_m))) return rc;
+        if ((rc = sc.grow(sc.ps_perm, sc.cap_ps_perm, total_m))) return rc;
+        if ((rc = sc.grow(sc.ps_tmp, sc.cap_ps_tmp, total_m))) return rc;
+        if ((rc = sc.grow(sc.ps_boi, sc.cap_ps_boi, total_m))) return rc;
+        if ((rc = sc.grow(sc.ps_stat, sc.cap_ps_stat, N))) return rc;
+    }
     if (!lp.mode.compose) {
+        if (lp.bounded && (rc = sc.grow(sc.bk_rec, sc.cap_bk_rec, 2 * total_m + int64_t(kMaxTypes) * N)))
+            return rc;
         if ((rc = sc.grow(sc.order, sc.cap_order, N))) return rc;
         if ((rc = sc.grow(sc.spill_list, sc.cap_spill_list, N))) return rc;
         if ((rc = sc.grow(sc.spill_list2, sc.cap_spill_list2, N))) return rc;
@@ -559,6 +673,7 @@ H1Params h1_params(const BatchView& in, const OutView& out, const vsbpp_params& 
     p.units.num_units = 0;
     p.criterion = prm.criterion;
     p.preopen = prm.preopen;
+    p.remark3 = (prm.flags & VSBPP_REMARK3) ? 1 : 0;
     p.seed = prm.seed;
     p.chunk = sh.chunk;
     p.slot_cap = sh.slot_cap;
@@ -580,8 +695,8 @@ void set_h16(H1Params& p, const LaunchPlan& lp, Scratch& sc) {
 }
 
 // Enqueue the whole pipeline on `st`.  plain = one launch per instance.
-int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutView& out0,
-            const vsbpp_params& prm, bool plain, cudaStream_t st) {
+int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutView& out0,
+                 const vsbpp_params& prm, bool plain, cudaStream_t st) {
     if (in.N == 0) return VSBPP_OK;
     OutView out = out0;
     PrepParams pp;
@@ -604,9 +719,39 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
         pp.wide_cap = lp.wide.cap_m;
         pp.huge_cap = lp.kc.enabled ? lp.kc.cap_m : 0;
         pp.huge_max_B1 = lp.kc.max_B1;
+        pp.one_class = lp.bounded ? 1 : 0;
         VS_TRY(validate_launch(pp, prep_grid, st));
         VS_TRY(order_launch(sc.hist(), sc.cursor(), sc.seg(), sc.queue(), sc.spill_seg(), st));
         VS_TRY(scatter_launch(in, sc.cls, sc.cursor(), sc.order, prep_grid, st));
+        if (lp.bounded) {
+            // bounded space: one warp per membrane system, largest first
+            BKParams bp;
+            std::memset(&bp, 0, sizeof(bp));
+            bp.in = in;
+            bp.out = out;
+            bp.criterion = prm.criterion;
+            bp.preopen = prm.preopen;
+            bp.max_open = static_cast<int32_t>(prm.max_open);
+            bp.seed = prm.seed;
+            bp.rec = sc.bk_rec;
+            bp.counters = g_counters;
+            if (plain) {
+                for (int64_t i = 0; i < in.N; ++i) {       // one single-warp launch per instance
+                    bp.range_begin = i;
+                    bp.range_end = i + 1;
+                    VS_TRY(bk_launch(bp, 1, st));
+                }
+                return VSBPP_OK;
+            }
+            bp.order = sc.order;
+            bp.seg = sc.seg();
+            bp.segment = kClassLarge;
+            bp.queue = sc.queue() + kClassLarge;
+            const bool timed = timing_begin(st);
+            VS_TRY(bk_launch(bp, lp.bk_grid, st));
+            timing_end(timed, st);
+            return VSBPP_OK;
+        }
         const H1Shape* shapes[3] = {&lp.large, &lp.small, &lp.wide};
         for (int c = 0; c < 3; ++c) {
             const H1Shape& sh = *shapes[c];
@@ -660,6 +805,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
             kp.out = out;
             kp.criterion = prm.criterion;
             kp.preopen = prm.preopen;
+            kp.remark3 = lp.remark3 ? 1 : 0;
             kp.seed = prm.seed;
             kp.order = sc.order;
             kp.seg = sc.seg();
@@ -711,6 +857,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
             xp.units.unit_base = sc.unit_base;
             xp.units.sublist = lp.mode.s;
             xp.criterion = prm.criterion;
+            xp.remark3 = lp.remark3 ? 1 : 0;
             xp.sublist = static_cast<int32_t>(lp.mode.s);
             xp.seed = prm.seed;
             xp.seg_units = sc.seg_units();
@@ -731,6 +878,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
             hp.units.sublist = lp.mode.s;
             hp.criterion = prm.criterion;
             hp.preopen = prm.preopen;
+            hp.remark3 = lp.remark3 ? 1 : 0;
             hp.seed = prm.seed;
             hp.sublist = static_cast<int32_t>(lp.mode.s);
             hp.max_bins = lp.h2_max_bins;
@@ -762,6 +910,45 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
     return VSBPP_OK;
 }
 
+// The pipeline, with the offline pre-sort around it when asked for: the
+// instances' weights are sorted into scratch (caller-order validation kept
+// aside), the sorted copy is packed, and each sorted position's bin id goes
+// back to the item's original position.
+int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutView& out,
+            const vsbpp_params& prm, bool plain, cudaStream_t st) {
+    if (!lp.presort) return enqueue_core(lp, sc, in, out, prm, plain, st);
+    if (in.N == 0) return VSBPP_OK;
+    PresortParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.in = in;
+    pp.w_sorted = sc.ps_w;
+    pp.perm = sc.ps_perm;
+    pp.tmp = sc.ps_tmp;
+    pp.status0 = sc.ps_stat;
+    pp.bin_of_item = out.bin_of_item;
+    pp.boi_sorted = sc.ps_boi;
+    pp.status = out.status;
+    pp.num_bins = out.num_bins;
+    pp.total = out.total;
+    const int grid = static_cast<int>(std::min<int64_t>(lp.prep_grid, (in.N + kPresortWarps - 1) / kPresortWarps));
+    VS_TRY(presort_launch(pp, grid, st));
+    BatchView sorted = in;
+    sorted.w_all = sc.ps_w;
+    OutView out2 = out;
+    out2.bin_of_item = sc.ps_boi;
+    const int rc = enqueue_core(lp, sc, sorted, out2, prm, plain, st);
+    if (rc != VSBPP_OK) return rc;
+    VS_TRY(unpermute_launch(pp, static_cast<int>(std::min<int64_t>(lp.prep_grid, (in.N + 7) / 8)), st));
+    return VSBPP_OK;
+}
+
+// Items the per-item scratch must hold when only N and max_m are known on the
+// host (the offsets live on the device): N * max_m bounds w_off[N].
+int64_t scratch_items(const LaunchPlan& lp, int64_t N, int64_t max_m) {
+    const bool per_item = lp.mode.compose || lp.presort || lp.bounded;
+    return per_item ? N * std::max<int64_t>(max_m, 1) : 0;
+}
+
 int check_instance_args(int64_t m, int32_t n, const void* w, const void* B) {
     if (m < 0 || n < 1 || n > VSBPP_MAX_TYPES) return VSBPP_EINVAL;
     if (!B || (m > 0 && !w)) return VSBPP_EINVAL;
@@ -785,7 +972,7 @@ int batch_common(int64_t N, const int32_t* w_all, const int64_t* w_off, const in
         Scratch& sc = scratch_for(st);
         // sublist scratch is sized from the host-side bound N * max_m, so the call
         // never has to read the device offsets back
-        const int64_t total_m = lp.mode.compose ? N * std::max<int64_t>(max_m, 1) : 0;
+        const int64_t total_m = scratch_items(lp, N, max_m);
         if ((rc = ensure_scratch(sc, lp, N, total_m))) return rc;
         BatchView in{N, w_all, w_off, 0, B_all, B_off, 0};
         OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
@@ -821,7 +1008,7 @@ int time_config(const vsbpp_config& cfg, int64_t N, const int32_t* w_all, const 
         return rc;
     }
     Scratch& sc = scratch_for(st);
-    const int64_t total_m = lp.mode.compose ? N * std::max<int64_t>(max_m, 1) : 0;
+    const int64_t total_m = scratch_items(lp, N, max_m);
     if ((rc = ensure_scratch(sc, lp, N, total_m))) {
         g_cfg = saved;
         return rc;
@@ -849,6 +1036,23 @@ int time_config(const vsbpp_config& cfg, int64_t N, const int32_t* w_all, const 
 }
 
 }  // namespace
+
+int vsbpp::check_params_public(const vsbpp_params* p) {
+    if (!p) return VSBPP_OK;
+    if (p->heuristic != VSBPP_H1 && p->heuristic != VSBPP_H2) return VSBPP_EINVAL;
+    if (p->criterion < VSBPP_FF || p->criterion > VSBPP_RANDOM) return VSBPP_EINVAL;
+    if (p->preopen != 0 && p->preopen != 1) return VSBPP_EINVAL;
+    if (p->flags & ~(VSBPP_REMARK3 | VSBPP_PRESORT)) return VSBPP_EINVAL;
+    if (p->sublist_size < 0) return VSBPP_EINVAL;
+    if (p->heuristic == VSBPP_H2 && p->sublist_size > VSBPP_H2_MAX_SUBLIST) return VSBPP_EINVAL;
+    if (p->max_open < 0) return VSBPP_EINVAL;
+    if (p->max_open > 0) {
+        // bounded space: first heuristic, without Remark 3
+        if (p->heuristic != VSBPP_H1 || (p->flags & VSBPP_REMARK3)) return VSBPP_EINVAL;
+        if (p->max_open > VSBPP_MAX_OPEN) return VSBPP_ECAPACITY;
+    }
+    return VSBPP_OK;
+}
 
 unsigned long long* vsbpp::counters_ptr() {
     std::lock_guard<std::recursive_mutex> lk(g_mu);
@@ -911,16 +1115,17 @@ int vsbpp_pack(const int32_t* w, int64_t m, const int32_t* B, int32_t n, const v
         *num_bins = 0;
         *total_capacity = 0;
         std::lock_guard<std::recursive_mutex> lk(g_mu);
-        static cudaStream_t own = nullptr;
-        if (!own) VS_TRY(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+        HostCtx* hc = host_ctx();                 // this device's own stream and staging
+        if (!hc) return VSBPP_ECUDA;
+        cudaStream_t own = hc->st;
         Scratch& sc = scratch_for(own);
         if ((rc = sc.grow(sc.h_w, sc.cap_h_w, m))) return rc;
         if ((rc = sc.grow(sc.h_B, sc.cap_h_B, n))) return rc;
         if ((rc = sc.grow(sc.h_boi, sc.cap_h_boi, m))) return rc;
         if ((rc = sc.grow(sc.h_bt, sc.cap_h_bt, m))) return rc;
         if ((rc = sc.grow(sc.h_small, sc.cap_h_small, 3))) return rc;
-        if (m > 0) VS_TRY(cudaMemcpyAsync(sc.h_w, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, own));
-        VS_TRY(cudaMemcpyAsync(sc.h_B, B, sizeof(int32_t) * n, cudaMemcpyHostToDevice, own));
+        if ((rc = hc->to_device(sc.h_w, w, sizeof(int32_t) * m))) return rc;
+        if ((rc = hc->to_device(sc.h_B, B, sizeof(int32_t) * n))) return rc;
         int32_t* d_status = reinterpret_cast<int32_t*>(sc.h_small + 2);
         rc = vsbpp_pack_device(sc.h_w, m, sc.h_B, n, p, sc.h_boi, sc.h_bt, sc.h_small, sc.h_small + 1,
                                d_status, own);
@@ -931,13 +1136,74 @@ int vsbpp_pack(const int32_t* w, int64_t m, const int32_t* B, int32_t n, const v
         const int32_t st = static_cast<int32_t>(small[2] & 0xFFFFFFFF);
         if (st != VSBPP_OK) return st;
         if (m > 0) {
-            VS_TRY(cudaMemcpyAsync(bin_of_item, sc.h_boi, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, own));
-            if (small[0] > 0)
-                VS_TRY(cudaMemcpyAsync(bin_type, sc.h_bt, sizeof(int32_t) * small[0], cudaMemcpyDeviceToHost, own));
+            if ((rc = hc->to_host(bin_of_item, sc.h_boi, sizeof(int32_t) * m))) return rc;
+            if (small[0] > 0 && (rc = hc->to_host(bin_type, sc.h_bt, sizeof(int32_t) * small[0]))) return rc;
             VS_TRY(cudaStreamSynchronize(own));
         }
         *num_bins = small[0];
         *total_capacity = small[1];
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
+    }
+}
+
+int vsbpp_pack_batch_host(int64_t N, const int32_t* w_all, const int64_t* w_off, const int32_t* B_all,
+                          const int32_t* B_off, int64_t max_m, const vsbpp_params* p,
+                          int32_t* bin_of_item_all, int32_t* bin_type_all, int64_t* num_bins,
+                          int64_t* total, int32_t* status) {
+    try {
+        if (N < 0 || max_m < 0) return VSBPP_EINVAL;
+        if (N == 0) return VSBPP_OK;
+        if (!w_off || !B_all || !B_off || !num_bins || !total || !status) return VSBPP_EINVAL;
+        int rc = check_params(p);
+        if (rc) return rc;
+        // the CSR offsets are on the host here: check them and take max_m
+        if (w_off[0] != 0 || B_off[0] != 0) return VSBPP_EINVAL;
+        int64_t mm = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            const int64_t mi = w_off[i + 1] - w_off[i];
+            if (mi < 0 || B_off[i + 1] < B_off[i]) return VSBPP_EINVAL;
+            mm = std::max(mm, mi);
+        }
+        const int64_t total_m = w_off[N];
+        const int64_t total_B = B_off[N];
+        if (total_m > 0 && (!w_all || !bin_of_item_all || !bin_type_all)) return VSBPP_EINVAL;
+        if (max_m == 0) max_m = mm;
+        if (mm > max_m) return VSBPP_EINVAL;
+        const vsbpp_params prm = defaults(p);
+        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        HostCtx* hc = host_ctx();
+        if (!hc) return VSBPP_ECUDA;
+        cudaStream_t st = hc->st;
+        LaunchPlan lp;
+        if ((rc = build_plan(prm, max_m, N, lp))) return rc;
+        Scratch& sc = scratch_for(st);
+        if ((rc = ensure_scratch(sc, lp, N, std::max<int64_t>(total_m, 1)))) return rc;
+        if ((rc = sc.grow(sc.h_w, sc.cap_h_w, total_m))) return rc;
+        if ((rc = sc.grow(sc.h_B, sc.cap_h_B, total_B))) return rc;
+        if ((rc = sc.grow(sc.h_boi, sc.cap_h_boi, total_m))) return rc;
+        if ((rc = sc.grow(sc.h_bt, sc.cap_h_bt, total_m))) return rc;
+        if ((rc = sc.grow(sc.hb_woff, sc.cap_hb_woff, N + 1))) return rc;
+        if ((rc = sc.grow(sc.hb_Boff, sc.cap_hb_Boff, N + 1))) return rc;
+        if ((rc = sc.grow(sc.hb_nb, sc.cap_hb_nb, N))) return rc;
+        if ((rc = sc.grow(sc.hb_tot, sc.cap_hb_tot, N))) return rc;
+        if ((rc = sc.grow(sc.hb_st, sc.cap_hb_st, N))) return rc;
+        if ((rc = hc->to_device(sc.h_w, w_all, sizeof(int32_t) * total_m)) ||
+            (rc = hc->to_device(sc.hb_woff, w_off, sizeof(int64_t) * (N + 1))) ||
+            (rc = hc->to_device(sc.h_B, B_all, sizeof(int32_t) * total_B)) ||
+            (rc = hc->to_device(sc.hb_Boff, B_off, sizeof(int32_t) * (N + 1))))
+            return rc;
+        BatchView in{N, sc.h_w, sc.hb_woff, 0, sc.h_B, sc.hb_Boff, 0};
+        OutView out{sc.h_boi, sc.h_bt, sc.hb_nb, sc.hb_tot, sc.hb_st, nullptr, nullptr, nullptr};
+        if ((rc = enqueue(lp, sc, in, out, prm, false, st))) return rc;
+        if ((rc = hc->to_host(bin_of_item_all, sc.h_boi, sizeof(int32_t) * total_m)) ||
+            (rc = hc->to_host(bin_type_all, sc.h_bt, sizeof(int32_t) * total_m)) ||
+            (rc = hc->to_host(num_bins, sc.hb_nb, sizeof(int64_t) * N)) ||
+            (rc = hc->to_host(total, sc.hb_tot, sizeof(int64_t) * N)) ||
+            (rc = hc->to_host(status, sc.hb_st, sizeof(int32_t) * N)))
+            return rc;
+        VS_TRY(cudaStreamSynchronize(st));
         return VSBPP_OK;
     } catch (...) {
         return VSBPP_ENOMEM;      // no exception crosses the C interface

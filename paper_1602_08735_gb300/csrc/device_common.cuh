@@ -36,6 +36,26 @@ __device__ __forceinline__ int pick_criterion(int crit, uint64_t seed, uint64_t 
     return crit == kRandom ? static_cast<int>(splitmix64(seed, key) % 3ull) : crit;
 }
 
+// Remark 3 of Section 6.3 read as a condition on Rule 5 (option
+// VSBPP_REMARK3): a bin divides off a new one only if every bin of its type
+// then holds at least half its capacity.  `below` is lane-distributed: lane t
+// (capacity Bl = B[t], 0 past the types) holds the number of type-t bins
+// below half.  A bin opened because nothing fits starts below half (opened);
+// `cross` says the chosen bin's load has just reached half (the Rule 5
+// condition), so it leaves the count; the division then fires only when no
+// bin of its type (capacity Bt) is still below half, and the empty bin it
+// divides off joins the count.  Called by all 32 lanes with uniform
+// arguments (other than Bl and below).
+__device__ __forceinline__ bool remark3_divide(uint32_t& below, uint32_t Bl, bool opened, uint64_t Bt,
+                                               bool cross) {
+    const bool mine = static_cast<uint64_t>(Bl) == Bt;
+    below += (opened && mine) ? 1u : 0u;
+    below -= (cross && mine) ? 1u : 0u;
+    const bool fire = cross && !__any_sync(kFull, mine && below != 0u);
+    below += (fire && mine) ? 1u : 0u;
+    return fire;
+}
+
 // Read-only view of a CSR batch.  A null offset array means a single
 // instance whose size is given directly (used by the single-instance calls).
 struct BatchView {

@@ -119,6 +119,7 @@ struct H1Params {
     int64_t* spill_seg2;
     unsigned long long* counters;  // null, or {items, fit tests} to add to
     int32_t compose;        // 1: write sublist-local results (see OutView)
+    int32_t remark3;        // 1: Rule 5 with Remark 3's per-type condition (VSBPP_REMARK3)
     int32_t bf_index;       // 1: the BF residual index is laid out (used when B_1 <= 1023)
     int32_t chunk;          // items staged per step (multiple of 32)
     int32_t slot_cap;       // bins per group (multiple of 128: whole segments)
@@ -359,7 +360,7 @@ struct H1Group {
     __device__ __forceinline__ bool item_loop(const H1Params& p, int64_t i, const int32_t* w,
                                               int64_t a, int64_t k, int32_t* raw, uint32_t Bl,
                                               bool use_idx, uint32_t& L_io,
-                                              unsigned long long& fit_tests) const {
+                                              unsigned long long& fit_tests, uint32_t& below) const {
         const int chunk = p.chunk;
         uint32_t L = L_io;
         int jc = 0, buf = 0, par = 0;
@@ -430,7 +431,9 @@ struct H1Group {
             if (!hit) r_old = Bt;
             const uint64_t r_new = r_old - wj;
             // Rule 5: 2*load_before < B_t <= 2*load_after, in residual terms
-            const bool fire = (Bt < 2 * r_old) && (2 * r_new <= Bt);
+            // (with Remark 3's per-type condition when asked for)
+            const bool cross = (Bt < 2 * r_old) && (2 * r_new <= Bt);
+            const bool fire = p.remark3 ? remark3_divide(below, Bl, !hit, Bt, cross) : cross;
             if (tid == static_cast<int>(owner(b))) {
                 if (hit) slots[b] = (static_cast<S>(r_new) << kShift) | static_cast<S>(b);
                 else put_new(b, r_new, t);
@@ -471,7 +474,7 @@ struct H1Group {
     __device__ __forceinline__ bool item_loop_warp(const H1Params& p, int64_t i, const int32_t* w,
                                                    int64_t a, int64_t k, int32_t* raw, uint32_t Bl,
                                                    bool B1_indexed, uint32_t& L_io,
-                                                   unsigned long long& fit_tests) const {
+                                                   unsigned long long& fit_tests, uint32_t& below) const {
         constexpr bool kSeg = CRIT != kBF;                        // FF or WF items occur
         constexpr bool kIdx = CRIT == kBF || CRIT == kRandom;     // BF items occur
         const int chunk = p.chunk;
@@ -587,8 +590,9 @@ struct H1Group {
                 r_old = Bt;
             }
             const uint32_t r_new = r_old - wj;
-            const bool fire = (static_cast<uint64_t>(Bt) < 2ull * r_old) &&
-                              (2ull * r_new <= static_cast<uint64_t>(Bt));        // Rule 5
+            const bool cross = (static_cast<uint64_t>(Bt) < 2ull * r_old) &&
+                               (2ull * r_new <= static_cast<uint64_t>(Bt));       // Rule 5
+            const bool fire = p.remark3 ? remark3_divide(below, Bl, !hit, Bt, cross) : cross;
             const uint32_t Lf = hit ? L : L + 1u;         // where a divided-off bin goes
             if (lane == winner) {
                 slots[b] = (static_cast<S>(r_new) << kShift) | static_cast<S>(b);
@@ -723,26 +727,28 @@ struct H1Group {
         }
         if (k > 0) load_chunk(w, 0, k, 0, chunk);
         unsigned long long fit_tests = 0;      // live bins summed over items (counters)
+        // Remark 3: type-t bins below half in lane t (the pre-opened empties)
+        uint32_t below = (p.preopen && lane < n) ? 1u : 0u;
         bool done;
         if constexpr (G == 1) {
             // one warp: the summary-driven loop whenever every criterion it
             // meets has its summaries (BF needs the residual index)
             if (p.criterion != kBF && p.criterion != kRandom) {
-                done = p.criterion == kFF ? item_loop_warp<kFF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests)
-                                          : item_loop_warp<kWF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests);
+                done = p.criterion == kFF ? item_loop_warp<kFF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests, below)
+                                          : item_loop_warp<kWF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests, below);
                 goto packed;
             }
             if (use_idx) {
-                done = p.criterion == kBF ? item_loop_warp<kBF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests)
-                                          : item_loop_warp<kRandom>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests);
+                done = p.criterion == kBF ? item_loop_warp<kBF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests, below)
+                                          : item_loop_warp<kRandom>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests, below);
                 goto packed;
             }
         }
         switch (p.criterion) {                 // the item loop, specialised per criterion
-            case kFF: done = item_loop<kFF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
-            case kBF: done = item_loop<kBF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
-            case kWF: done = item_loop<kWF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
-            default: done = item_loop<kRandom>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests); break;
+            case kFF: done = item_loop<kFF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests, below); break;
+            case kBF: done = item_loop<kBF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests, below); break;
+            case kWF: done = item_loop<kWF>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests, below); break;
+            default: done = item_loop<kRandom>(p, i, w, a, k, raw, Bl, use_idx, L, fit_tests, below); break;
         }
     packed:
         if (!done) return;                     // spilled: a full-size launch repacks it

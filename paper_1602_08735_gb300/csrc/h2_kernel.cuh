@@ -110,7 +110,13 @@ __global__ void h2_pack_kernel(const H2Params p) {
                 const uint64_t Bt = static_cast<uint32_t>(B[t]);
                 const uint64_t r_old = chosen_r, r_new = chosen_r - wj;
                 res[chosen * T + tid] = static_cast<uint32_t>(r_new);
-                if (Bt < 2 * r_old && 2 * r_new <= Bt) {      // Rule 5
+                bool fire = Bt < 2 * r_old && 2 * r_new <= Bt;       // Rule 5
+                if (fire && p.remark3) {
+                    // Remark 3: every bin of type t must now hold at least half
+                    for (int x = 0; x < L; ++x)
+                        fire = fire && !(typ[x * T + tid] == t && Bt < 2ull * res[x * T + tid]);
+                }
+                if (fire) {
                     res[L * T + tid] = static_cast<uint32_t>(Bt);
                     typ[L * T + tid] = static_cast<uint8_t>(t);
                     ++L;

@@ -12,6 +12,7 @@ struct H2Params {
     UnitMap units;
     int32_t criterion;
     int32_t preopen;
+    int32_t remark3;      // 1: Rule 5 with Remark 3's per-type condition (generic kernel only)
     uint64_t seed;
     int32_t sublist;      // s (1..6)
     int32_t perms;        // s!
@@ -26,6 +27,7 @@ struct H2XParams {
     OutView out;                    // compose-mode fields are used
     UnitMap units;
     int32_t criterion;
+    int32_t remark3;                // 1: Rule 5 with Remark 3's per-type condition
     int32_t sublist;                // s (7..12)
     uint64_t seed;
     const int64_t* seg_units;       // [1] = number of sublists (device)

@@ -65,7 +65,8 @@ __device__ __forceinline__ void h2x_decode(uint32_t rank, int k, int (&perm)[S])
 template <int S, int CRIT>
 __device__ __forceinline__ uint64_t h2x_pack(const int (&perm)[S], int k, const uint32_t* ws, const uint32_t* bs,
                                              uint64_t seed, int64_t g, uint32_t rank, uint32_t (&r)[2 * S],
-                                             uint32_t (&cp)[2 * S], uint32_t (&slot)[S], uint32_t& fit) {
+                                             uint32_t (&cp)[2 * S], uint32_t (&slot)[S], uint32_t& fit,
+                                             bool remark3) {
     constexpr int kSlots = 2 * S;
     constexpr uint64_t kNo = ~0ull;
 #pragma unroll
@@ -100,8 +101,16 @@ __device__ __forceinline__ uint64_t h2x_pack(const int (&perm)[S], int k, const 
                 cap = xs == static_cast<uint32_t>(x) ? cp[x] : cap;
             }
             const uint32_t r_new = r_old - wq;
-            const bool fire = (static_cast<uint64_t>(cap) < 2ull * r_old) &&
-                              (2ull * r_new <= static_cast<uint64_t>(cap));     // Rule 5
+            bool fire = (static_cast<uint64_t>(cap) < 2ull * r_old) &&
+                        (2ull * r_new <= static_cast<uint64_t>(cap));           // Rule 5
+            if (remark3 && fire) {
+                // Remark 3: no other bin of this type (capacities are distinct)
+                // may be below half; the chosen one holds half now
+#pragma unroll
+                for (int x = 0; x < 2 * q; ++x)
+                    fire = fire && !(static_cast<uint32_t>(x) != xs && cp[x] == cap &&
+                                     static_cast<uint64_t>(cap) < 2ull * r[x]);
+            }
             tot += r_old == cap ? cap : 0u;            // the bin's first item: it becomes used
             fit += alive;
             alive += (hit ? 0u : 1u) + (fire ? 1u : 0u);
@@ -190,7 +199,7 @@ __global__ void __launch_bounds__(128) h2x_search_kernel(const H2XParams p) {
             h2x_decode<S>(static_cast<uint32_t>(rr), k, perm);
             uint32_t r[2 * S], cp[2 * S], slot[S], fit;
             const uint64_t tot = h2x_pack<S, CRIT>(perm, k, ws, bs, p.seed, g, static_cast<uint32_t>(rr), r, cp,
-                                                   slot, fit);
+                                                   slot, fit, p.remark3 != 0);
             const unsigned long long key = (tot << 29) | static_cast<unsigned long long>(rr);
             best = key < best ? key : best;
             fits += fit;
@@ -234,7 +243,8 @@ __global__ void __launch_bounds__(128) h2x_write_kernel(const H2XParams p) {
             int perm[S];
             h2x_decode<S>(rank, k, perm);
             uint32_t r[2 * S], cp[2 * S], slot[S], fit;
-            const uint64_t tot = h2x_pack<S, CRIT>(perm, k, ws, bs, p.seed, g, rank, r, cp, slot, fit);
+            const uint64_t tot = h2x_pack<S, CRIT>(perm, k, ws, bs, p.seed, g, rank, r, cp, slot, fit,
+                                                   p.remark3 != 0);
             const int64_t base = p.in.w_begin(i) + a;
             uint32_t used = 0;
             int cnt = 0;

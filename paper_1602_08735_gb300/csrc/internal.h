@@ -11,8 +11,13 @@
 #include "h2_params.cuh"
 #include "prep_params.cuh"
 #include "kc_params.cuh"
+#include "variants_params.cuh"
 
 namespace vsbpp {
+
+// Checks of vsbpp_params shared by every entry point (null = defaults):
+// VSBPP_OK, VSBPP_EINVAL or VSBPP_ECAPACITY (a bound above VSBPP_MAX_OPEN).
+int check_params_public(const vsbpp_params* p);
 
 // The device work counters {items, fit tests} while vsbpp_counters_enable is
 // on, else null.
@@ -52,6 +57,13 @@ cudaError_t h2x_launch(const H2XParams& p, int grid, cudaStream_t st);
 int h2x_blocks_per_sm(int sublist, int criterion);
 int h2_blocks_per_sm(int threads, int smem);
 int h2_blocks_per_sm_reg(int threads, int sublist, int criterion);   // register kernel (no preopen)
+
+// Offline pre-sort (VSBPP_PRESORT) and its inverse; bounded-space kernel.
+cudaError_t presort_launch(const PresortParams& p, int grid, cudaStream_t st);
+cudaError_t unpermute_launch(const PresortParams& p, int grid, cudaStream_t st);
+cudaError_t bk_launch(const BKParams& p, int grid, cudaStream_t st);
+int bk_blocks_per_sm();
+constexpr int kBKWarpsPerBlock = kBKWarps;
 
 cudaError_t validate_launch(const PrepParams& p, int grid, cudaStream_t st);
 cudaError_t order_launch(uint32_t* hist, int64_t* cursor, int64_t* seg, unsigned long long* queue,

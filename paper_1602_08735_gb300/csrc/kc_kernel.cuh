@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(32) kc_pack_kernel(const KCParams p) {
         if (p.preopen) {
             for (int t = 0; t < n; ++t) W.append(L++, static_cast<uint32_t>(B[t]), static_cast<uint32_t>(t));
         }
+        uint32_t below = (p.preopen && lane < n) ? 1u : 0u;   // Remark 3: type-t bins below half
         unsigned long long fit_tests = 0;
         // weights a 32-item block ahead (lane l holds item block + l); each
         // item's weight is a shuffle off the dependent chain, and the items'
@@ -305,7 +306,8 @@ __global__ void __launch_bounds__(32) kc_pack_kernel(const KCParams p) {
             }
             const uint32_t Bt = __shfl_sync(kFull, Bl, static_cast<int>(t));
             const uint32_t r_new = r_old - wj;
-            if (Bt < 2 * r_old && 2 * r_new <= Bt) {            // Rule 5
+            const bool cross = Bt < 2 * r_old && 2 * r_new <= Bt;          // Rule 5
+            if (p.remark3 ? remark3_divide(below, Bl, !hit, Bt, cross) : cross) {
                 W.append(L, Bt, t);
                 ++L;
             }

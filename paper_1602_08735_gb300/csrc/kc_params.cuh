@@ -16,6 +16,7 @@ struct KCParams {
     OutView out;
     int32_t criterion;
     int32_t preopen;
+    int32_t remark3;         // 1: Rule 5 with Remark 3's per-type condition
     uint64_t seed;
     const int32_t* order;
     const int64_t* seg;

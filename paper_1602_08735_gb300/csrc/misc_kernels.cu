@@ -47,7 +47,7 @@ int h1_blocks_per_sm(bool wide, int G, int groups, int smem) {
 static const void* h2_reg_kernel(int sublist, int criterion);
 
 cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaStream_t st) {
-    if (!p.preopen) {
+    if (!p.preopen && !p.remark3) {
         // bins in registers; sublist size and criterion fixed at compile time
         const void* k = h2_reg_kernel(p.sublist, p.criterion);
         if (k) {

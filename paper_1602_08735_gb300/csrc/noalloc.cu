@@ -63,7 +63,7 @@ extern "C" int vsbpp_pack_batch_noalloc(int64_t N, const int32_t* w_all, const i
     prm.criterion = VSBPP_BF;
     if (p) prm = *p;
     if (prm.heuristic != VSBPP_H1 || prm.criterion < VSBPP_FF || prm.criterion > VSBPP_RANDOM ||
-        (prm.preopen & ~1) || prm.reserved != 0 || prm.sublist_size < 0)
+        (prm.preopen & ~1) || prm.flags != 0 || prm.max_open != 0 || prm.sublist_size < 0)
         return VSBPP_EINVAL;
     // one membrane system per instance only (sublists need per-sublist scratch)
     if (prm.sublist_size != 0 && prm.sublist_size < max_m) return VSBPP_ECAPACITY;

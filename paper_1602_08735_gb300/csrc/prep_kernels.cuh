@@ -66,7 +66,9 @@ __global__ void validate_kernel(const PrepParams p) {
             if (first != ~0ull) code = (first & 3ull) == 1ull ? VSBPP_EINVAL : VSBPP_ETOOBIG;
         }
         int c = kClassNone;
-        if (code == VSBPP_OK && m > 0 && p.classify) {
+        if (code == VSBPP_OK && m > 0 && p.classify && p.one_class) {
+            c = kClassLarge;
+        } else if (code == VSBPP_OK && m > 0 && p.classify) {
             const int64_t bins = 2 * m + (p.preopen ? n : 0);
             if (B1 <= p.narrow_max_B && m <= p.small_m && m <= p.small_cap && bins <= p.narrow_bins) {
                 c = kClassSmall;

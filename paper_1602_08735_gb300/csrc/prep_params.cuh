@@ -18,6 +18,8 @@ struct PrepParams {
     BatchView in;
     OutView out;
     int32_t classify;        // 1: first heuristic with one unit per instance
+    int32_t one_class;       // 1 (with classify): every packable instance in the large class
+                             // (the bounded-space kernel holds any size)
     int64_t small_m;         // m <= small_m -> small class
     int64_t narrow_cap;      // largest m the narrow kernels hold
     int64_t small_cap;       // largest m the single-warp kernel holds

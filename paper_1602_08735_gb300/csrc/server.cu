@@ -100,7 +100,7 @@ struct vsbpp_server {
     bool stop = false;
     std::thread worker;
     PinnedPool pinned;
-    std::vector<double> lat_us;
+    std::vector<double> lat_us, wait_us, svc_us;    // submit->done, submit->admit, admit->done
     int64_t completed = 0, items = 0;
     Clock::time_point t_first{}, t_last{};
     bool any = false;
@@ -122,7 +122,7 @@ struct Req {
     int status = VSBPP_OK;
     int lane = 0;
     bool done = false;
-    Clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_admit, t_done;
 
     int64_t* h_small() const {
         return reinterpret_cast<int64_t*>(reinterpret_cast<char*>(h_out) +
@@ -143,9 +143,13 @@ void finish(Req* r, int status) {
     s->completed += 1;
     s->items += r->m;
     s->t_last = now;
-    const double us = std::chrono::duration<double, std::micro>(now - r->t_submit).count();
-    if (s->lat_us.size() >= 200000) s->lat_us.erase(s->lat_us.begin(), s->lat_us.begin() + 100000);
-    s->lat_us.push_back(us);
+    auto keep = [](std::vector<double>& v, double x) {
+        if (v.size() >= 200000) v.erase(v.begin(), v.begin() + 100000);
+        v.push_back(x);
+    };
+    keep(s->lat_us, std::chrono::duration<double, std::micro>(now - r->t_submit).count());
+    keep(s->wait_us, std::chrono::duration<double, std::micro>(r->t_admit - r->t_submit).count());
+    keep(s->svc_us, std::chrono::duration<double, std::micro>(now - r->t_admit).count());
     s->cv.notify_all();
 }
 
@@ -209,6 +213,7 @@ void worker_main(vsbpp_server* s) {
             if (s->stop) return;
             r = s->waiting.front();
             s->waiting.pop_front();
+            r->t_admit = Clock::now();
             s->in_flight += 1;
             s->in_use += r->need;
             // the lane with the fewest items in flight
@@ -289,10 +294,8 @@ int vsbpp_server_submit(vsbpp_server* s, const int32_t* w, int64_t m, const int3
     try {
         if (!s || !ticket || !B || m < 0 || (m > 0 && !w) || n < 1 || n > VSBPP_MAX_TYPES)
             return VSBPP_EINVAL;
-        if (p && (p->reserved != 0 || p->heuristic < VSBPP_H1 || p->heuristic > VSBPP_H2 ||
-                  p->criterion < VSBPP_FF || p->criterion > VSBPP_RANDOM || (p->preopen & ~1) ||
-                  p->sublist_size < 0 || (p->heuristic == VSBPP_H2 && p->sublist_size > VSBPP_H2_MAX_SUBLIST)))
-            return VSBPP_EINVAL;
+        const int prc = vsbpp::check_params_public(p);
+        if (prc != VSBPP_OK) return prc;
         const size_t need = request_bytes(m, n);
         if (need > s->budget) return VSBPP_ECAPACITY;
         {
@@ -381,25 +384,32 @@ int vsbpp_server_poll(vsbpp_server* s, uint64_t ticket, int32_t* bin_of_item, in
 int vsbpp_server_stats(vsbpp_server* s, vsbpp_server_stats_t* out) {
     try {
         if (!s || !out) return VSBPP_EINVAL;
-        std::vector<double> v;
+        std::vector<double> v, wv, sv;
         {
             std::lock_guard<std::mutex> lk(s->mu);
             v = s->lat_us;
+            wv = s->wait_us;
+            sv = s->svc_us;
             out->completed = s->completed;
             out->items_packed = s->items;
             out->busy_s = s->any ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;
         }
-        out->p50_us = out->p99_us = out->max_us = 0.0;
-        if (!v.empty()) {
-            std::sort(v.begin(), v.end());
-            auto q = [&](double f) {
-                const size_t k = static_cast<size_t>(f * static_cast<double>(v.size() - 1) + 0.5);
-                return v[std::min(k, v.size() - 1)];
-            };
-            out->p50_us = q(0.50);
-            out->p99_us = q(0.99);
-            out->max_us = v.back();
-        }
+        // nearest-rank percentile of a sorted copy (0 when empty)
+        auto q = [](std::vector<double>& x, double f) {
+            if (x.empty()) return 0.0;
+            const size_t k = static_cast<size_t>(f * static_cast<double>(x.size() - 1) + 0.5);
+            return x[std::min(k, x.size() - 1)];
+        };
+        std::sort(v.begin(), v.end());
+        std::sort(wv.begin(), wv.end());
+        std::sort(sv.begin(), sv.end());
+        out->p50_us = q(v, 0.50);
+        out->p99_us = q(v, 0.99);
+        out->max_us = v.empty() ? 0.0 : v.back();
+        out->wait_p50_us = q(wv, 0.50);
+        out->wait_p99_us = q(wv, 0.99);
+        out->service_p50_us = q(sv, 0.50);
+        out->service_p99_us = q(sv, 0.99);
         return VSBPP_OK;
     } catch (...) {
         return VSBPP_ENOMEM;      // no exception crosses the C interface

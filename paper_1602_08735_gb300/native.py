@@ -20,12 +20,14 @@ FF, BF, WF, RANDOM = 0, 1, 2, 3
 H1, H2 = 1, 2
 OK, EINVAL, ETOOBIG, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, ENOTFOUND, ECAPACITY = 0, -1, -2, -3, -4, -5, -6, -7, -8
 MAX_TYPES = 32
+MAX_OPEN = 32                 # largest bound of the bounded-space variant
+REMARK3, PRESORT = 1, 2       # option flags (vsbpp_params.flags)
 
 # Every entry point declared in include/vsbpp.h.
 EXPORTS = (
     "vsbpp_strerror", "vsbpp_version", "vsbpp_last_cuda_error",
     "vsbpp_pack", "vsbpp_pack_device", "vsbpp_pack_batch", "vsbpp_pack_plain",
-    "vsbpp_pack_batch_noalloc",
+    "vsbpp_pack_batch_host", "vsbpp_pack_batch_noalloc",
     "vsbpp_counters_enable", "vsbpp_counters_read",
     "vsbpp_kernel_timing_enable", "vsbpp_kernel_timing_read",
     "vsbpp_plan_create", "vsbpp_plan_run", "vsbpp_plan_destroy",
@@ -44,7 +46,7 @@ class VsbppError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("heuristic", ctypes.c_int32), ("criterion", ctypes.c_int32),
                 ("sublist_size", ctypes.c_int64), ("preopen", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("flags", ctypes.c_int32), ("seed", ctypes.c_uint64), ("max_open", ctypes.c_int64)]
 
 
 class Config(ctypes.Structure):
@@ -63,7 +65,9 @@ class Counters(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("items_packed", ctypes.c_int64),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
-                ("max_us", ctypes.c_double), ("busy_s", ctypes.c_double)]
+                ("max_us", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("wait_p50_us", ctypes.c_double), ("wait_p99_us", ctypes.c_double),
+                ("service_p50_us", ctypes.c_double), ("service_p99_us", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -95,6 +99,8 @@ def load(path: str = LIB_PATH):
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = [i64, vp, vp, vp, vp, i64, pp, vp, vp, vp, vp, vp, vp]
+        lib.vsbpp_pack_batch_host.restype = ctypes.c_int
+        lib.vsbpp_pack_batch_host.argtypes = [i64, vp, vp, vp, vp, i64, pp, vp, vp, vp, vp, vp]
         if hasattr(lib, "vsbpp_plan_create"):
             lib.vsbpp_plan_create.restype = ctypes.c_int
             lib.vsbpp_plan_create.argtypes = [i64, i64, i64, pp, ctypes.POINTER(vp)]
@@ -146,8 +152,8 @@ def strerror(code: int) -> str:
 
 
 def make_params(heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
-                preopen: int = 0, seed: int = 0) -> Params:
-    return Params(heuristic, criterion, sublist_size, preopen, 0, seed & (2**64 - 1))
+                preopen: int = 0, seed: int = 0, flags: int = 0, max_open: int = 0) -> Params:
+    return Params(heuristic, criterion, sublist_size, preopen, flags, seed & (2**64 - 1), max_open)
 
 
 def _ptr(x) -> int | None:
@@ -178,7 +184,7 @@ class Packing:
 
 
 def pack(w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0, preopen: int = 0,
-         seed: int = 0) -> Packing:
+         seed: int = 0, flags: int = 0, max_open: int = 0) -> Packing:
     """Host-memory call (vsbpp_pack): numpy in, numpy out, synchronous."""
     lib = load()
     w = np.ascontiguousarray(w, dtype=np.int32)
@@ -188,7 +194,7 @@ def pack(w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0, 
     bt = np.full(max(m, 1), -1, dtype=np.int32)
     nb = ctypes.c_int64(0)
     tot = ctypes.c_int64(0)
-    p = make_params(heuristic, criterion, sublist_size, preopen, seed)
+    p = make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open)
     wb = w if m > 0 else np.zeros(1, dtype=np.int32)
     Bb = B if B.shape[0] > 0 else np.zeros(1, dtype=np.int32)
     rc = lib.vsbpp_pack(_ptr(wb), m, _ptr(Bb), int(B.shape[0]), ctypes.byref(p), _ptr(boi), _ptr(bt),
@@ -199,10 +205,10 @@ def pack(w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0, 
 
 def pack_device(w, B, bin_of_item, bin_type, num_bins, total, status, heuristic: int = H1,
                 criterion: int = BF, sublist_size: int = 0, preopen: int = 0, seed: int = 0,
-                stream=None) -> int:
+                stream=None, flags: int = 0, max_open: int = 0) -> int:
     """Device-memory call (vsbpp_pack_device) on torch CUDA tensors; async."""
     lib = load()
-    p = make_params(heuristic, criterion, sublist_size, preopen, seed)
+    p = make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open)
     return int(lib.vsbpp_pack_device(_ptr(w), int(w.numel()), _ptr(B), int(B.numel()), ctypes.byref(p),
                                      _ptr(bin_of_item), _ptr(bin_type), _ptr(num_bins), _ptr(total),
                                      _ptr(status), _stream_handle(stream)))
@@ -264,26 +270,61 @@ def _batch_call(fn_name, db: DeviceBatch, out: DeviceResult, params: Params, str
 
 
 def pack_batch(db: DeviceBatch, out: DeviceResult, heuristic: int = H1, criterion: int = BF,
-               sublist_size: int = 0, preopen: int = 0, seed: int = 0, stream=None, max_m=None) -> int:
+               sublist_size: int = 0, preopen: int = 0, seed: int = 0, stream=None, max_m=None,
+               flags: int = 0, max_open: int = 0) -> int:
     """Batched persistent launch (vsbpp_pack_batch); async on ``stream``."""
     return _batch_call("vsbpp_pack_batch", db, out,
-                       make_params(heuristic, criterion, sublist_size, preopen, seed), stream, max_m)
+                       make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open),
+                       stream, max_m)
 
 
 def pack_plain(db: DeviceBatch, out: DeviceResult, heuristic: int = H1, criterion: int = BF,
-               sublist_size: int = 0, preopen: int = 0, seed: int = 0, stream=None, max_m=None) -> int:
+               sublist_size: int = 0, preopen: int = 0, seed: int = 0, stream=None, max_m=None,
+               flags: int = 0, max_open: int = 0) -> int:
     """One launch per instance (vsbpp_pack_plain); async on ``stream``."""
     return _batch_call("vsbpp_pack_plain", db, out,
-                       make_params(heuristic, criterion, sublist_size, preopen, seed), stream, max_m)
+                       make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open),
+                       stream, max_m)
 
 
 def pack_batch_noalloc(db: DeviceBatch, out: DeviceResult, heuristic: int = H1, criterion: int = BF,
                        sublist_size: int = 0, preopen: int = 0, seed: int = 0, stream=None,
-                       max_m=None) -> int:
+                       max_m=None, flags: int = 0, max_open: int = 0) -> int:
     """vsbpp_pack_batch_noalloc: the batched pack with the library's static
     device scratch (for callers that cannot allocate); async on ``stream``."""
     return _batch_call("vsbpp_pack_batch_noalloc", db, out,
-                       make_params(heuristic, criterion, sublist_size, preopen, seed), stream, max_m)
+                       make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open),
+                       stream, max_m)
+
+
+@dataclass
+class HostResult:
+    """Outputs of a host-memory batch call (numpy, or pinned torch tensors)."""
+    status: object
+    bin_of_item: object
+    bin_type: object
+    num_bins: object
+    total: object
+
+    @classmethod
+    def empty(cls, N: int, total_items: int):
+        return cls(np.zeros(max(N, 1), dtype=np.int32), np.full(max(total_items, 1), -1, dtype=np.int32),
+                   np.full(max(total_items, 1), -1, dtype=np.int32), np.zeros(max(N, 1), dtype=np.int64),
+                   np.zeros(max(N, 1), dtype=np.int64))
+
+
+def pack_batch_host(w_all, w_off, B_all, B_off, out: HostResult, heuristic: int = H1,
+                    criterion: int = BF, sublist_size: int = 0, preopen: int = 0, seed: int = 0,
+                    max_m: int = 0, flags: int = 0, max_open: int = 0) -> int:
+    """vsbpp_pack_batch_host: a CSR batch in host memory (numpy arrays or
+    pinned torch CPU tensors) packed in one synchronous call; the library
+    copies in and out.  Returns the host-side status."""
+    lib = load()
+    N = int((w_off.shape[0] if hasattr(w_off, "shape") else len(w_off))) - 1
+    p = make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open)
+    return int(lib.vsbpp_pack_batch_host(N, _ptr(w_all), _ptr(w_off), _ptr(B_all), _ptr(B_off), int(max_m),
+                                         ctypes.byref(p), _ptr(out.bin_of_item), _ptr(out.bin_type),
+                                         _ptr(out.num_bins), _ptr(out.total), _ptr(out.status)))
 
 
 def get_config() -> dict:
@@ -337,9 +378,9 @@ class Plan:
     """A batch shape recorded into a CUDA graph (vsbpp_plan_*)."""
 
     def __init__(self, N: int, total_m: int, max_m: int, heuristic: int = H1, criterion: int = BF,
-                 sublist_size: int = 0, preopen: int = 0, seed: int = 0):
+                 sublist_size: int = 0, preopen: int = 0, seed: int = 0, flags: int = 0, max_open: int = 0):
         self._lib = load()
-        self._p = make_params(heuristic, criterion, sublist_size, preopen, seed)
+        self._p = make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open)
         h = ctypes.c_void_p()
         rc = self._lib.vsbpp_plan_create(N, total_m, max_m, ctypes.byref(self._p), ctypes.byref(h))
         if rc != 0:
@@ -367,11 +408,12 @@ class Plan:
 
 
 def autotune(db: "DeviceBatch", out: "DeviceResult", heuristic: int = H1, criterion: int = BF,
-             sublist_size: int = 0, preopen: int = 0, seed: int = 0, stream=None):
+             sublist_size: int = 0, preopen: int = 0, seed: int = 0, stream=None, flags: int = 0,
+             max_open: int = 0):
     """Time candidate launch configurations on this batch and install the
     fastest; returns (config dict, best milliseconds)."""
     lib = load()
-    p = make_params(heuristic, criterion, sublist_size, preopen, seed)
+    p = make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open)
     best = Config()
     ms = ctypes.c_double(0)
     rc = lib.vsbpp_autotune(db.N, _ptr(db.w_all), _ptr(db.w_off), _ptr(db.B_all), _ptr(db.B_off),
@@ -409,11 +451,11 @@ class Server:
         self._h = h
 
     def submit(self, w, B, heuristic: int = H1, criterion: int = BF, sublist_size: int = 0,
-               preopen: int = 0, seed: int = 0) -> int:
+               preopen: int = 0, seed: int = 0, flags: int = 0, max_open: int = 0) -> int:
         """Returns a ticket (>0), or raises VsbppError (e.g. EBUSY)."""
         w = np.ascontiguousarray(w, dtype=np.int32)
         B = np.ascontiguousarray(B, dtype=np.int32)
-        p = make_params(heuristic, criterion, sublist_size, preopen, seed)
+        p = make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open)
         t = ctypes.c_uint64(0)
         wb = w if w.shape[0] > 0 else np.zeros(1, dtype=np.int32)
         rc = self._lib.vsbpp_server_submit(self._h, _ptr(wb), int(w.shape[0]), _ptr(B), int(B.shape[0]),

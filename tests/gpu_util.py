@@ -7,21 +7,22 @@ from paper_1602_08735_gb300 import native
 
 
 def run_batch(batch, heuristic=1, criterion=1, sublist_size=0, preopen=0, seed=0, plain=False,
-              max_m=None):
+              max_m=None, flags=0, max_open=0):
     import torch
     db = native.DeviceBatch.from_host(batch)
     out = native.DeviceResult.empty(db.N, db.total_items)
     fn = native.pack_plain if plain else native.pack_batch
-    rc = fn(db, out, heuristic, criterion, sublist_size, preopen, seed, max_m=max_m)
+    rc = fn(db, out, heuristic, criterion, sublist_size, preopen, seed, max_m=max_m, flags=flags,
+            max_open=max_open)
     assert rc == 0, native.strerror(rc)
     torch.cuda.synchronize()
     st, boi, bt, nb, tot = out.to_host(db.N, db.total_items)
     return oracle.BatchResult(st, boi, bt, nb, tot)
 
 
-def run_oracle(batch, heuristic=1, criterion=1, sublist_size=0, preopen=0, seed=0):
+def run_oracle(batch, heuristic=1, criterion=1, sublist_size=0, preopen=0, seed=0, flags=0, max_open=0):
     return oracle.pack_many(batch.w_all, batch.w_off, batch.B_all, batch.B_off, heuristic, criterion,
-                            sublist_size, preopen, seed)
+                            sublist_size, preopen, seed, flags, max_open=max_open)
 
 
 def assert_same(batch, got, ref, what=""):

@@ -29,11 +29,11 @@ def _lib():
 
 
 def test_hand_examples_host_api():
+    """Every hand-worked packing, the Remark 3, pre-sort and bounded-space
+    ones included, through the host-memory call."""
     for ex in P.load_golden("hand_examples.json")["examples"]:
-        if ex.get("flags", 0):
-            continue                  # oracle-only reading (Remark 3 condition), not in the library
         r = native.pack(ex["w"], ex["B"], ex["heuristic"], ex["criterion"], ex["sublist_size"],
-                        ex["preopen"], ex["seed"])
+                        ex["preopen"], ex["seed"], ex.get("flags", 0), ex.get("max_open", 0))
         assert r.status == 0, ex["name"]
         assert r.bin_of_item.tolist() == ex["bin_of_item"], ex["name"]
         assert r.bin_type.tolist() == ex["bin_type"], ex["name"]

@@ -28,7 +28,8 @@ def saved_config(lib):
 
 
 def _p(**kw):
-    base = dict(heuristic=native.H1, criterion=native.BF, sublist_size=0, preopen=0, reserved=0, seed=0)
+    base = dict(heuristic=native.H1, criterion=native.BF, sublist_size=0, preopen=0, flags=0, seed=0,
+                max_open=0)
     base.update(kw)
     return native.Params(**base)
 
@@ -48,8 +49,10 @@ def _pack(lib, w, B, params, m=None, n=None):
 
 
 BAD_PARAMS = [dict(heuristic=0), dict(heuristic=3), dict(criterion=-1), dict(criterion=4),
-              dict(preopen=2), dict(preopen=-1), dict(reserved=1), dict(sublist_size=-1),
-              dict(heuristic=native.H2, sublist_size=13)]
+              dict(preopen=2), dict(preopen=-1), dict(flags=4), dict(flags=-1), dict(sublist_size=-1),
+              dict(heuristic=native.H2, sublist_size=13), dict(max_open=-1),
+              dict(heuristic=native.H2, sublist_size=5, max_open=3),
+              dict(flags=native.REMARK3, max_open=2)]
 
 
 @pytest.mark.parametrize("bad", BAD_PARAMS)
@@ -67,6 +70,47 @@ def test_bad_parameters_rejected(lib, bad):
     plan = ctypes.c_void_p()
     assert lib.vsbpp_plan_create(1, 2, 2, ctypes.byref(_p(**bad)), ctypes.byref(plan)) == EINVAL
     assert not plan.value
+
+
+def test_bound_above_the_limit(lib):
+    """A bounded-space bound above VSBPP_MAX_OPEN: ECAPACITY from every entry
+    point, before any device work."""
+    p = _p(max_open=native.MAX_OPEN + 1)
+    assert _pack(lib, [3, 4], [5], p) == ECAPACITY
+    one = np.zeros(2, dtype=np.int64)
+    buf = np.zeros(4, dtype=np.int64)
+    assert lib.vsbpp_pack_batch(1, buf.ctypes.data, one.ctypes.data, buf.ctypes.data, buf.ctypes.data, 2,
+                                ctypes.byref(p), buf.ctypes.data, buf.ctypes.data, buf.ctypes.data,
+                                buf.ctypes.data, buf.ctypes.data, None) == ECAPACITY
+
+
+@pytest.mark.parametrize("case", ["n_neg", "off0", "w_off_down", "B_off_down", "max_m_small", "params"])
+def test_host_batch_arguments(lib, case):
+    """vsbpp_pack_batch_host checks its host CSR offsets and parameters
+    before any device work: EINVAL."""
+    w = np.array([1, 2, 3], dtype=np.int32)
+    w_off = np.array([0, 2, 3], dtype=np.int64)
+    B = np.array([5, 4], dtype=np.int32)
+    B_off = np.array([0, 1, 2], dtype=np.int32)
+    N, max_m, p = 2, 0, _p()
+    if case == "n_neg":
+        N = -1
+    elif case == "off0":
+        w_off = np.array([1, 2, 3], dtype=np.int64)
+    elif case == "w_off_down":
+        w_off = np.array([0, 3, 2], dtype=np.int64)
+    elif case == "B_off_down":
+        B_off = np.array([0, 2, 1], dtype=np.int32)
+    elif case == "max_m_small":
+        max_m = 1
+    else:
+        p = _p(criterion=7)
+    out = native.HostResult.empty(2, 3)
+    rc = lib.vsbpp_pack_batch_host(N, w.ctypes.data, w_off.ctypes.data, B.ctypes.data, B_off.ctypes.data,
+                                   max_m, ctypes.byref(p), out.bin_of_item.ctypes.data,
+                                   out.bin_type.ctypes.data, out.num_bins.ctypes.data, out.total.ctypes.data,
+                                   out.status.ctypes.data)
+    assert rc == EINVAL
 
 
 @pytest.mark.parametrize("case", ["n0", "n33", "m_neg", "w_null", "B_null"])

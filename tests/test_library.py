@@ -31,5 +31,5 @@ def test_library_builds_and_exports_everything():
 def test_library_loads_without_gpu():
     from paper_1602_08735_gb300 import native
     lib = native.load()
-    assert lib.vsbpp_version() == 10000
+    assert lib.vsbpp_version() == 10100
     assert native.strerror(-2).startswith("an item is heavier")
