@@ -499,6 +499,15 @@ def run_reference(args, ws, rank):
 
 
 # -------------------------------------------------------------------- ours
+def rank_batch(native, I, instances, ws, rank):
+    """This rank's part of the global batch (config-3 recipe, seed 3,
+    instances * ws instances) under the library's longest-first split."""
+    from paper_1602_08735_gb300 import shard
+    whole = I.config3(seed=3, N=instances * ws)
+    part, _ = shard.split(whole, ws, rank)
+    return part
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -512,7 +521,9 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    batch = I.config3(seed=3 + rank, N=args.instances)
+    # one batch of instances x world instances, split over the ranks by the
+    # library's LPT split (vsbpp_shard); at one GPU it is config 3 itself
+    batch = rank_batch(native, I, args.instances, ws, rank)
     db = native.DeviceBatch.from_host(batch, device=dev)
     outs = [native.DeviceResult.empty(db.N, db.total_items, device=dev) for _ in PASSES]
     tuned = None
@@ -699,7 +710,8 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": WORKLOAD, "instances": db.N, "items_per_step": int(items_per_step),
                        "passes": [p[0] for p in PASSES], "l2": "flushed before each timed step",
                        "graph": "each pass is a CUDA-graph replay of the batched persistent launch",
-                       "parallelism": f"instances sharded, {ws} GPU(s), no collective",
+                       "parallelism": f"one batch of {args.instances * ws} instances split over {ws} GPU(s) "
+                                      "by the library's longest-first split (vsbpp_shard), no collective",
                        "launch_config": tuned["config"] if tuned else native.get_config(),
                        "autotuned": tuned is not None},
             "autotune": tuned,

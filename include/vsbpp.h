@@ -277,6 +277,22 @@ int vsbpp_pack_batch_noalloc(int64_t N, const int32_t *w_all, const int64_t *w_o
                              void *stream);
 
 /*
+ * vsbpp_shard -- split one batch across `world` processes, one per GPU, for
+ * the multi-GPU path (instances are independent problems, Section 6.1, so
+ * they shard with no collective on the data).  Longest processing time
+ * first: instances in decreasing m (equal m: lower index first) each go to
+ * the rank holding the fewest items so far (equal: lowest rank).  m is the
+ * cost: each membrane system is one warp's chain of m dependent item steps.
+ *   w_off[N+1]            host, CSR offsets of the batch
+ *   rank_of[N]            out (host): the rank that packs instance i
+ *   items_of_rank[world]  out (host, may be NULL): items assigned per rank
+ * Host-only and deterministic (every rank computes the same split); no CUDA
+ * call.  EINVAL for N < 0, world < 1, null arrays or decreasing offsets.
+ */
+int vsbpp_shard(int64_t N, const int64_t *w_off, int32_t world, int32_t *rank_of,
+                int64_t *items_of_rank);
+
+/*
  * vsbpp_pack_plain -- the same batch, packed the plain way: one kernel launch
  * per instance, one instance after another on `stream`, each launch a single
  * thread block with the per-instance kernel.  Same arguments and results as

@@ -16,6 +16,8 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <numeric>
+#include <queue>
 #include <vector>
 
 #include "internal.h"
@@ -1224,6 +1226,37 @@ int vsbpp_pack_plain(int64_t N, const int32_t* w_all, const int64_t* w_off, cons
                      int64_t* total, int32_t* status, void* stream) {
     return batch_common(N, w_all, w_off, B_all, B_off, max_m, p, bin_of_item_all, bin_type_all,
                         num_bins, total, status, stream, true);
+}
+
+int vsbpp_shard(int64_t N, const int64_t* w_off, int32_t world, int32_t* rank_of, int64_t* items_of_rank) {
+    try {
+        if (N < 0 || world < 1 || !w_off || (N > 0 && !rank_of)) return VSBPP_EINVAL;
+        for (int64_t i = 0; i < N; ++i)
+            if (w_off[i + 1] < w_off[i]) return VSBPP_EINVAL;
+        std::vector<int64_t> idx(static_cast<size_t>(N));
+        std::iota(idx.begin(), idx.end(), int64_t(0));
+        std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+            return w_off[a + 1] - w_off[a] > w_off[b + 1] - w_off[b];
+        });
+        // least-loaded rank first, lowest rank on ties
+        using Load = std::pair<int64_t, int32_t>;
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (int32_t r = 0; r < world; ++r) heap.push(Load(0, r));
+        std::vector<int64_t> load(static_cast<size_t>(world), 0);
+        for (int64_t i : idx) {
+            Load top = heap.top();
+            heap.pop();
+            rank_of[i] = top.second;
+            top.first += w_off[i + 1] - w_off[i];
+            load[static_cast<size_t>(top.second)] = top.first;
+            heap.push(top);
+        }
+        if (items_of_rank)
+            for (int32_t r = 0; r < world; ++r) items_of_rank[r] = load[static_cast<size_t>(r)];
+        return VSBPP_OK;
+    } catch (...) {
+        return VSBPP_ENOMEM;      // no exception crosses the C interface
+    }
 }
 
 int vsbpp_counters_enable(int enable) {

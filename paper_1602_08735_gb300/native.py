@@ -27,7 +27,7 @@ REMARK3, PRESORT = 1, 2       # option flags (vsbpp_params.flags)
 EXPORTS = (
     "vsbpp_strerror", "vsbpp_version", "vsbpp_last_cuda_error",
     "vsbpp_pack", "vsbpp_pack_device", "vsbpp_pack_batch", "vsbpp_pack_plain",
-    "vsbpp_pack_batch_host", "vsbpp_pack_batch_noalloc",
+    "vsbpp_pack_batch_host", "vsbpp_pack_batch_noalloc", "vsbpp_shard",
     "vsbpp_counters_enable", "vsbpp_counters_read",
     "vsbpp_kernel_timing_enable", "vsbpp_kernel_timing_read",
     "vsbpp_plan_create", "vsbpp_plan_run", "vsbpp_plan_destroy",
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = [i64, vp, vp, vp, vp, i64, pp, vp, vp, vp, vp, vp, vp]
+        lib.vsbpp_shard.restype = ctypes.c_int
+        lib.vsbpp_shard.argtypes = [i64, vp, i32, vp, vp]
         lib.vsbpp_pack_batch_host.restype = ctypes.c_int
         lib.vsbpp_pack_batch_host.argtypes = [i64, vp, vp, vp, vp, i64, pp, vp, vp, vp, vp, vp]
         if hasattr(lib, "vsbpp_plan_create"):
@@ -295,6 +297,19 @@ def pack_batch_noalloc(db: DeviceBatch, out: DeviceResult, heuristic: int = H1, 
     return _batch_call("vsbpp_pack_batch_noalloc", db, out,
                        make_params(heuristic, criterion, sublist_size, preopen, seed, flags, max_open),
                        stream, max_m)
+
+
+def shard(w_off, world: int):
+    """vsbpp_shard: (rank_of[N] int32, items_of_rank[world] int64) for a
+    batch's host CSR offsets split over `world` processes."""
+    w_off = np.ascontiguousarray(w_off, dtype=np.int64)
+    N = int(w_off.shape[0]) - 1
+    rank_of = np.zeros(max(N, 1), dtype=np.int32)
+    items = np.zeros(max(world, 1), dtype=np.int64)
+    rc = load().vsbpp_shard(N, _ptr(w_off), int(world), _ptr(rank_of), _ptr(items))
+    if rc != 0:
+        raise VsbppError(rc, "vsbpp_shard")
+    return rank_of[:N].copy(), items[:world].copy()
 
 
 @dataclass

@@ -1,6 +1,7 @@
 """The multi-rank path of bench.py on CPU: two gloo ranks rendezvous on
-127.0.0.1, each packs its own shard of instances (different seeds, no
-collective on the data), and the timing is reduced with max/sum over ranks."""
+127.0.0.1, each takes its part of one global batch under the library's
+split (no collective on the data), and the timing is reduced with max/sum
+over ranks."""
 import os
 import socket
 import subprocess
@@ -21,9 +22,12 @@ assert ws == 2
 mx = bench.max_over_ranks(float(rank + 1), ws)
 sm = bench.sum_over_ranks(float(10 * (rank + 1)), ws)
 bench.barrier(ws)
-shard = I.config3(seed=3 + rank, N=8)
-print(json.dumps({"rank": rank, "max": mx, "sum": sm, "first_w": int(shard.w_all[0]),
-                  "items": shard.total_items}))
+from paper_1602_08735_gb300 import native
+native.load()
+part = bench.rank_batch(native, I, 8, ws, rank)
+whole = I.config3(seed=3, N=16)
+print(json.dumps({"rank": rank, "max": mx, "sum": sm, "instances": part.N,
+                  "items": part.total_items, "whole_items": whole.total_items}))
 import torch.distributed as dist
 dist.destroy_process_group()
 """ % ROOT
@@ -39,6 +43,8 @@ def _free_port():
 
 def test_two_gloo_ranks():
     pytest.importorskip("torch")
+    from paper_1602_08735_gb300 import build
+    build.build()
     port = _free_port()
     procs = []
     for r in range(2):
@@ -54,4 +60,5 @@ def test_two_gloo_ranks():
         res.append(json.loads(o.strip().splitlines()[-1]))
     assert all(r["max"] == 2.0 for r in res)
     assert all(r["sum"] == 30.0 for r in res)
-    assert res[0]["items"] != res[1]["items"] or res[0]["first_w"] != res[1]["first_w"]
+    assert res[0]["instances"] + res[1]["instances"] == 16
+    assert res[0]["items"] + res[1]["items"] == res[0]["whole_items"]
