@@ -182,6 +182,8 @@ struct Scratch {
     int32_t* ps_boi = nullptr;  int64_t cap_ps_boi = 0;
     int32_t* ps_stat = nullptr; int64_t cap_ps_stat = 0;
     int32_t* bk_rec = nullptr;  int64_t cap_bk_rec = 0;     // bounded space: per-bin records
+    uint16_t* kd_over = nullptr; int64_t cap_kd_over = 0;  // cluster kernel: bins past shared memory
+    int32_t* kd_dense = nullptr; int64_t cap_kd_dense = 0; // cluster kernel: dense id per bin
     // host-memory batch call: device copies of the CSR offsets and the per-instance outputs
     int64_t* hb_woff = nullptr; int64_t cap_hb_woff = 0;
     int32_t* hb_Boff = nullptr; int64_t cap_hb_Boff = 0;
@@ -269,7 +271,7 @@ struct Scratch {
         void* bufs[] = {cls, order, nu, unit_base, unit_count, unit_total, local_types, fixed, kc_slots,
                         spill_list, spill_list2, h2x_best, h_w, h_B, h_boi, h_bt, h_small,
                         ps_w, ps_perm, ps_tmp, ps_boi, ps_stat, bk_rec, hb_woff, hb_Boff, hb_nb,
-                        hb_tot, hb_st};
+                        hb_tot, hb_st, kd_over, kd_dense};
         for (void* q : bufs) free_buf(q);
         for (void* q : retired) free_buf(q);
         *this = Scratch();
@@ -395,8 +397,21 @@ struct KCShape {
     int grid = 0;
 };
 
+// Cluster kernel for the systems beyond shared memory whose B_1 and bins fit
+// its 16-bit slots (the rest go to the global-memory kernel).
+struct KDShape {
+    bool enabled = false;
+    int smem = 0;
+    int segs0 = 0, segs1 = 0;
+    int max_B1 = 0;
+    int pres = 0;
+    int clusters = 0;
+    int64_t over_bins = 0;
+};
+
 struct LaunchPlan {
     Mode mode;
+    KDShape kd{};
     vsbpp_config cfg;
     H1Shape large{}, small{}, wide{}, sub{};
     H1Shape full{};       // worst-case slots: repacks systems that outgrew large/small
@@ -629,6 +644,21 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         kc.grid = static_cast<int>(std::min<int64_t>(int64_t(occ) * di.sms, std::max<int64_t>(N, 1)));
     }
     if (!lp.kc.enabled) lp.large16_cap_m = 0;     // no global-memory fallback for its spills
+    if (lp.kc.enabled) {
+        // the systems of the global-memory class go to two-CTA clusters first:
+        // 16-bit slots in both CTAs' shared memory (B_1 <= 1023 with BF items,
+        // whose presence rows take 128 KB of CTA 0; else B_1 <= 2047)
+        KDShape& kd = lp.kd;
+        kd.pres = bfi;
+        kd.max_B1 = kd.pres ? 1023 : kKDMaxB1;
+        kd.smem = smax;
+        kd.segs1 = kd.smem / kKDSegBytes;
+        kd.segs0 = (kd.smem - kd_bins_offset(kd.max_B1, kd.pres)) / kKDSegBytes;
+        kd.over_bins = std::max<int64_t>(0, int64_t(kKDMaxBins) - int64_t(kd.segs0 + kd.segs1) * kKDSeg);
+        const int mc = kd.segs0 > 0 ? kd_max_clusters(prm.criterion, kd.smem) : 0;
+        kd.clusters = static_cast<int>(std::min<int64_t>(mc, std::max<int64_t>(N, 1)));
+        kd.enabled = kd.clusters > 0;
+    }
     return VSBPP_OK;
 }
 
@@ -652,6 +682,11 @@ int ensure_scratch(Scratch& sc, const LaunchPlan& lp, int64_t N, int64_t total_m
         if ((rc = sc.grow(sc.spill_list2, sc.cap_spill_list2, N))) return rc;
         if (lp.kc.enabled && (rc = sc.grow(sc.kc_slots, sc.cap_kc_slots, int64_t(lp.kc.grid) * lp.kc.bin_cap)))
             return rc;
+        if (lp.kd.enabled) {
+            if ((rc = sc.grow(sc.kd_over, sc.cap_kd_over, std::max<int64_t>(1, lp.kd.clusters * lp.kd.over_bins))))
+                return rc;
+            if ((rc = sc.grow(sc.kd_dense, sc.cap_kd_dense, int64_t(lp.kd.clusters) * kKDMaxBins))) return rc;
+        }
         return VSBPP_OK;
     }
     const int64_t U = total_m / std::max<int64_t>(lp.mode.s, 1) + N;   // >= sum ceil(m_i/s)
@@ -818,8 +853,37 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
             kp.max_B1 = lp.kc.max_B1;
             kp.pres_words = lp.kc.pres_words;
             kp.counters = g_counters;
-            VS_TRY(kc_launch(kp, lp.kc.grid, lp.kc.smem, st));
-            // systems that outgrew the worst-case shared-memory shape
+            if (lp.kd.enabled) {
+                // the class in two-CTA clusters; the systems they cannot hold
+                // join the list the global-memory kernel packs next
+                KDParams dp;
+                std::memset(&dp, 0, sizeof(dp));
+                dp.in = in;
+                dp.out = out;
+                dp.criterion = prm.criterion;
+                dp.preopen = prm.preopen;
+                dp.remark3 = lp.remark3 ? 1 : 0;
+                dp.seed = prm.seed;
+                dp.order = sc.order;
+                dp.seg = sc.seg();
+                dp.segment = kClassHuge;
+                dp.queue = sc.queue() + kClassHuge;
+                dp.spill_list = sc.spill_list2;
+                dp.spill_seg = sc.spill_seg() + 2;
+                dp.over = sc.kd_over;
+                dp.over_bins = lp.kd.over_bins;
+                dp.dense = sc.kd_dense;
+                dp.max_B1 = lp.kd.max_B1;
+                dp.pres = lp.kd.pres;
+                dp.segs0 = lp.kd.segs0;
+                dp.segs1 = lp.kd.segs1;
+                dp.smem = lp.kd.smem;
+                dp.counters = g_counters;
+                VS_TRY(kd_launch(dp, lp.kd.clusters, st));
+            } else {
+                VS_TRY(kc_launch(kp, lp.kc.grid, lp.kc.smem, st));
+            }
+            // systems that outgrew the worst-case shared-memory shape (or the clusters)
             kp.order = sc.spill_list2;
             kp.seg = sc.spill_seg() + 2;
             kp.segment = 0;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "vsbpp.h"
@@ -12,6 +13,7 @@
 #include "prep_params.cuh"
 #include "kc_params.cuh"
 #include "variants_params.cuh"
+#include "kd_params.cuh"
 
 namespace vsbpp {
 
@@ -49,6 +51,9 @@ int h1w16_slots();
 int h1w16_bytes(int bf_index);
 
 cudaError_t kc_launch(const KCParams& p, int grid, int smem, cudaStream_t st);
+// Cluster kernel (bins in two CTAs' shared memory): `clusters` two-CTA clusters.
+cudaError_t kd_launch(const KDParams& p, int clusters, cudaStream_t st);
+int kd_max_clusters(int criterion, int smem);
 int kc_blocks_per_sm(int smem);
 
 cudaError_t h2_launch(const H2Params& p, int threads, int grid, int smem, cudaStream_t st);

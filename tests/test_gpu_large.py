@@ -96,6 +96,47 @@ def test_config4_full_size(crit):
             _check_prefix(res.bin_of_item, res.bin_type, pre)
 
 
+@pytest.mark.parametrize("crit", [native.BF, native.RANDOM])
+def test_cluster_kernel_remote_and_overflow(crit):
+    """A system of ~1.8*10^5 bins: past CTA 0's shared memory into CTA 1's
+    (distributed shared memory) and into the global-memory overflow of the
+    two-CTA cluster kernel (BF items: 165 k bins on chip), against the
+    oracle; RANDOM keeps every summary (segment maxima and presence rows)."""
+    rng = np.random.default_rng(122)
+    w = I.mixture_weights(rng, 0.9, (501, 1000), (1, 300), 200_000)
+    b = I.from_instances([(w, np.array([1000, 700], dtype=np.int32))])
+    assert_same(b, run_batch(b, 1, crit, seed=8), run_oracle(b, 1, crit, seed=8), f"kd overflow c{crit}")
+
+
+@pytest.mark.parametrize("crit", [native.FF, native.BF, native.WF])
+def test_cluster_kernel_closed_form(crit):
+    """Items heavier than half of the one capacity: each opens its own bin
+    and divides off the empty bin the next item takes (Rule 5), so item j is
+    in bin j and the total is m * B_1 for every criterion.  2.5*10^5 items
+    reach the global-memory overflow for every criterion; 6*10^5 pass the
+    cluster kernel's 2^19 bins, and the global-memory kernel packs them."""
+    rng = np.random.default_rng(130 + crit)
+    ms = (250_000, 600_000)
+    b = I.from_instances([(rng.integers(501, 1001, size=m).astype(np.int32), np.array([1000], dtype=np.int32))
+                          for m in ms])
+    got = run_batch(b, 1, crit)
+    assert np.all(got.status == 0)
+    for i, mi in enumerate(ms):
+        a = int(b.w_off[i])
+        assert got.num_bins[i] == mi and got.total[i] == 1000 * mi
+        assert np.array_equal(got.bin_of_item[a:a + mi], np.arange(mi, dtype=np.int32))
+        assert np.all(got.bin_type[a:a + mi] == 0)
+
+
+def test_cluster_kernel_wide_residuals_hand_on():
+    """B_1 past the presence rows of BF (1023): the global-memory kernel."""
+    rng = np.random.default_rng(140)
+    b = I.from_instances([(I.mixture_weights(rng, 0.8, (1, 100), (400, 1500), 60_000),
+                           np.array([1500, 1000, 640, 300], dtype=np.int32))])
+    for crit in (native.BF, native.RANDOM, native.WF):
+        assert_same(b, run_batch(b, 1, crit, seed=3), run_oracle(b, 1, crit, seed=3), f"wide B1 c{crit}")
+
+
 def test_many_tiny_instances():
     """100,000 instances of 0..12 items (empty ones included) in one batch:
     the size-class machinery, the work queue and the composition pass at a
