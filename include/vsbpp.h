@@ -41,8 +41,11 @@
  *   zero bins and total 0.  On an error the output arrays of that instance
  *   are unspecified and num_bins = total = 0.
  *
- * Threading: every entry point may be called from any host thread; calls are
- * serialised internally per process.  Device entry points are asynchronous
+ * Threading: every entry point may be called from any host thread.  Calls on
+ * different streams (or devices) proceed at the same time; calls on the same
+ * stream, on the same plan, or host-memory calls on the same device, are
+ * serialised by the library.  The launch configuration and the counter and
+ * timing switches are process-wide.  Device entry points are asynchronous
  * with respect to the host and ordered on the caller's stream.
  *
  * Parameter layout changed in 1.1.0: `reserved` became `flags` and `max_open`

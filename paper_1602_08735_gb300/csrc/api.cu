@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -26,7 +27,13 @@ using namespace vsbpp;
 
 namespace {
 
+// Locks.  g_mu guards the process-wide tables (launch configuration, work
+// counters, the per-stream scratch map, per-device pools and host contexts)
+// and is held only while they are read or changed.  Each stream's scratch,
+// each plan and each device's host context has a lock of its own, held for
+// a whole call, so calls on different streams or devices proceed at once.
 std::recursive_mutex g_mu;
+std::mutex g_timing_mu;          // the kernel-timing ring
 std::atomic<int> g_last_cuda{0};
 unsigned long long* g_counters = nullptr;   // device {items, fit tests} or null
 
@@ -42,6 +49,7 @@ struct KernelTiming {
 
 // Records the start event of the main launch on `st` when timing applies.
 bool timing_begin(cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
     if (!g_timing.on) return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
@@ -62,6 +70,7 @@ bool timing_begin(cudaStream_t st) {
 
 void timing_end(bool started, cudaStream_t st) {
     if (!started) return;
+    std::lock_guard<std::mutex> lk(g_timing_mu);
     auto& pr = g_timing.ev[g_timing.head];
     if (cudaEventRecord(pr[1], st) != cudaSuccess) return;
     g_timing.head = (g_timing.head + 1) % KernelTiming::kRing;
@@ -74,10 +83,14 @@ struct DeviceInfo {
     int max_smem_optin = 0;
 };
 
-DeviceInfo& device_info() {
-    static DeviceInfo di;
+// Attributes of the current device (cached per device).
+DeviceInfo device_info() {
+    static std::mutex mu;
+    static std::map<int, DeviceInfo> cache;
     int dev = 0;
     cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    DeviceInfo& di = cache[dev];
     if (di.dev != dev) {
         di.dev = dev;
         cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev);
@@ -118,6 +131,7 @@ cudaMemPool_t scratch_pool() {
     static std::map<int, cudaMemPool_t> pools;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
     auto it = pools.find(dev);
     if (it != pools.end()) return it->second;
     cudaMemPool_t pool = nullptr;
@@ -151,6 +165,7 @@ cudaMemPool_t scratch_pool() {
 // cudaMalloc; an outgrown buffer met under capture is set aside and freed by
 // the next call made outside capture.
 struct Scratch {
+    std::shared_ptr<std::recursive_mutex> mu = std::make_shared<std::recursive_mutex>();   // held for a call
     bool ordered = false;            // grows in stream order on `ord`
     cudaStream_t ord = nullptr;
     std::vector<void*> sync_bufs;    // cudaMalloc buffers of an ordered scratch
@@ -274,7 +289,9 @@ struct Scratch {
                         hb_tot, hb_st, kd_over, kd_dense};
         for (void* q : bufs) free_buf(q);
         for (void* q : retired) free_buf(q);
+        auto keep = mu;
         *this = Scratch();
+        mu = keep;
     }
 };
 
@@ -284,7 +301,10 @@ std::map<cudaStream_t, Scratch>& stream_scratch() {
 }
 
 // The scratch of stream `st` (created on first use, growing in stream order).
+// The map's nodes never move, so the reference stays valid; the caller holds
+// the scratch's own lock while it uses it.
 Scratch& scratch_for(cudaStream_t st) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
     auto& m = stream_scratch();
     auto it = m.find(st);
     if (it == m.end()) {
@@ -301,6 +321,7 @@ Scratch& scratch_for(cudaStream_t st) {
 // overlaps the transfer of the other.
 struct HostCtx {
     static constexpr size_t kChunk = size_t(8) << 20;
+    std::recursive_mutex mu;         // held for a whole host-memory call
     cudaStream_t st = nullptr;
     void* pin[2] = {nullptr, nullptr};
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -364,6 +385,7 @@ HostCtx* host_ctx() {
     static std::map<int, HostCtx> ctx;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
     HostCtx& c = ctx[dev];
     return c.init() == VSBPP_OK ? &c : nullptr;
 }
@@ -411,6 +433,7 @@ struct KDShape {
 
 struct LaunchPlan {
     Mode mode;
+    unsigned long long* counters = nullptr;   // work counters when the plan was made (or null)
     KDShape kd{};
     vsbpp_config cfg;
     H1Shape large{}, small{}, wide{}, sub{};
@@ -426,6 +449,17 @@ struct LaunchPlan {
     int bk_grid = 0;
     int prep_grid = 0;
 };
+
+// The process-wide settings a launch plan reads, copied under g_mu.
+struct Snapshot {
+    vsbpp_config cfg;
+    unsigned long long* counters;
+};
+
+Snapshot snapshot() {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    return Snapshot{g_cfg, g_counters};
+}
 
 int round4(int64_t x) { return static_cast<int>((x + 3) & ~int64_t(3)); }
 // Shared-memory kernels read whole 128-bin segments.
@@ -514,10 +548,11 @@ void cap_grid(H1Shape& sh, int64_t units) {
     if (blocks < sh.grid) sh.grid = static_cast<int>(blocks);
 }
 
-int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp) {
-    const DeviceInfo& di = device_info();
+int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp, const Snapshot& snap) {
+    const DeviceInfo di = device_info();
     if (di.sms <= 0) return record(cudaErrorNoDevice);
-    lp.cfg = g_cfg;
+    lp.cfg = snap.cfg;
+    lp.counters = snap.counters;
     const int chunk = lp.cfg.chunk;
     const int smax = di.max_smem_optin;
     max_m = std::max<int64_t>(max_m, 1);
@@ -700,7 +735,7 @@ int ensure_scratch(Scratch& sc, const LaunchPlan& lp, int64_t N, int64_t total_m
 }
 
 H1Params h1_params(const BatchView& in, const OutView& out, const vsbpp_params& prm,
-                   const H1Shape& sh) {
+                   const H1Shape& sh, unsigned long long* counters) {
     H1Params p;
     std::memset(&p, 0, sizeof(p));
     p.in = in;
@@ -717,7 +752,7 @@ H1Params h1_params(const BatchView& in, const OutView& out, const vsbpp_params& 
     p.group_bytes = sh.smem / sh.groups;
     p.cls = nullptr;
     p.want_cls = 0;
-    p.counters = g_counters;
+    p.counters = counters;
     p.bf_index = sh.bf_index;
     return p;
 }
@@ -771,7 +806,7 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
             bp.max_open = static_cast<int32_t>(prm.max_open);
             bp.seed = prm.seed;
             bp.rec = sc.bk_rec;
-            bp.counters = g_counters;
+            bp.counters = lp.counters;
             if (plain) {
                 for (int64_t i = 0; i < in.N; ++i) {       // one single-warp launch per instance
                     bp.range_begin = i;
@@ -795,7 +830,7 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
             if (plain && c == kClassLarge) {
                 // the plain path: one single-block launch per instance, in turn
                 for (int64_t i = 0; i < in.N; ++i) {
-                    H1Params p = h1_params(in, out, prm, sh);
+                    H1Params p = h1_params(in, out, prm, sh, lp.counters);
                     p.range_begin = i;
                     p.range_end = i + 1;
                     p.cls = sc.cls;
@@ -809,7 +844,7 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
             }
             // (plain path: the rare wide-slot and global-memory instances
             // share one work-stealing launch per class)
-            H1Params p = h1_params(in, out, prm, sh);
+            H1Params p = h1_params(in, out, prm, sh, lp.counters);
             p.order = sc.order;
             p.seg = sc.seg();
             p.segment = c;
@@ -826,7 +861,7 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
         {
             // systems that outgrew their slots, repacked from the start at full
             // size; a system that outgrows that too is listed for global memory
-            H1Params p = h1_params(in, out, prm, lp.full);
+            H1Params p = h1_params(in, out, prm, lp.full, lp.counters);
             p.order = sc.spill_list;
             p.seg = sc.spill_seg();
             p.segment = 0;
@@ -852,7 +887,7 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
             kp.bin_cap = lp.kc.bin_cap;
             kp.max_B1 = lp.kc.max_B1;
             kp.pres_words = lp.kc.pres_words;
-            kp.counters = g_counters;
+            kp.counters = lp.counters;
             if (lp.kd.enabled) {
                 // the class in two-CTA clusters; the systems they cannot hold
                 // join the list the global-memory kernel packs next
@@ -878,7 +913,7 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
                 dp.segs0 = lp.kd.segs0;
                 dp.segs1 = lp.kd.segs1;
                 dp.smem = lp.kd.smem;
-                dp.counters = g_counters;
+                dp.counters = lp.counters;
                 VS_TRY(kd_launch(dp, lp.kd.clusters, st));
             } else {
                 VS_TRY(kc_launch(kp, lp.kc.grid, lp.kc.smem, st));
@@ -929,7 +964,7 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
             xp.seg_units = sc.seg_units();
             xp.best = sc.h2x_best;
             xp.queue = sc.queue();
-            xp.counters = g_counters;
+            xp.counters = lp.counters;
             xp.only_instance = only;
             VS_TRY(cudaMemsetAsync(sc.queue(), 0, sizeof(unsigned long long), st));     // task counter
             const bool timed = !plain && timing_begin(st);
@@ -949,12 +984,12 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
             hp.sublist = static_cast<int32_t>(lp.mode.s);
             hp.max_bins = lp.h2_max_bins;
             hp.only_instance = only;
-            hp.counters = g_counters;
+            hp.counters = lp.counters;
             const bool timed = !plain && timing_begin(st);
             VS_TRY(h2_launch(hp, lp.h2_threads, plain ? 1 : lp.h2_grid, lp.h2_smem, st));
             timing_end(timed, st);
         } else {
-            H1Params p = h1_params(in, out, prm, lp.sub);
+            H1Params p = h1_params(in, out, prm, lp.sub, lp.counters);
             p.units.unit_base = sc.unit_base;
             p.units.sublist = lp.mode.s;
             p.compose = 1;
@@ -1031,11 +1066,11 @@ int batch_common(int64_t N, const int32_t* w_all, const int64_t* w_off, const in
         int rc = check_params(p);
         if (rc) return rc;
         const vsbpp_params prm = defaults(p);
-        std::lock_guard<std::recursive_mutex> lk(g_mu);
         LaunchPlan lp;
-        if ((rc = build_plan(prm, max_m, N, lp))) return rc;
+        if ((rc = build_plan(prm, max_m, N, lp, snapshot()))) return rc;
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         Scratch& sc = scratch_for(st);
+        std::lock_guard<std::recursive_mutex> lk(*sc.mu);
         // sublist scratch is sized from the host-side bound N * max_m, so the call
         // never has to read the device offsets back
         const int64_t total_m = scratch_items(lp, N, max_m);
@@ -1065,20 +1100,15 @@ int time_config(const vsbpp_config& cfg, int64_t N, const int32_t* w_all, const 
                 const int32_t* B_all, const int32_t* B_off, int64_t max_m, const vsbpp_params& prm,
                 int32_t* boi, int32_t* bt, int64_t* nb, int64_t* tot, int32_t* status,
                 cudaStream_t st, int reps, double* ms_out) {
-    const vsbpp_config saved = g_cfg;
-    g_cfg = cfg;
     LaunchPlan lp;
-    int rc = build_plan(prm, max_m, N, lp);
-    if (rc) {
-        g_cfg = saved;
-        return rc;
-    }
+    Snapshot snap = snapshot();
+    snap.cfg = cfg;                            // the candidate, not the installed table
+    int rc = build_plan(prm, max_m, N, lp, snap);
+    if (rc) return rc;
     Scratch& sc = scratch_for(st);
+    std::lock_guard<std::recursive_mutex> lk(*sc.mu);
     const int64_t total_m = scratch_items(lp, N, max_m);
-    if ((rc = ensure_scratch(sc, lp, N, total_m))) {
-        g_cfg = saved;
-        return rc;
-    }
+    if ((rc = ensure_scratch(sc, lp, N, total_m))) return rc;
     BatchView in{N, w_all, w_off, 0, B_all, B_off, 0};
     OutView out{boi, bt, nb, tot, status, nullptr, nullptr, nullptr};
     cudaEvent_t e0, e1;
@@ -1096,7 +1126,6 @@ int time_config(const vsbpp_config& cfg, int64_t N, const int32_t* w_all, const 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    g_cfg = saved;
     *ms_out = best;
     return rc;
 }
@@ -1157,11 +1186,11 @@ int vsbpp_pack_device(const int32_t* w, int64_t m, const int32_t* B, int32_t n, 
             return VSBPP_EINVAL;
         if ((rc = check_params(p))) return rc;
         const vsbpp_params prm = defaults(p);
-        std::lock_guard<std::recursive_mutex> lk(g_mu);
         LaunchPlan lp;
-        if ((rc = build_plan(prm, std::max<int64_t>(m, 1), 1, lp))) return rc;
+        if ((rc = build_plan(prm, std::max<int64_t>(m, 1), 1, lp, snapshot()))) return rc;
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         Scratch& sc = scratch_for(st);
+        std::lock_guard<std::recursive_mutex> lk(*sc.mu);
         if ((rc = ensure_scratch(sc, lp, 1, m))) return rc;
         BatchView in{1, w, nullptr, m, B, nullptr, n};
         OutView out{bin_of_item, bin_type, num_bins, total_capacity, status, nullptr, nullptr, nullptr};
@@ -1180,11 +1209,12 @@ int vsbpp_pack(const int32_t* w, int64_t m, const int32_t* B, int32_t n, const v
         if ((rc = check_params(p))) return rc;
         *num_bins = 0;
         *total_capacity = 0;
-        std::lock_guard<std::recursive_mutex> lk(g_mu);
         HostCtx* hc = host_ctx();                 // this device's own stream and staging
         if (!hc) return VSBPP_ECUDA;
+        std::lock_guard<std::recursive_mutex> lkh(hc->mu);
         cudaStream_t own = hc->st;
         Scratch& sc = scratch_for(own);
+        std::lock_guard<std::recursive_mutex> lk(*sc.mu);
         if ((rc = sc.grow(sc.h_w, sc.cap_h_w, m))) return rc;
         if ((rc = sc.grow(sc.h_B, sc.cap_h_B, n))) return rc;
         if ((rc = sc.grow(sc.h_boi, sc.cap_h_boi, m))) return rc;
@@ -1238,13 +1268,14 @@ int vsbpp_pack_batch_host(int64_t N, const int32_t* w_all, const int64_t* w_off,
         if (max_m == 0) max_m = mm;
         if (mm > max_m) return VSBPP_EINVAL;
         const vsbpp_params prm = defaults(p);
-        std::lock_guard<std::recursive_mutex> lk(g_mu);
         HostCtx* hc = host_ctx();
         if (!hc) return VSBPP_ECUDA;
+        std::lock_guard<std::recursive_mutex> lkh(hc->mu);
         cudaStream_t st = hc->st;
         LaunchPlan lp;
-        if ((rc = build_plan(prm, max_m, N, lp))) return rc;
+        if ((rc = build_plan(prm, max_m, N, lp, snapshot()))) return rc;
         Scratch& sc = scratch_for(st);
+        std::lock_guard<std::recursive_mutex> lk(*sc.mu);
         if ((rc = ensure_scratch(sc, lp, N, std::max<int64_t>(total_m, 1)))) return rc;
         if ((rc = sc.grow(sc.h_w, sc.cap_h_w, total_m))) return rc;
         if ((rc = sc.grow(sc.h_B, sc.cap_h_B, total_B))) return rc;
@@ -1356,7 +1387,7 @@ int vsbpp_counters_read(vsbpp_counters* out, int reset) {
 }
 
 int vsbpp_kernel_timing_enable(int enable) {
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    std::lock_guard<std::mutex> lk(g_timing_mu);
     g_timing.on = enable != 0;
     g_timing.count = 0;
     return VSBPP_OK;
@@ -1365,7 +1396,7 @@ int vsbpp_kernel_timing_enable(int enable) {
 int vsbpp_kernel_timing_read(float* ms, int32_t max, int32_t* count) {
     try {
         if (!count || max < 0 || (max > 0 && !ms)) return VSBPP_EINVAL;
-        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        std::lock_guard<std::mutex> lk(g_timing_mu);
         *count = 0;
         const int have = g_timing.count;
         const int first = (g_timing.head - have + KernelTiming::kRing) % KernelTiming::kRing;
@@ -1412,14 +1443,13 @@ int vsbpp_plan_create(int64_t N, int64_t total_m, int64_t max_m, const vsbpp_par
         if (N < 0 || total_m < 0 || max_m < 0) return VSBPP_EINVAL;
         int rc = check_params(p);
         if (rc) return rc;
-        std::lock_guard<std::recursive_mutex> lk(g_mu);
         PlanImpl* pl = new (std::nothrow) PlanImpl();
         if (!pl) return VSBPP_ENOMEM;
         pl->N = N;
         pl->total_m = total_m;
         pl->max_m = max_m;
         pl->prm = defaults(p);
-        if ((rc = build_plan(pl->prm, max_m, N, pl->lp)) ||
+        if ((rc = build_plan(pl->prm, max_m, N, pl->lp, snapshot())) ||
             (rc = ensure_scratch(pl->sc, pl->lp, N, std::max<int64_t>(total_m, 1))) ||
             (rc = record(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking)))) {
             pl->sc.release();
@@ -1441,7 +1471,7 @@ int vsbpp_plan_run(vsbpp_plan* plan, const int32_t* w_all, const int64_t* w_off,
         PlanImpl* pl = reinterpret_cast<PlanImpl*>(plan);
         if (pl->N == 0) return VSBPP_OK;
         if (!w_off || !B_all || !B_off || !boi || !bt || !nb || !tot || !status) return VSBPP_EINVAL;
-        std::lock_guard<std::recursive_mutex> lk(g_mu);
+        std::lock_guard<std::recursive_mutex> lk(*pl->sc.mu);   // one call per plan at a time
         cudaStream_t ust = static_cast<cudaStream_t>(stream);
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         VS_TRY(cudaStreamIsCapturing(ust, &cs));
@@ -1483,8 +1513,8 @@ int vsbpp_plan_run(vsbpp_plan* plan, const int32_t* w_all, const int64_t* w_off,
 
 int vsbpp_plan_destroy(vsbpp_plan* plan) {
     if (!plan) return VSBPP_OK;
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
     PlanImpl* pl = reinterpret_cast<PlanImpl*>(plan);
+    { std::lock_guard<std::recursive_mutex> lk(*pl->sc.mu); }    // no call of this plan is running
     cudaDeviceSynchronize();
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->cap) cudaStreamDestroy(pl->cap);
@@ -1503,10 +1533,10 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
         int rc = check_params(p);
         if (rc) return rc;
         const vsbpp_params prm = defaults(p);
-        std::lock_guard<std::recursive_mutex> lk(g_mu);
         cudaStream_t st = static_cast<cudaStream_t>(stream);
+        std::lock_guard<std::recursive_mutex> lk(*scratch_for(st).mu);
         // Coordinate descent over the four knobs, starting from the current table.
-        vsbpp_config cur = g_cfg;
+        vsbpp_config cur = snapshot().cfg;
         double cur_ms = 0;
         if ((rc = time_config(cur, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb, tot, status,
                               st, 3, &cur_ms)))
@@ -1541,7 +1571,10 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
                 }
             }
         }
-        g_cfg = cur;
+        {
+            std::lock_guard<std::recursive_mutex> lkg(g_mu);
+            g_cfg = cur;
+        }
         if (best) *best = cur;
         if (best_ms) *best_ms = cur_ms;
         return VSBPP_OK;

@@ -253,3 +253,35 @@ def test_kernel_timing_hook():
         native.kernel_timing_enable(False)
     assert native.pack_batch(db, out, 1, native.BF, 0) == 0
     assert native.kernel_timing_read() == []
+
+
+def test_two_host_threads_on_two_streams():
+    """Calls on different streams run at once (each stream's scratch has its
+    own lock); every result still equals the oracle's."""
+    import threading
+    b = I.config3(N=160, m_hi=4000, seed=77)
+    ref = run_oracle(b, 1, native.BF)
+    res, errs = {}, []
+
+    def work(k):
+        try:
+            st = torch.cuda.Stream()
+            db = native.DeviceBatch.from_host(b)
+            out = native.DeviceResult.empty(db.N, db.total_items)
+            for _ in range(3):
+                rc = native.pack_batch(db, out, 1, native.BF, stream=st)
+                assert rc == 0
+            st.synchronize()
+            res[k] = out.to_host(db.N, db.total_items)
+        except Exception as e:          # reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for k in range(2):
+        st_, boi, bt, nb, tot = res[k]
+        assert_same(b, oracle.BatchResult(st_, boi, bt, nb, tot), ref, f"thread {k}")
