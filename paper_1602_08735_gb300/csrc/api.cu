@@ -198,6 +198,10 @@ struct Scratch {
     int32_t* ps_stat = nullptr; int64_t cap_ps_stat = 0;
     int32_t* bk_rec = nullptr;  int64_t cap_bk_rec = 0;     // bounded space: per-bin records
     uint16_t* kd_over = nullptr; int64_t cap_kd_over = 0;  // cluster kernel: bins past shared memory
+    // a second stream for the single-warp class, forked from and joined to
+    // the caller's stream by events (captured into graphs as fork / join)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int32_t* kd_dense = nullptr; int64_t cap_kd_dense = 0; // cluster kernel: dense id per bin
     // host-memory batch call: device copies of the CSR offsets and the per-instance outputs
     int64_t* hb_woff = nullptr; int64_t cap_hb_woff = 0;
@@ -267,6 +271,13 @@ struct Scratch {
         return VSBPP_OK;
     }
 
+    int ensure_side() {
+        if (side) return VSBPP_OK;
+        VS_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        VS_TRY(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        return record(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    }
+
     int ensure_fixed() {
         if (fixed) return VSBPP_OK;
         void* q = nullptr;
@@ -289,6 +300,9 @@ struct Scratch {
                         hb_tot, hb_st, kd_over, kd_dense};
         for (void* q : bufs) free_buf(q);
         for (void* q : retired) free_buf(q);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
         auto keep = mu;
         *this = Scratch();
         mu = keep;
@@ -712,6 +726,7 @@ int ensure_scratch(Scratch& sc, const LaunchPlan& lp, int64_t N, int64_t total_m
     if (!lp.mode.compose) {
         if (lp.bounded && (rc = sc.grow(sc.bk_rec, sc.cap_bk_rec, 2 * total_m + int64_t(kMaxTypes) * N)))
             return rc;
+        if (lp.cfg.small_m > 0 && (rc = sc.ensure_side())) return rc;
         if ((rc = sc.grow(sc.order, sc.cap_order, N))) return rc;
         if ((rc = sc.grow(sc.spill_list, sc.cap_spill_list, N))) return rc;
         if ((rc = sc.grow(sc.spill_list2, sc.cap_spill_list2, N))) return rc;
@@ -746,6 +761,7 @@ H1Params h1_params(const BatchView& in, const OutView& out, const vsbpp_params& 
     p.criterion = prm.criterion;
     p.preopen = prm.preopen;
     p.remark3 = (prm.flags & VSBPP_REMARK3) ? 1 : 0;
+    p.no_trend = (prm.flags & VSBPP_PRESORT) ? 1 : 0;
     p.seed = prm.seed;
     p.chunk = sh.chunk;
     p.slot_cap = sh.slot_cap;
@@ -825,8 +841,17 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
             return VSBPP_OK;
         }
         const H1Shape* shapes[3] = {&lp.large, &lp.small, &lp.wide};
+        // the single-warp class (smaller slots, more warps per SM) runs beside
+        // the large one on a second stream: its blocks take the shared memory
+        // the large class's warps give back as its queue runs dry
+        const bool fork = !plain && lp.cfg.small_m > 0 && sc.side;
+        if (fork) {
+            VS_TRY(cudaEventRecord(sc.ev_fork, st));
+            VS_TRY(cudaStreamWaitEvent(sc.side, sc.ev_fork, 0));
+        }
         for (int c = 0; c < 3; ++c) {
             const H1Shape& sh = *shapes[c];
+            const cudaStream_t cs = (fork && c == kClassSmall) ? sc.side : st;
             if (plain && c == kClassLarge) {
                 // the plain path: one single-block launch per instance, in turn
                 for (int64_t i = 0; i < in.N; ++i) {
@@ -854,9 +879,13 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
                 p.spill_seg = sc.spill_seg();
             }
             if (c == kClassLarge) set_h16(p, lp, sc);
-            const bool timed = c == kClassLarge && timing_begin(st);
-            VS_TRY(launch_shape(sh, c == kClassWide, p, sh.groups, sh.grid, st));
-            timing_end(timed, st);
+            const bool timed = c == kClassLarge && timing_begin(cs);
+            VS_TRY(launch_shape(sh, c == kClassWide, p, sh.groups, sh.grid, cs));
+            timing_end(timed, cs);
+        }
+        if (fork) {
+            VS_TRY(cudaEventRecord(sc.ev_join, sc.side));
+            VS_TRY(cudaStreamWaitEvent(st, sc.ev_join, 0));
         }
         {
             // systems that outgrew their slots, repacked from the start at full

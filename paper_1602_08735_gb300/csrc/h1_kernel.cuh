@@ -120,6 +120,8 @@ struct H1Params {
     unsigned long long* counters;  // null, or {items, fit tests} to add to
     int32_t compose;        // 1: write sublist-local results (see OutView)
     int32_t remark3;        // 1: Rule 5 with Remark 3's per-type condition (VSBPP_REMARK3)
+    int32_t no_trend;       // 1: spill only when the slots run out (lists sorted by
+                            // decreasing weight open most of their bins first)
     int32_t bf_index;       // 1: the BF residual index is laid out (used when B_1 <= 1023)
     int32_t chunk;          // items staged per step (multiple of 32)
     int32_t slot_cap;       // bins per group (multiple of 128: whole segments)

@@ -173,7 +173,7 @@ struct H1Warp {
             // outgrow the slots (a larger shape, or global memory, repacks the
             // system from the start); after 2048 items also stop when the
             // bins so far, extrapolated to all k items, pass 9/8 of the slots
-            const bool trend = j0 >= 2048u &&
+            const bool trend = !p.no_trend && j0 >= 2048u &&
                                static_cast<uint64_t>(L) * k >
                                    static_cast<uint64_t>(cap_bins) * j0 + ((static_cast<uint64_t>(cap_bins) * j0) >> 3);
             if (p.spill_list && (L + 2u * cnt > cap_bins || trend)) {
@@ -439,7 +439,7 @@ struct H1Warp {
         uint32_t wpre = weight(w, 32 + ulane, k);
         for (uint32_t j0 = 0; j0 < k; j0 += 32u) {
             const uint32_t cnt = min(32u, k - j0);
-            const bool trend = j0 >= 2048u &&
+            const bool trend = !p.no_trend && j0 >= 2048u &&
                                static_cast<uint64_t>(L) * k > static_cast<uint64_t>(cap_bins) * j0;
             if (L + 2u * cnt > cap_bins || trend) {
                 if (lane == 0) {

@@ -89,12 +89,6 @@ struct KDWarp {
     }
 };
 
-// residual / type of slot k (0..7) of a 16-byte word
-__device__ __forceinline__ uint32_t kd_slot(const uint4& q, int k) {
-    const uint32_t w = k < 2 ? q.x : k < 4 ? q.y : k < 6 ? q.z : q.w;
-    return (k & 1) ? (w >> 16) : (w & 0xFFFFu);
-}
-
 template <int CRIT>
 __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -194,11 +188,11 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
             const uint32_t wnext = jn < m ? static_cast<uint32_t>(__ldg(w + jn)) : 0u;
             const int cnext = pick_criterion(p.criterion, p.seed, static_cast<uint64_t>(jn));
             const int cnt = static_cast<int>(min(static_cast<int64_t>(32), m - j0));
-            uint32_t bout = 0;
+            uint32_t bout = 0, fit_blk = 0;       // fit tests of this block (< 2^24)
             for (int jj = 0; jj < cnt; ++jj) {
                 const uint32_t wj = __shfl_sync(kFull, wcur, jj);
                 const int c = CRIT == kRandom ? __shfl_sync(kFull, ccur, jj) : CRIT;
-                fit_tests += L;
+                fit_blk += L;
                 const uint32_t nseg = (L + 511u) >> 9;
                 const uint32_t ntile = (nseg + 31u) >> 5;
 
@@ -241,40 +235,54 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                     }
                 }
 
-                // 2. the chosen bin in segment S (first match), or a new bin
+                // 2. the chosen bin in segment S (first match in slot order), or
+                //    a new bin.  Two slots per 32-bit word: halfword compares
+                //    give 0xFFFF per matching slot, one flag byte per slot
+                //    (byte permute) and __ffs give the first match of each half.
                 const bool hit = S >= 0;
                 uint32_t b, r_old, ty;
-                uint4 q0 = make_uint4(0u, 0u, 0u, 0u), q1 = q0;
+                uint32_t q[8], mk[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) q[k] = mk[k] = 0u;
                 uint32_t own = 32u, ok = 16u;         // lane and slot (0..15) of the chosen bin
                 if (hit) {
                     const uint4* sp = K.seg_ptr(static_cast<uint32_t>(S));
-                    q0 = sp[lane];
-                    q1 = sp[32 + lane];
-                    int f0 = 8, f1 = 8;
+                    const uint4 qa = sp[lane], qb = sp[32 + lane];
+                    q[0] = qa.x; q[1] = qa.y; q[2] = qa.z; q[3] = qa.w;
+                    q[4] = qb.x; q[5] = qb.y; q[6] = qb.z; q[7] = qb.w;
+                    if (c == kFF) {
+                        const uint32_t W2 = (wj << 5) * 0x10001u;      // residual >= w <=> slot >= w << 5
 #pragma unroll
-                    for (int k = 7; k >= 0; --k) {
-                        const uint32_t r0 = kd_slot(q0, k) >> 5, r1 = kd_slot(q1, k) >> 5;
-                        const bool m0 = c == kFF ? r0 >= wj : r0 == want;
-                        const bool m1 = c == kFF ? r1 >= wj : r1 == want;
-                        f0 = m0 ? k : f0;
-                        f1 = m1 ? k : f1;
+                        for (int k = 0; k < 8; ++k) mk[k] = __vcmpgeu2(q[k], W2);
+                    } else {
+                        const uint32_t R2 = (want << 5) * 0x10001u;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) mk[k] = __vcmpeq2(q[k] & 0xFFE0FFE0u, R2);
                     }
+                    const uint32_t a0 = __byte_perm(mk[0], mk[1], 0x7531), a1 = __byte_perm(mk[2], mk[3], 0x7531);
+                    const uint32_t b0 = __byte_perm(mk[4], mk[5], 0x7531), b1 = __byte_perm(mk[6], mk[7], 0x7531);
+                    const int f0 = a0 ? (__ffs(a0) - 1) >> 3 : a1 ? 4 + ((__ffs(a1) - 1) >> 3) : 8;
+                    const int f1 = b0 ? (__ffs(b0) - 1) >> 3 : b1 ? 4 + ((__ffs(b1) - 1) >> 3) : 8;
                     const unsigned h0 = __ballot_sync(kFull, f0 < 8);
-                    uint32_t idx, sv;
+                    uint32_t idx;
                     if (h0) {
                         own = static_cast<uint32_t>(__ffs(h0) - 1);
-                        const int fo = __shfl_sync(kFull, f0, static_cast<int>(own));
-                        idx = 8u * own + static_cast<uint32_t>(fo);
-                        ok = static_cast<uint32_t>(fo);
+                        ok = static_cast<uint32_t>(__shfl_sync(kFull, f0, static_cast<int>(own)));
+                        idx = 8u * own + ok;
                     } else {
                         const unsigned h1 = __ballot_sync(kFull, f1 < 8);
                         own = static_cast<uint32_t>(__ffs(h1) - 1);
-                        const int fo = __shfl_sync(kFull, f1, static_cast<int>(own));
-                        idx = 256u + 8u * own + static_cast<uint32_t>(fo);
-                        ok = 8u + static_cast<uint32_t>(fo);
+                        const uint32_t fo = static_cast<uint32_t>(__shfl_sync(kFull, f1, static_cast<int>(own)));
+                        idx = 256u + 8u * own + fo;
+                        ok = 8u + fo;
                     }
-                    const uint32_t mine = ok < 8u ? kd_slot(q0, static_cast<int>(ok)) : kd_slot(q1, static_cast<int>(ok - 8u));
-                    sv = __shfl_sync(kFull, mine, static_cast<int>(own));
+                    // slot `ok` of every lane (ok is uniform), the owner's broadcast
+                    const uint32_t o2 = ok >> 1;      // a select tree keeps q in registers
+                    const uint32_t wlo = (o2 & 2u) ? ((o2 & 1u) ? q[3] : q[2]) : ((o2 & 1u) ? q[1] : q[0]);
+                    const uint32_t whi = (o2 & 2u) ? ((o2 & 1u) ? q[7] : q[6]) : ((o2 & 1u) ? q[5] : q[4]);
+                    const uint32_t wsel = (o2 & 4u) ? whi : wlo;
+                    const uint32_t sv = __shfl_sync(kFull, (ok & 1u) ? (wsel >> 16) : (wsel & 0xFFFFu),
+                                                    static_cast<int>(own));
                     b = static_cast<uint32_t>(S) * 512u + idx;
                     r_old = sv >> 5;
                     ty = sv & 31u;
@@ -303,14 +311,18 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 if (W::kSeg) {
                     uint32_t nm;
                     if (hit) {
-                        uint32_t top = 0;
+                        // halfword maxima of this lane's words, the chosen slot
+                        // holding its new value; the residual is the slot >> 5
+                        const uint32_t nsv = (r_new << 5) | ty;
+                        uint32_t mx = 0u;
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            uint32_t r = (k < 8 ? kd_slot(q0, k) : kd_slot(q1, k - 8)) >> 5;
-                            r = (lane == own && static_cast<uint32_t>(k) == ok) ? r_new : r;
-                            top = max(top, r);
+                        for (int k = 0; k < 8; ++k) {
+                            uint32_t wv = q[k];
+                            if (lane == own && (ok >> 1) == static_cast<uint32_t>(k))
+                                wv = (ok & 1u) ? ((wv & 0xFFFFu) | (nsv << 16)) : ((wv & 0xFFFF0000u) | nsv);
+                            mx = __vmaxu2(mx, wv);
                         }
-                        nm = __reduce_max_sync(kFull, top);
+                        nm = __reduce_max_sync(kFull, max(mx & 0xFFFFu, mx >> 16) >> 5);
                     } else {
                         nm = max(static_cast<uint32_t>(K.segmax[Sb]), r_new);
                     }
@@ -326,29 +338,42 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 }
                 if (W::kIdx) {
                     if (hit) {
-                        // does segment S still hold a bin of residual r_old?
-                        uint32_t cntl = 0;
+                        // does segment S still hold a bin of residual r_old?  BF and
+                        // WF items matched exactly r_old above (16 mask bits a slot)
+                        uint32_t cntl = 0u;
+                        if (c != kFF) {
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            const uint32_t r = (k < 8 ? kd_slot(q0, k) : kd_slot(q1, k - 8)) >> 5;
-                            cntl += (r == r_old && !(lane == own && static_cast<uint32_t>(k) == ok)) ? 1u : 0u;
+                            for (int k = 0; k < 8; ++k) cntl += __popc(mk[k]);
+                        } else {
+                            const uint32_t R2 = (r_old << 5) * 0x10001u;
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) cntl += __popc(__vcmpeq2(q[k] & 0xFFE0FFE0u, R2));
                         }
-                        const uint32_t cnt = __reduce_add_sync(kFull, cntl);
-                        if (cnt == 0u) {
+                        const uint32_t others = (__reduce_add_sync(kFull, cntl) >> 4) - 1u;   // the chosen one left
+                        if (others == 0u) {
                             if (lane == 0) K.pres[r_old * 32u + (Sb >> 5)] &= ~(1u << (Sb & 31));
                             __syncwarp();
                             const bool any = __any_sync(kFull, K.pres[r_old * 32u + lane] != 0u);
                             if (!any && lane == 0) K.gp[r_old >> 5] &= ~(1u << (r_old & 31));
                         }
+                        __syncwarp();
                     }
-                    K.pres_set(r_new, Sb);
-                    if (fire) K.pres_set(Bt, Sf);
+                    // r_new's bits (lanes 0, 1) and the divided-off bin's (lanes 2, 3) at once
+                    if (lane < 4u) {
+                        const uint32_t r = lane < 2u ? r_new : (fire ? Bt : 0u);
+                        const uint32_t Sx = lane < 2u ? Sb : Sf;
+                        if (r > 0u) {
+                            if (lane & 1u) atomicOr(&K.gp[r >> 5], 1u << (r & 31));
+                            else atomicOr(&K.pres[r * 32u + (Sx >> 5)], 1u << (Sx & 31));
+                        }
+                    }
                 }
                 __syncwarp();
                 L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
                 bout = lane == static_cast<uint32_t>(jj) ? b : bout;
             }
             if (lane < static_cast<uint32_t>(cnt)) raw[j0 + lane] = static_cast<int32_t>(bout);
+            fit_tests += fit_blk;
             wcur = wnext;
             ccur = cnext;
         }
