@@ -699,7 +699,7 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
         // whose presence rows take 128 KB of CTA 0; else B_1 <= 2047)
         KDShape& kd = lp.kd;
         kd.pres = bfi;
-        kd.max_B1 = kd.pres ? 1023 : kKDMaxB1;
+        kd.max_B1 = kd.pres ? kKDMaxB1Idx : kKDMaxB1;
         kd.smem = smax;
         kd.segs1 = kd.smem / kKDSegBytes;
         kd.segs0 = (kd.smem - kd_bins_offset(kd.max_B1, kd.pres)) / kKDSegBytes;

@@ -8,29 +8,34 @@
 // fits, the Rule 5 division when a bin's load first reaches half its
 // capacity); the flat scan's answer is found exactly through summaries:
 //
-//   slot      16 bits per bin, (residual << 5) | type (B_1 <= 2047, n <= 32);
-//             the bin's creation index is its position.  Bins 0.. live in
-//             CTA 0's shared memory, the next ones in CTA 1's (read and
-//             written through distributed shared memory), the rest in a
-//             global-memory overflow area; a system past 2^19 bins is handed
-//             to the global-memory kernel.
-//   segment   512 bins (1 KB: two 16-byte words per lane).
-//   segmax    largest residual of each segment, tilemax of each 32 segments
-//             (FF and WF items): FF takes the first tile, then the first
-//             segment, whose maximum is >= w; WF the first whose maximum is
-//             the largest of all.
-//   gp, pres  (BF items) bit r of gp: some bin has residual r; row r of pres:
-//             one bit per segment holding a bin of residual r.  BF takes
-//             r* = the least residual >= w present, then the first segment in
-//             row r*: no bin anywhere has a residual in [w, r*), so the first
-//             bin of residual r* there is the flat scan's answer.
+//   slot       16 bits per bin, (residual << 5) | type (B_1 <= 2047, n <= 32);
+//              the bin's creation index is its position.  Bins 0.. live in
+//              CTA 0's shared memory, the next ones in CTA 1's (read and
+//              written through distributed shared memory), the rest in a
+//              global-memory overflow area; a system past 2^19 bins goes to
+//              the global-memory kernel from the start.
+//   segment    512 bins (1 KB), made of four 128-bin sub-segments (8 bytes,
+//              four slots, per lane).
+//   maxima     (FF and WF items) the largest residual of every sub-segment
+//              in shared memory, of every tile of 32 sub-segments in
+//              registers (tile l + 32q in lane l).  FF: one warp minimum over
+//              (tile, maximum) keys of the tiles whose maximum is >= w, one
+//              over the tile's sub-segments; WF: one warp maximum over
+//              (maximum, -tile) keys, one minimum over the tile's
+//              sub-segments holding that maximum.
+//   presence   (BF items, B_1 <= 1023) the residuals present, one 32-bit word
+//              per lane in registers; row r in shared memory: one bit per
+//              segment holding a bin of residual r.  r* = the least present
+//              residual >= w (one warp minimum), then the first segment in row
+//              r* (one more): no bin anywhere has a residual in [w, r*), so
+//              the first bin of residual r* there is the flat scan's answer.
 //
-// Within the chosen segment each lane reads its 16 slots; the first match
-// (FF: residual >= w; BF, WF: residual = the one sought) is one ballot per
-// half.  Updates (the chosen slot, a divided-off bin, the summaries) are
-// made by the one warp of CTA 0, ordered by __syncwarp before the next item.
-// CTA 1 only lends its shared memory: it waits at the cluster barrier until
-// CTA 0 has packed every system it takes.
+// In the chosen sub-segment (FF, WF) or segment (BF) each lane turns its
+// matching slots into (position, slot) keys, and one warp minimum names the
+// bin with its residual and type.  The chain per item is straight-line
+// arithmetic and warp reductions; the stores of an item are ordered before
+// the next item's reads by __syncwarp.  CTA 1's warp only lends its shared
+// memory: it waits at the closing cluster barrier.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -41,56 +46,44 @@ namespace vsbpp {
 
 namespace cg = cooperative_groups;
 
-template <int CRIT>
-struct KDWarp {
-    static constexpr bool kSeg = CRIT != kBF;                    // FF or WF items occur
-    static constexpr bool kIdx = CRIT == kBF || CRIT == kRandom;  // BF items occur
-
-    uint32_t lane;
-    uint16_t* segmax;
-    uint16_t* tilemax;
-    uint32_t* Bs;
-    uint32_t* gp;
-    uint32_t* pres;
-    unsigned char* bins0;    // CTA 0's bins
-    unsigned char* bins1;    // CTA 1's bins (distributed shared memory)
+struct KDMem {
+    unsigned char* bins0;    // CTA 0's segments
+    unsigned char* bins1;    // CTA 1's segments (distributed shared memory)
     unsigned char* over;     // global-memory overflow of this cluster
     uint32_t segs0, segs1;
 
-    __device__ __forceinline__ uint4* seg_ptr(uint32_t S) const {
-        if (S < segs0) return reinterpret_cast<uint4*>(bins0 + static_cast<size_t>(S) * kKDSegBytes);
+    __device__ __forceinline__ unsigned char* seg(uint32_t S) const {
+        if (S < segs0) return bins0 + static_cast<size_t>(S) * kKDSegBytes;
         S -= segs0;
-        if (S < segs1) return reinterpret_cast<uint4*>(bins1 + static_cast<size_t>(S) * kKDSegBytes);
-        S -= segs1;
-        return reinterpret_cast<uint4*>(over + static_cast<size_t>(S) * kKDSegBytes);
+        if (S < segs1) return bins1 + static_cast<size_t>(S) * kKDSegBytes;
+        return over + static_cast<size_t>(S - segs1) * kKDSegBytes;
     }
-    __device__ __forceinline__ uint16_t* slot_ptr(uint32_t b) const {
-        return reinterpret_cast<uint16_t*>(seg_ptr(b >> 9)) + (b & 511u);
+    __device__ __forceinline__ uint16_t* slot(uint32_t b) const {
+        return reinterpret_cast<uint16_t*>(seg(b >> 9)) + (b & 511u);
     }
-
-    // A segment reads as empty (residual 0 fits nothing) until its bins exist.
-    __device__ __forceinline__ void zero_seg(uint32_t S) const {
-        uint4* p = seg_ptr(S);
-        p[lane] = make_uint4(0u, 0u, 0u, 0u);
-        p[32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+    // the lane's four slots of sub-segment G
+    __device__ __forceinline__ uint2 sub(uint32_t G, uint32_t lane) const {
+        return reinterpret_cast<const uint2*>(seg(G >> 2) + (G & 3u) * 256u)[lane];
     }
-
-    __device__ __forceinline__ void refresh_tile(uint32_t T) const {
-        const uint32_t v = segmax[T * 32 + lane];
-        const uint32_t mx = __reduce_max_sync(kFull, v);
-        if (lane == 0) tilemax[T] = static_cast<uint16_t>(mx);
-    }
-
-    __device__ __forceinline__ void pres_set(uint32_t r, uint32_t S) const {
-        if (lane == 0 && r > 0u) {
-            pres[r * 32 + (S >> 5)] |= 1u << (S & 31);
-            gp[r >> 5] |= 1u << (r & 31);
-        }
+    // a segment reads as empty (residual 0 fits nothing) until its bins exist
+    __device__ __forceinline__ void zero(uint32_t S, uint32_t lane) const {
+        uint4* q = reinterpret_cast<uint4*>(seg(S));
+        q[lane] = make_uint4(0u, 0u, 0u, 0u);
+        q[32 + lane] = make_uint4(0u, 0u, 0u, 0u);
     }
 };
 
+// slot c (0..3) of a lane's 8 bytes
+__device__ __forceinline__ uint32_t kd_half(uint2 v, int c) {
+    const uint32_t x = c < 2 ? v.x : v.y;
+    return (c & 1) ? (x >> 16) : (x & 0xFFFFu);
+}
+
 template <int CRIT>
 __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
+    constexpr bool kSeg = CRIT != kBF;                    // FF or WF items occur
+    constexpr bool kIdx = CRIT == kBF || CRIT == kRandom;  // BF items occur
+    constexpr uint32_t kNo = 0xFFFFFFFFu;
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
     cluster.sync();                                   // both CTAs are running
@@ -98,21 +91,17 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
         cluster.sync();                               // CTA 1 lends its memory until CTA 0 is done
         return;
     }
-    using W = KDWarp<CRIT>;
-    W K;
-    K.lane = threadIdx.x & 31u;
-    const uint32_t lane = K.lane;
-    K.segmax = reinterpret_cast<uint16_t*>(smem + kKDOffSegmax);
-    K.tilemax = reinterpret_cast<uint16_t*>(smem + kKDOffTilemax);
-    K.Bs = reinterpret_cast<uint32_t*>(smem + kKDOffBs);
-    K.gp = reinterpret_cast<uint32_t*>(smem + kKDOffGp);
-    K.pres = reinterpret_cast<uint32_t*>(smem + kKDOffPres);
-    K.bins0 = smem + kd_bins_offset(p.max_B1, p.pres);
-    K.bins1 = cluster.map_shared_rank(smem, 1);
+    const uint32_t lane = threadIdx.x & 31u;
+    uint16_t* submax = reinterpret_cast<uint16_t*>(smem + kKDOffSubmax);
+    uint32_t* Bs = reinterpret_cast<uint32_t*>(smem + kKDOffBs);
+    uint32_t* pres = reinterpret_cast<uint32_t*>(smem + kKDOffPres);
+    KDMem M;
+    M.bins0 = smem + kd_bins_offset(p.max_B1, p.pres);
+    M.bins1 = cluster.map_shared_rank(smem, 1);
     const uint32_t cid = blockIdx.x >> 1;
-    K.over = reinterpret_cast<unsigned char*>(p.over + static_cast<size_t>(cid) * static_cast<size_t>(p.over_bins));
-    K.segs0 = static_cast<uint32_t>(p.segs0);
-    K.segs1 = static_cast<uint32_t>(p.segs1);
+    M.over = reinterpret_cast<unsigned char*>(p.over + static_cast<size_t>(cid) * static_cast<size_t>(p.over_bins));
+    M.segs0 = static_cast<uint32_t>(p.segs0);
+    M.segs1 = static_cast<uint32_t>(p.segs1);
     int32_t* dense = p.dense + static_cast<size_t>(cid) * kKDMaxBins;
     const unsigned lt = (1u << lane) - 1u;
 
@@ -131,7 +120,7 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
         const int32_t* B = p.in.B_all + p.in.B_begin(i);
         const uint32_t Bl = lane < static_cast<uint32_t>(n) ? static_cast<uint32_t>(B[lane]) : 0u;
         const uint32_t B1 = __shfl_sync(kFull, Bl, 0);
-        if (B1 > static_cast<uint32_t>(W::kIdx ? p.max_B1 : kKDMaxB1)) {
+        if (B1 > static_cast<uint32_t>(kIdx ? p.max_B1 : kKDMaxB1)) {
             // residuals past the slot or presence layout: the global-memory kernel
             if (lane == 0) {
                 const unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long*>(p.spill_seg + 1), 1ull);
@@ -139,30 +128,33 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
             }
             continue;
         }
-        K.Bs[lane] = Bl;
-        for (uint32_t x = lane; x < static_cast<uint32_t>(kKDMaxSegs); x += 32) K.segmax[x] = 0;
-        K.tilemax[lane] = 0;
-        if (W::kIdx) {
-            K.gp[lane] = 0u;
-            K.gp[32 + lane] = 0u;
-            for (uint32_t x = lane; x < (B1 + 1u) * 32u; x += 32) K.pres[x] = 0u;
-        }
+        Bs[lane] = Bl;
+        uint32_t tm[4] = {0u, 0u, 0u, 0u};           // tile maxima: tile lane + 32 t
+        uint32_t gw = 0u;                            // residuals 32 lane .. 32 lane + 31 present
+        if (kSeg)
+            for (uint32_t x = lane; x < static_cast<uint32_t>(kKDMaxSubs / 2); x += 32)
+                reinterpret_cast<uint32_t*>(submax)[x] = 0u;
+        if (kIdx)
+            for (uint32_t x = lane; x < (B1 + 1u) * 32u; x += 32) pres[x] = 0u;
         __syncwarp();
         int32_t* raw = p.out.bin_of_item + wb;
 
         uint32_t L = 0;
-        uint32_t below = 0;                  // Remark 3: type-t bins below half, lane t
-        if (p.preopen) {                     // literal Rule 2: one empty bin per type, segment 0
-            K.zero_seg(0);
+        uint32_t below = 0;                          // Remark 3: type-t bins below half, lane t
+        if (p.preopen) {                             // literal Rule 2: one empty bin per type, sub-segment 0
+            M.zero(0, lane);
             __syncwarp();
-            if (lane < static_cast<uint32_t>(n)) *K.slot_ptr(lane) = static_cast<uint16_t>((Bl << 5) | lane);
-            if (W::kSeg && lane == 0) {
-                K.segmax[0] = static_cast<uint16_t>(B1);
-                K.tilemax[0] = static_cast<uint16_t>(B1);
+            if (lane < static_cast<uint32_t>(n)) *M.slot(lane) = static_cast<uint16_t>((Bl << 5) | lane);
+            if (kSeg) {
+                if (lane == 0) submax[0] = static_cast<uint16_t>(B1);
+                tm[0] = lane == 0 ? B1 : 0u;
             }
-            if (W::kIdx && lane < static_cast<uint32_t>(n)) {
-                atomicOr(&K.pres[Bl * 32], 1u);
-                atomicOr(&K.gp[Bl >> 5], 1u << (Bl & 31));
+            if (kIdx) {
+                if (lane < static_cast<uint32_t>(n)) atomicOr(&pres[Bl * 32u], 1u);
+                for (int t = 0; t < n; ++t) {
+                    const uint32_t r = __shfl_sync(kFull, Bl, t);
+                    gw |= (r >> 5) == lane ? 1u << (r & 31) : 0u;
+                }
             }
             below = lane < static_cast<uint32_t>(n) ? 1u : 0u;
             L = static_cast<uint32_t>(n);
@@ -188,105 +180,104 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
             const uint32_t wnext = jn < m ? static_cast<uint32_t>(__ldg(w + jn)) : 0u;
             const int cnext = pick_criterion(p.criterion, p.seed, static_cast<uint64_t>(jn));
             const int cnt = static_cast<int>(min(static_cast<int64_t>(32), m - j0));
-            uint32_t bout = 0, fit_blk = 0;       // fit tests of this block (< 2^24)
+            uint32_t bout = 0, fit_blk = 0;          // fit tests of this block (< 2^24)
             for (int jj = 0; jj < cnt; ++jj) {
                 const uint32_t wj = __shfl_sync(kFull, wcur, jj);
                 const int c = CRIT == kRandom ? __shfl_sync(kFull, ccur, jj) : CRIT;
                 fit_blk += L;
-                const uint32_t nseg = (L + 511u) >> 9;
-                const uint32_t ntile = (nseg + 31u) >> 5;
 
-                // 1. the segment holding the answer, and the residual sought
-                int S = -1;
-                uint32_t want = 0;
-                if (W::kSeg && c == kFF) {
-                    const unsigned bt = __ballot_sync(kFull, lane < ntile && K.tilemax[lane] >= wj);
-                    if (bt) {
-                        const uint32_t T = static_cast<uint32_t>(__ffs(bt) - 1);
-                        const uint32_t s = T * 32u + lane;
-                        const unsigned bs = __ballot_sync(kFull, s < nseg && K.segmax[s] >= wj);
-                        S = static_cast<int>(T * 32u) + __ffs(bs) - 1;
+                // 1. the chosen bin b and its slot (residual << 5 | type), or none
+                bool hit = false;
+                uint32_t b = 0, sl = 0;
+                uint2 q4 = make_uint2(0u, 0u);        // FF / WF: this lane's slots of sub-segment G
+                uint32_t q16[8];                      // BF: this lane's slots of segment S
+#pragma unroll
+                for (int k = 0; k < 8; ++k) q16[k] = 0u;
+                uint32_t rowv = 0u, mcnt = 0u;        // BF: word `lane` of row r*, matches of r* in S
+                if (kSeg && c == kFF) {
+                    uint32_t key = kNo;
+#pragma unroll
+                    for (int t = 3; t >= 0; --t)
+                        key = tm[t] >= wj ? ((lane + 32u * t) << 16) | tm[t] : key;
+                    key = __reduce_min_sync(kFull, key);
+                    hit = key != kNo;
+                    if (hit) {
+                        const uint32_t T = key >> 16;
+                        const uint32_t sv = submax[T * 32u + lane];
+                        const uint32_t G = T * 32u + __reduce_min_sync(kFull, sv >= wj ? lane : 32u);
+                        q4 = M.sub(G, lane);
+                        const uint32_t W5 = wj << 5;  // residual >= w  <=>  slot >= w << 5
+                        uint32_t k3 = kNo;
+#pragma unroll
+                        for (int cc = 3; cc >= 0; --cc) {
+                            const uint32_t s = kd_half(q4, cc);
+                            k3 = s >= W5 ? ((4u * lane + cc) << 16) | s : k3;
+                        }
+                        k3 = __reduce_min_sync(kFull, k3);
+                        b = G * 128u + (k3 >> 16);
+                        sl = k3 & 0xFFFFu;
                     }
-                } else if (W::kSeg && c == kWF) {
-                    const uint32_t tm = lane < ntile ? static_cast<uint32_t>(K.tilemax[lane]) : 0u;
-                    const uint32_t mx = __reduce_max_sync(kFull, tm);
-                    if (mx >= wj) {
-                        want = mx;
-                        const uint32_t T = static_cast<uint32_t>(__ffs(__ballot_sync(kFull, lane < ntile && tm == mx)) - 1);
-                        const uint32_t s = T * 32u + lane;
-                        const unsigned bs = __ballot_sync(kFull, s < nseg && K.segmax[s] == mx);
-                        S = static_cast<int>(T * 32u) + __ffs(bs) - 1;
+                } else if (kSeg && c == kWF) {
+                    uint32_t key = 0u;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) key = max(key, (tm[t] << 8) | (127u - (lane + 32u * t)));
+                    key = __reduce_max_sync(kFull, key);
+                    const uint32_t Mx = key >> 8;
+                    hit = Mx >= wj;
+                    if (hit) {
+                        const uint32_t T = 127u - (key & 255u);
+                        const uint32_t sv = submax[T * 32u + lane];
+                        const uint32_t G = T * 32u + __reduce_min_sync(kFull, sv == Mx ? lane : 32u);
+                        q4 = M.sub(G, lane);
+                        uint32_t k3 = kNo;
+#pragma unroll
+                        for (int cc = 3; cc >= 0; --cc) {
+                            const uint32_t s = kd_half(q4, cc);
+                            k3 = (s >> 5) == Mx ? ((4u * lane + cc) << 16) | s : k3;
+                        }
+                        k3 = __reduce_min_sync(kFull, k3);
+                        b = G * 128u + (k3 >> 16);
+                        sl = k3 & 0xFFFFu;
                     }
-                } else if (W::kIdx) {
-                    // the least residual >= w present: words lane and 32 + lane of gp
-                    const uint32_t wi = wj >> 5, lo = ~((1u << (wj & 31)) - 1u);
-                    uint32_t g0 = K.gp[lane], g1 = K.gp[32 + lane];
-                    g0 = lane < wi ? 0u : (lane == wi ? g0 & lo : g0);
-                    g1 = 32u + lane < wi ? 0u : (32u + lane == wi ? g1 & lo : g1);
-                    const unsigned b0 = __ballot_sync(kFull, g0 != 0u), b1 = __ballot_sync(kFull, g1 != 0u);
-                    if (b0 | b1) {
-                        const int src = b0 ? __ffs(b0) - 1 : __ffs(b1) - 1;
-                        const uint32_t word = __shfl_sync(kFull, b0 ? g0 : g1, src);
-                        want = static_cast<uint32_t>((b0 ? src : 32 + src) * 32 + __ffs(word) - 1);
-                        const uint32_t rv = K.pres[want * 32u + lane];
-                        const unsigned bv = __ballot_sync(kFull, rv != 0u);
-                        const int s2 = __ffs(bv) - 1;
-                        S = s2 * 32 + __ffs(__shfl_sync(kFull, rv, s2)) - 1;
+                } else if (kIdx) {
+                    const uint32_t wi = wj >> 5;
+                    const uint32_t mw = gw & (lane < wi ? 0u : lane == wi ? ~((1u << (wj & 31)) - 1u) : kNo);
+                    const uint32_t R = __reduce_min_sync(kFull, mw ? 32u * lane + static_cast<uint32_t>(__ffs(mw) - 1) : kNo);
+                    hit = R != kNo;
+                    if (hit) {
+                        rowv = pres[R * 32u + lane];
+                        const uint32_t S = __reduce_min_sync(
+                            kFull, rowv ? 32u * lane + static_cast<uint32_t>(__ffs(rowv) - 1) : kNo);
+                        const unsigned char* base = M.seg(S);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint2 v2 = reinterpret_cast<const uint2*>(base + 256 * k)[lane];
+                            q16[2 * k] = v2.x;
+                            q16[2 * k + 1] = v2.y;
+                        }
+                        const uint32_t R5 = R << 5;
+                        uint32_t k3 = kNo;
+#pragma unroll
+                        for (int k = 3; k >= 0; --k) {
+#pragma unroll
+                            for (int cc = 3; cc >= 0; --cc) {
+                                const uint32_t x = q16[2 * k + (cc >> 1)];
+                                const uint32_t s = (cc & 1) ? (x >> 16) : (x & 0xFFFFu);
+                                const bool hr = (s & 0xFFE0u) == R5;
+                                mcnt += hr ? 1u : 0u;
+                                k3 = hr ? ((128u * k + 4u * lane + cc) << 16) | s : k3;
+                            }
+                        }
+                        k3 = __reduce_min_sync(kFull, k3);
+                        b = S * 512u + (k3 >> 16);
+                        sl = k3 & 0xFFFFu;
                     }
                 }
-
-                // 2. the chosen bin in segment S (first match in slot order), or
-                //    a new bin.  Two slots per 32-bit word: halfword compares
-                //    give 0xFFFF per matching slot, one flag byte per slot
-                //    (byte permute) and __ffs give the first match of each half.
-                const bool hit = S >= 0;
-                uint32_t b, r_old, ty;
-                uint32_t q[8], mk[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) q[k] = mk[k] = 0u;
-                uint32_t own = 32u, ok = 16u;         // lane and slot (0..15) of the chosen bin
+                uint32_t r_old, ty;
                 if (hit) {
-                    const uint4* sp = K.seg_ptr(static_cast<uint32_t>(S));
-                    const uint4 qa = sp[lane], qb = sp[32 + lane];
-                    q[0] = qa.x; q[1] = qa.y; q[2] = qa.z; q[3] = qa.w;
-                    q[4] = qb.x; q[5] = qb.y; q[6] = qb.z; q[7] = qb.w;
-                    if (c == kFF) {
-                        const uint32_t W2 = (wj << 5) * 0x10001u;      // residual >= w <=> slot >= w << 5
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) mk[k] = __vcmpgeu2(q[k], W2);
-                    } else {
-                        const uint32_t R2 = (want << 5) * 0x10001u;
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) mk[k] = __vcmpeq2(q[k] & 0xFFE0FFE0u, R2);
-                    }
-                    const uint32_t a0 = __byte_perm(mk[0], mk[1], 0x7531), a1 = __byte_perm(mk[2], mk[3], 0x7531);
-                    const uint32_t b0 = __byte_perm(mk[4], mk[5], 0x7531), b1 = __byte_perm(mk[6], mk[7], 0x7531);
-                    const int f0 = a0 ? (__ffs(a0) - 1) >> 3 : a1 ? 4 + ((__ffs(a1) - 1) >> 3) : 8;
-                    const int f1 = b0 ? (__ffs(b0) - 1) >> 3 : b1 ? 4 + ((__ffs(b1) - 1) >> 3) : 8;
-                    const unsigned h0 = __ballot_sync(kFull, f0 < 8);
-                    uint32_t idx;
-                    if (h0) {
-                        own = static_cast<uint32_t>(__ffs(h0) - 1);
-                        ok = static_cast<uint32_t>(__shfl_sync(kFull, f0, static_cast<int>(own)));
-                        idx = 8u * own + ok;
-                    } else {
-                        const unsigned h1 = __ballot_sync(kFull, f1 < 8);
-                        own = static_cast<uint32_t>(__ffs(h1) - 1);
-                        const uint32_t fo = static_cast<uint32_t>(__shfl_sync(kFull, f1, static_cast<int>(own)));
-                        idx = 256u + 8u * own + fo;
-                        ok = 8u + fo;
-                    }
-                    // slot `ok` of every lane (ok is uniform), the owner's broadcast
-                    const uint32_t o2 = ok >> 1;      // a select tree keeps q in registers
-                    const uint32_t wlo = (o2 & 2u) ? ((o2 & 1u) ? q[3] : q[2]) : ((o2 & 1u) ? q[1] : q[0]);
-                    const uint32_t whi = (o2 & 2u) ? ((o2 & 1u) ? q[7] : q[6]) : ((o2 & 1u) ? q[5] : q[4]);
-                    const uint32_t wsel = (o2 & 4u) ? whi : wlo;
-                    const uint32_t sv = __shfl_sync(kFull, (ok & 1u) ? (wsel >> 16) : (wsel & 0xFFFFu),
-                                                    static_cast<int>(own));
-                    b = static_cast<uint32_t>(S) * 512u + idx;
-                    r_old = sv >> 5;
-                    ty = sv & 31u;
-                } else {
+                    r_old = sl >> 5;
+                    ty = sl & 31u;
+                } else {                              // nothing fits: smallest type holding w
                     ty = 31u - static_cast<uint32_t>(__clz(__ballot_sync(kFull, Bl >= wj)));
                     b = L;
                     r_old = __shfl_sync(kFull, Bl, static_cast<int>(ty));
@@ -297,75 +288,95 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 const bool fire = p.remark3 ? remark3_divide(below, Bl, !hit, Bt, cross) : cross;
                 const uint32_t Lf = hit ? L : L + 1u;
 
-                // 3. stores: new segments cleared first, then the slots
-                if (!hit && (b & 511u) == 0u) K.zero_seg(b >> 9);
-                if (fire && (Lf & 511u) == 0u) K.zero_seg(Lf >> 9);
+                // 2. stores: a segment a new bin opens is cleared first
+                if (!hit && (b & 511u) == 0u) M.zero(b >> 9, lane);
+                if (fire && (Lf & 511u) == 0u) M.zero(Lf >> 9, lane);
                 __syncwarp();
                 if (lane == 0) {
-                    *K.slot_ptr(b) = static_cast<uint16_t>((r_new << 5) | ty);
-                    if (fire) *K.slot_ptr(Lf) = static_cast<uint16_t>((Bt << 5) | ty);
+                    *M.slot(b) = static_cast<uint16_t>((r_new << 5) | ty);
+                    if (fire) *M.slot(Lf) = static_cast<uint16_t>((Bt << 5) | ty);
                 }
-                const uint32_t Sb = b >> 9, Sf = Lf >> 9;
+                __syncwarp();
 
-                // 4. summaries of the touched segments
-                if (W::kSeg) {
+                // 3. sub-segment and tile maxima (FF / WF items occur)
+                if (kSeg) {
+                    const uint32_t Gb = b >> 7, Gf = Lf >> 7;
+                    const uint32_t nsv = (r_new << 5) | ty;
                     uint32_t nm;
                     if (hit) {
-                        // halfword maxima of this lane's words, the chosen slot
-                        // holding its new value; the residual is the slot >> 5
-                        const uint32_t nsv = (r_new << 5) | ty;
+                        // the sub-segment's four slots a lane, the chosen one updated
+                        // (a BF item, under RANDOM, holds its segment in q16)
+                        const uint32_t pos = b & 127u, k = (b >> 7) & 3u;
+                        uint2 v2 = q4;
+                        if (c == kBF) {
+                            v2.x = k == 0u ? q16[0] : k == 1u ? q16[2] : k == 2u ? q16[4] : q16[6];
+                            v2.y = k == 0u ? q16[1] : k == 1u ? q16[3] : k == 2u ? q16[5] : q16[7];
+                        }
                         uint32_t mx = 0u;
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            uint32_t wv = q[k];
-                            if (lane == own && (ok >> 1) == static_cast<uint32_t>(k))
-                                wv = (ok & 1u) ? ((wv & 0xFFFFu) | (nsv << 16)) : ((wv & 0xFFFF0000u) | nsv);
-                            mx = __vmaxu2(mx, wv);
+                        for (int cc = 0; cc < 4; ++cc) {
+                            const uint32_t s = (lane == (pos >> 2) && (pos & 3u) == static_cast<uint32_t>(cc))
+                                                   ? nsv : kd_half(v2, cc);
+                            mx = max(mx, s >> 5);
                         }
-                        nm = __reduce_max_sync(kFull, max(mx & 0xFFFFu, mx >> 16) >> 5);
+                        nm = __reduce_max_sync(kFull, mx);
                     } else {
-                        nm = max(static_cast<uint32_t>(K.segmax[Sb]), r_new);
+                        nm = max(static_cast<uint32_t>(submax[Gb]), r_new);
                     }
-                    if (fire && Sf == Sb) nm = max(nm, Bt);
-                    __syncwarp();
+                    if (fire && Gf == Gb) nm = max(nm, Bt);
                     if (lane == 0) {
-                        K.segmax[Sb] = static_cast<uint16_t>(nm);
-                        if (fire && Sf != Sb) K.segmax[Sf] = static_cast<uint16_t>(max(static_cast<uint32_t>(K.segmax[Sf]), Bt));
+                        submax[Gb] = static_cast<uint16_t>(nm);
+                        if (fire && Gf != Gb) submax[Gf] = static_cast<uint16_t>(max(static_cast<uint32_t>(submax[Gf]), Bt));
                     }
                     __syncwarp();
-                    K.refresh_tile(Sb >> 5);
-                    if (fire && (Sf >> 5) != (Sb >> 5)) K.refresh_tile(Sf >> 5);
+                    // tile maxima from the touched tiles' rows
+                    const uint32_t Tb = Gb >> 5, Tf = Gf >> 5;
+                    const bool two = fire && Tf != Tb;
+                    const uint32_t tb = __reduce_max_sync(kFull, static_cast<uint32_t>(submax[Tb * 32u + lane]));
+                    const uint32_t tf = two ? __reduce_max_sync(kFull, static_cast<uint32_t>(submax[Tf * 32u + lane])) : 0u;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const uint32_t tile = lane + 32u * t;
+                        tm[t] = tile == Tb ? tb : tm[t];
+                        tm[t] = (two && tile == Tf) ? tf : tm[t];
+                    }
                 }
-                if (W::kIdx) {
+
+                // 4. residual presence (BF items occur)
+                if (kIdx) {
+                    const uint32_t Sb = b >> 9, Sf = Lf >> 9;
                     if (hit) {
-                        // does segment S still hold a bin of residual r_old?  BF and
-                        // WF items matched exactly r_old above (16 mask bits a slot)
-                        uint32_t cntl = 0u;
-                        if (c != kFF) {
+                        // does segment Sb still hold a bin of residual r_old?  A BF
+                        // item counted r* = r_old in the scan (the chosen bin
+                        // included); other items count after the store
+                        uint32_t cl = mcnt;
+                        if (c != kBF) {
+                            const unsigned char* base = M.seg(Sb);
+                            cl = 0u;
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) cntl += __popc(mk[k]);
-                        } else {
-                            const uint32_t R2 = (r_old << 5) * 0x10001u;
+                            for (int k = 0; k < 4; ++k) {
+                                const uint2 v2 = reinterpret_cast<const uint2*>(base + 256 * k)[lane];
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) cntl += __popc(__vcmpeq2(q[k] & 0xFFE0FFE0u, R2));
+                                for (int cc = 0; cc < 4; ++cc) cl += (kd_half(v2, cc) >> 5) == r_old ? 1u : 0u;
+                            }
+                            rowv = pres[r_old * 32u + lane];
                         }
-                        const uint32_t others = (__reduce_add_sync(kFull, cntl) >> 4) - 1u;   // the chosen one left
+                        const uint32_t others = __reduce_add_sync(kFull, cl) - (c == kBF ? 1u : 0u);
                         if (others == 0u) {
-                            if (lane == 0) K.pres[r_old * 32u + (Sb >> 5)] &= ~(1u << (Sb & 31));
-                            __syncwarp();
-                            const bool any = __any_sync(kFull, K.pres[r_old * 32u + lane] != 0u);
-                            if (!any && lane == 0) K.gp[r_old >> 5] &= ~(1u << (r_old & 31));
+                            const uint32_t nw = lane == (Sb >> 5) ? rowv & ~(1u << (Sb & 31)) : rowv;
+                            if (lane == (Sb >> 5)) pres[r_old * 32u + lane] = nw;
+                            const bool any = __any_sync(kFull, nw != 0u);
+                            gw &= (!any && lane == (r_old >> 5)) ? ~(1u << (r_old & 31)) : kNo;
                         }
                         __syncwarp();
                     }
-                    // r_new's bits (lanes 0, 1) and the divided-off bin's (lanes 2, 3) at once
-                    if (lane < 4u) {
-                        const uint32_t r = lane < 2u ? r_new : (fire ? Bt : 0u);
-                        const uint32_t Sx = lane < 2u ? Sb : Sf;
-                        if (r > 0u) {
-                            if (lane & 1u) atomicOr(&K.gp[r >> 5], 1u << (r & 31));
-                            else atomicOr(&K.pres[r * 32u + (Sx >> 5)], 1u << (Sx & 31));
-                        }
+                    if (r_new > 0u) {
+                        if (lane == (Sb >> 5)) atomicOr(&pres[r_new * 32u + lane], 1u << (Sb & 31));
+                        gw |= lane == (r_new >> 5) ? 1u << (r_new & 31) : 0u;
+                    }
+                    if (fire) {
+                        if (lane == (Sf >> 5)) atomicOr(&pres[Bt * 32u + lane], 1u << (Sf & 31));
+                        gw |= lane == (Bt >> 5) ? 1u << (Bt & 31) : 0u;
                     }
                 }
                 __syncwarp();
@@ -388,15 +399,15 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
             bool used = false;
             uint32_t t = 0;
             if (x < L) {
-                const uint32_t sv = *K.slot_ptr(x);
+                const uint32_t sv = *M.slot(x);
                 t = sv & 31u;
-                used = (sv >> 5) < K.Bs[t];
+                used = (sv >> 5) < Bs[t];
             }
             const unsigned bal = __ballot_sync(kFull, used);
             const uint32_t d = dbase + __popc(bal & lt);
             if (used) {
                 p.out.bin_type[wb + d] = static_cast<int32_t>(t);
-                tot += K.Bs[t];
+                tot += Bs[t];
             }
             if (x < L) dense[x] = used ? static_cast<int32_t>(d) : -1;
             dbase += __popc(bal);

@@ -7,13 +7,15 @@
 
 namespace vsbpp {
 
-constexpr int kKDSeg = 512;                         // bins per segment (16-bit slots: 1 KB)
+constexpr int kKDSeg = 512;                         // bins per segment (16-bit slots: 1 KB), BF presence unit
 constexpr int kKDSegBytes = kKDSeg * 2;
+constexpr int kKDSub = 128;                         // bins per sub-segment (8 bytes a lane), FF / WF scan unit
 constexpr int kKDMaxSegs = 1024;                    // 2^19 bins per membrane system
 constexpr int kKDMaxBins = kKDMaxSegs * kKDSeg;
-constexpr int kKDTiles = kKDMaxSegs / 32;           // 32 segments per tile
+constexpr int kKDMaxSubs = kKDMaxBins / kKDSub;     // 4096
+constexpr int kKDTiles = kKDMaxSubs / 32;           // 128 tiles of 32 sub-segments (4 per lane)
 constexpr int kKDMaxB1 = 2047;                      // 11-bit residuals
-constexpr int kKDGpWords = (kKDMaxB1 + 1) / 32;     // 64
+constexpr int kKDMaxB1Idx = 1023;                   // with BF items: one present-residual word per lane
 
 struct KDParams {
     BatchView in;
@@ -38,13 +40,11 @@ struct KDParams {
     unsigned long long* counters;
 };
 
-// CTA 0's layout: segment maxima, tile maxima, capacities, residual-present
-// bitmap, per-residual segment bitmaps (BF), then its bins.
-constexpr int kKDOffSegmax = 0;
-constexpr int kKDOffTilemax = kKDOffSegmax + 2 * kKDMaxSegs;
-constexpr int kKDOffBs = kKDOffTilemax + 2 * kKDTiles;
-constexpr int kKDOffGp = kKDOffBs + 4 * kMaxTypes;
-constexpr int kKDOffPres = kKDOffGp + 4 * kKDGpWords;
+// CTA 0's layout: sub-segment maxima (FF / WF items), capacities,
+// per-residual segment bitmaps (BF items), then its bins.
+constexpr int kKDOffSubmax = 0;
+constexpr int kKDOffBs = kKDOffSubmax + 2 * kKDMaxSubs;
+constexpr int kKDOffPres = kKDOffBs + 4 * kMaxTypes;
 
 __host__ __device__ inline int kd_pres_bytes(int max_B1, int pres) {
     return pres ? (max_B1 + 1) * 32 * 4 : 0;
