@@ -375,7 +375,8 @@ def serving_run(native, I, rate, n_req):
 
 
 # ------------------------------------------------------------------ oracle
-KERNEL_OF = {1: "h1w_pack_kernel (first heuristic, one warp per membrane system)",
+KERNEL_OF = {1: "h1w_pack_kernel (first heuristic, one warp per membrane system; two launches side by "
+                "side: systems above and up to small_m items, timed from fork to join)",
              2: "h2_pack_kernel_reg (second heuristic, one warp per sublist)"}
 KERNEL_SOURCES = {1: ["paper_1602_08735_gb300/csrc/h1w_kernel.cuh", "paper_1602_08735_gb300/csrc/h1_kernel.cuh",
                       "paper_1602_08735_gb300/csrc/device_common.cuh"],

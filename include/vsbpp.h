@@ -331,9 +331,10 @@ int vsbpp_counters_read(vsbpp_counters *out, int reset);
 /*
  * Kernel timing (measurement).  While enabled, every vsbpp_pack_batch call
  * made on a stream that is not capturing records a CUDA event pair on that
- * stream around its main packing kernel: the first-heuristic kernel of the
- * instances held in shared memory (the large class), or the second-
- * heuristic kernel.  Up to 256 pairs are kept (the oldest are overwritten).
+ * stream around its main packing phase: the first-heuristic kernels of the
+ * instances held in shared memory (both size classes, from the fork of the
+ * second stream to the join), the bounded-space kernel, or the
+ * second-heuristic kernel.  Up to 256 pairs are kept (the oldest are overwritten).
  * vsbpp_kernel_timing_read waits for the recorded pairs, writes up to `max`
  * durations in milliseconds to ms[] (oldest first), their number to *count,
  * and forgets them.  Enabling or disabling also forgets them.
@@ -367,16 +368,20 @@ int vsbpp_plan_destroy(vsbpp_plan *plan);
  * Launch configuration and autotuner.
  *
  * The batched first-heuristic kernel runs thread groups of `warps` warps per
- * instance; instances with m <= small_m go to single-warp groups.  The
- * autotuner times candidate configurations on the caller's batch (device CSR
- * arrays as in vsbpp_pack_batch; the outputs are scratch it may overwrite) and
- * installs the fastest for the batch's heuristic; vsbpp_tune_save/load keep
- * the table in a small JSON file.
+ * instance; instances with m <= small_m go to single-warp groups whose bin
+ * slots are sized for small_m, launched on a second stream beside the larger
+ * instances' launch (their blocks take the shared memory the larger ones'
+ * warps give back as their queue runs dry).  The autotuner times candidate
+ * configurations on the caller's batch (device CSR arrays as in
+ * vsbpp_pack_batch; the outputs are scratch it may overwrite) and installs
+ * the fastest for the batch's heuristic; vsbpp_tune_save/load keep the table
+ * in a small JSON file.
  */
 typedef struct {
     int32_t large_warps;    /* warps per group for instances with m > small_m (1..32, power of 2) */
     int32_t small_m;        /* instances at or below this size use one warp each (>= 0)           */
-    int32_t small_warps_per_block; /* warps per thread block in the single-warp kernel (1..32)     */
+    int32_t small_warps_per_block; /* warps per thread block in the single-warp kernel (1, 2, 4,
+                               8 or 16)                                                      */
     int32_t chunk;          /* items staged in shared memory per step (multiple of 32)            */
     int32_t slot_pct;       /* bin slots per membrane system in the shared-memory kernels, as a
                                percentage of its items (+64); 200 = the worst case (every item

@@ -100,11 +100,12 @@ DeviceInfo device_info() {
 }
 
 // Defaults: the autotuner's choice on the 4096-instance benchmark batch
-// (one warp per membrane system).
+// (one warp per membrane system; systems of up to 6000 items in the smaller
+// single-warp shape, beside the large class on a second stream).
 vsbpp_config g_cfg = {
     /*large_warps=*/1,
-    /*small_m=*/0,
-    /*small_warps_per_block=*/16,
+    /*small_m=*/6000,
+    /*small_warps_per_block=*/1,
     /*chunk=*/512,
     /*slot_pct=*/80,
     /*h2_blocks_per_sm=*/0,
@@ -845,6 +846,9 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
         // the large one on a second stream: its blocks take the shared memory
         // the large class's warps give back as its queue runs dry
         const bool fork = !plain && lp.cfg.small_m > 0 && sc.side;
+        // kernel timing brackets the whole packing phase: both classes, from
+        // the fork to the join
+        const bool timed = !plain && timing_begin(st);
         if (fork) {
             VS_TRY(cudaEventRecord(sc.ev_fork, st));
             VS_TRY(cudaStreamWaitEvent(sc.side, sc.ev_fork, 0));
@@ -879,14 +883,13 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
                 p.spill_seg = sc.spill_seg();
             }
             if (c == kClassLarge) set_h16(p, lp, sc);
-            const bool timed = c == kClassLarge && timing_begin(cs);
             VS_TRY(launch_shape(sh, c == kClassWide, p, sh.groups, sh.grid, cs));
-            timing_end(timed, cs);
         }
         if (fork) {
             VS_TRY(cudaEventRecord(sc.ev_join, sc.side));
             VS_TRY(cudaStreamWaitEvent(st, sc.ev_join, 0));
         }
+        timing_end(timed, st);
         {
             // systems that outgrew their slots, repacked from the start at full
             // size; a system that outgrows that too is listed for global memory
@@ -1564,29 +1567,32 @@ int vsbpp_autotune(int64_t N, const int32_t* w_all, const int64_t* w_off, const 
         const vsbpp_params prm = defaults(p);
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         std::lock_guard<std::recursive_mutex> lk(*scratch_for(st).mu);
-        // Coordinate descent over the four knobs, starting from the current table.
+        // Coordinate descent over the knobs, starting from the current table.
         vsbpp_config cur = snapshot().cfg;
         double cur_ms = 0;
         if ((rc = time_config(cur, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb, tot, status,
                               st, 3, &cur_ms)))
             return rc;
         const int warps[] = {1, 2, 4, 8, 16, 32};
-        const int smalls[] = {0, 128, 512, 1024, 2048, 4096, 8192, 16384};
-        const int wpb[] = {2, 4, 8, 16};
+        // the single-warp class's size bound and block size are searched as
+        // pairs: its blocks only fit beside the large class's warps when small
+        const int smalls[] = {0, 1000, 2000, 4000, 5000, 6000, 7000, 8000};
+        const int wpb[] = {1, 2, 4, 16};
         const int chunks[] = {256, 512, 1024, 2048};
         const int pcts[] = {60, 70, 80, 100, 130, 200};
         for (int pass = 0; pass < 2; ++pass) {
-            for (int knob = 0; knob < 5; ++knob) {
-                const int* vals = knob == 0 ? warps : knob == 1 ? smalls : knob == 2 ? wpb
-                                  : knob == 3 ? chunks : pcts;
-                const int nv = knob == 0 ? 6 : knob == 1 ? 8 : knob == 4 ? 6 : 4;
+            for (int knob = 0; knob < 4; ++knob) {
+                const int* vals = knob == 0 ? warps : knob == 2 ? chunks : pcts;
+                const int nv = knob == 0 ? 6 : knob == 1 ? 8 * 4 : knob == 2 ? 4 : 6;
                 for (int v = 0; v < nv; ++v) {
                     vsbpp_config c = cur;
                     if (knob == 0) c.large_warps = vals[v];
-                    if (knob == 1) c.small_m = vals[v];
-                    if (knob == 2) c.small_warps_per_block = vals[v];
-                    if (knob == 3) c.chunk = vals[v];
-                    if (knob == 4) c.slot_pct = vals[v];
+                    if (knob == 1) {
+                        c.small_m = smalls[v / 4];
+                        c.small_warps_per_block = wpb[v % 4];
+                    }
+                    if (knob == 2) c.chunk = vals[v];
+                    if (knob == 3) c.slot_pct = vals[v];
                     if (std::memcmp(&c, &cur, sizeof(c)) == 0) continue;
                     double ms = 0;
                     const int r2 = time_config(c, N, w_all, w_off, B_all, B_off, max_m, prm, boi, bt, nb,
