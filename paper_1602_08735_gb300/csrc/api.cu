@@ -784,8 +784,10 @@ void set_h16(H1Params& p, const LaunchPlan& lp, Scratch& sc) {
 }
 
 // Enqueue the whole pipeline on `st`.  plain = one launch per instance.
+// split: the single-warp class may run on the second stream (batched device
+// calls and plans; see the caller).
 int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutView& out0,
-                 const vsbpp_params& prm, bool plain, cudaStream_t st) {
+                 const vsbpp_params& prm, bool plain, cudaStream_t st, bool split_ok) {
     if (in.N == 0) return VSBPP_OK;
     OutView out = out0;
     PrepParams pp;
@@ -798,9 +800,12 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
     pp.narrow_max_B = SlotTraits<uint32_t>::kMaxCap;
     const int prep_grid = static_cast<int>(std::min<int64_t>(lp.prep_grid, (in.N + 7) / 8));
 
+    // the single-warp class runs beside the large one on the second stream,
+    // or not at all (every system in the large class)
+    const bool split = !plain && split_ok && lp.cfg.small_m > 0 && sc.side;
     if (!lp.mode.compose) {
         pp.classify = 1;
-        pp.small_m = plain ? 0 : lp.cfg.small_m;      // plain path: no single-warp class
+        pp.small_m = split ? lp.cfg.small_m : 0;
         pp.narrow_cap = lp.large.cap_m;
         pp.narrow_bins = lp.large.warp_kernel ? (int64_t(1) << 40) : 65536;   // one-warp shapes spill instead
         pp.narrow_cap16 = lp.large16_cap_m;
@@ -845,7 +850,7 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
         // the single-warp class (smaller slots, more warps per SM) runs beside
         // the large one on a second stream: its blocks take the shared memory
         // the large class's warps give back as its queue runs dry
-        const bool fork = !plain && lp.cfg.small_m > 0 && sc.side;
+        const bool fork = split;
         // kernel timing brackets the whole packing phase: both classes, from
         // the fork to the join
         const bool timed = !plain && timing_begin(st);
@@ -1047,9 +1052,15 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
 // instances' weights are sorted into scratch (caller-order validation kept
 // aside), the sorted copy is packed, and each sorted position's bin id goes
 // back to the item's original position.
+//
+// split_ok: the size-class split (small_m) with its second stream pays off
+// for device-resident batches (batched calls, plans and their graphs) and is
+// measured to cost more than it gains for single-instance calls (the serving
+// lanes) and the host-buffer batch call, which pack every system in the large
+// class instead.
 int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutView& out,
-            const vsbpp_params& prm, bool plain, cudaStream_t st) {
-    if (!lp.presort) return enqueue_core(lp, sc, in, out, prm, plain, st);
+            const vsbpp_params& prm, bool plain, cudaStream_t st, bool split_ok = true) {
+    if (!lp.presort) return enqueue_core(lp, sc, in, out, prm, plain, st, split_ok);
     if (in.N == 0) return VSBPP_OK;
     PresortParams pp;
     std::memset(&pp, 0, sizeof(pp));
@@ -1069,7 +1080,7 @@ int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutVie
     sorted.w_all = sc.ps_w;
     OutView out2 = out;
     out2.bin_of_item = sc.ps_boi;
-    const int rc = enqueue_core(lp, sc, sorted, out2, prm, plain, st);
+    const int rc = enqueue_core(lp, sc, sorted, out2, prm, plain, st, split_ok);
     if (rc != VSBPP_OK) return rc;
     VS_TRY(unpermute_launch(pp, static_cast<int>(std::min<int64_t>(lp.prep_grid, (in.N + 7) / 8)), st));
     return VSBPP_OK;
@@ -1226,7 +1237,7 @@ int vsbpp_pack_device(const int32_t* w, int64_t m, const int32_t* B, int32_t n, 
         if ((rc = ensure_scratch(sc, lp, 1, m))) return rc;
         BatchView in{1, w, nullptr, m, B, nullptr, n};
         OutView out{bin_of_item, bin_type, num_bins, total_capacity, status, nullptr, nullptr, nullptr};
-        return enqueue(lp, sc, in, out, prm, false, st);
+        return enqueue(lp, sc, in, out, prm, false, st, false);
     } catch (...) {
         return VSBPP_ENOMEM;      // no exception crosses the C interface
     }
@@ -1325,7 +1336,7 @@ int vsbpp_pack_batch_host(int64_t N, const int32_t* w_all, const int64_t* w_off,
             return rc;
         BatchView in{N, sc.h_w, sc.hb_woff, 0, sc.h_B, sc.hb_Boff, 0};
         OutView out{sc.h_boi, sc.h_bt, sc.hb_nb, sc.hb_tot, sc.hb_st, nullptr, nullptr, nullptr};
-        if ((rc = enqueue(lp, sc, in, out, prm, false, st))) return rc;
+        if ((rc = enqueue(lp, sc, in, out, prm, false, st, false))) return rc;
         if ((rc = hc->to_host(bin_of_item_all, sc.h_boi, sizeof(int32_t) * total_m)) ||
             (rc = hc->to_host(bin_type_all, sc.h_bt, sizeof(int32_t) * total_m)) ||
             (rc = hc->to_host(num_bins, sc.hb_nb, sizeof(int64_t) * N)) ||
