@@ -23,14 +23,19 @@
 //           of residual r (NS words), and the bitmap of residuals present
 //           (32 words, word l in lane l's register).  BF takes the least
 //           residual >= w present (one warp minimum), then the first segment
-//           in its row.
+//           in its row.  Both bitmaps run from the top bit down (residual or
+//           segment 32q + x is bit 31 - x of word q), so one count of leading
+//           zeros finds the least member of a word.
 //
 // Within the chosen segment each lane reads one 16-byte quad; one warp
 // minimum over (index, residual or capacity) keys names the bin, and the
 // segment's new maximum comes from the same read (count of bins at the old
-// maximum and the largest other residual, reduced alongside).  All smem
-// writes of an item are made by lane 0 in program order; one __syncwarp()
-// orders them before the next item's reads.  Item weights are read from
+// maximum and the largest other residual, reduced alongside).  Every lane
+// makes every shared-memory store of an item with the same value (predicated
+// where a store may not apply), so each lane reads back only what it stored
+// itself and the item needs no barrier; the spread index rows of the larger
+// shapes (one writer lane, other reader lanes) take one __syncwarp() per
+// item.  Item weights are read from
 // global memory a 32-item block ahead, each lane holding one item's weight
 // together with the capacity of the smallest type that holds it.
 #pragma once
@@ -49,8 +54,8 @@ __host__ __device__ inline int h1w_ns(int slot_cap) {
          : slot_cap <= kWarpMaxSlots ? 8 : 0;
 }
 
-// Shared memory of one warp: slots, a 16-byte pad (the write target of a bin
-// that does not divide), the BF rows (1024 residuals x NS words) and a
+// Shared memory of one warp: slots, a 16-byte pad (the write target of the
+// 16-bit form's bin that does not divide), the BF rows (1024 residuals x NS words) and a
 // 16-byte pad (the target of index writes that do not apply) when laid out,
 // capacities.
 __host__ __device__ inline int h1w_group_bytes(int slot_cap, int bf_index) {
@@ -102,6 +107,13 @@ struct H1Warp {
         return d;
     }
 
+    // This lane's part of "residual >= x" in the present-residual bitmap
+    // (residual 32 * lane + y at bit 31 - y).
+    __device__ __forceinline__ uint32_t present_mask(uint32_t x) const {
+        const uint32_t xi = x >> 5, ul = static_cast<uint32_t>(lane);
+        return ul < xi ? 0u : ul == xi ? (0xFFFFFFFFu >> (x & 31)) : 0xFFFFFFFFu;
+    }
+
     // Type of a capacity (capacities are distinct and descending).
     __device__ __forceinline__ uint32_t type_of(uint32_t cap, int n) const {
         int lo = 0, hi = n - 1;
@@ -146,7 +158,7 @@ struct H1Warp {
         const uint32_t ulane = static_cast<uint32_t>(lane);
 
         uint32_t sm[NS];                 // segment maxima, segment 32q + lane
-        uint32_t wb = 0;                 // residuals 32*lane .. 32*lane+31 present
+        uint32_t wb = 0;                 // residuals 32*lane .. 32*lane+31 present, top bit first
 #pragma unroll
         for (int q = 0; q < NS; ++q) sm[q] = 0;
         // start state (preopened bins: all in segment 0)
@@ -154,7 +166,7 @@ struct H1Warp {
         if (IDX) {
             for (uint32_t t = 0; t < L; ++t) {
                 const uint32_t r = Bs[t];
-                if ((r >> 5) == ulane) wb |= 1u << (r & 31);
+                if ((r >> 5) == ulane) wb |= 0x80000000u >> (r & 31);
             }
         }
 
@@ -189,14 +201,17 @@ struct H1Warp {
             dnext = descriptor(wpre, static_cast<int64_t>(j0) + 32 + ulane, n, p.seed, key0);
             wpre = weight(w, static_cast<int64_t>(j0) + 64 + ulane, k);
             uint32_t d = __shfl_sync(kFull, dblk, 0);
-            uint32_t bout = 0;
+            uint32_t msk = IDX ? present_mask(d & 0x7FFFu) : 0u;
+            uint32_t bout = 0, fit_blk = 0;          // fit tests of the block (< 2^20)
         for (uint32_t jj = 0; jj < cnt; ++jj) {
-            // the next item's descriptor (independent of the packing state)
+            // the next item's descriptor and present-residual mask
+            // (independent of the packing state, off the item's chain)
             const uint32_t dn = __shfl_sync(kFull, dblk, static_cast<int>((jj + 1u) & 31u));
+            const uint32_t mskn = IDX ? present_mask(dn & 0x7FFFu) : 0u;
             const uint32_t wj = d & 0x7FFFu;
             const uint32_t Bn = (d >> 16) & 0x7FFFu;
             const int c = CRIT == kRandom ? static_cast<int>(((d >> 15) & 1u) | ((d >> 30) & 2u)) : CRIT;
-            fit_tests += L;
+            fit_blk += L;
             uint32_t pend_word = 0;
             if (IDX) pend_word = rows[pend_at];
 
@@ -228,14 +243,15 @@ struct H1Warp {
                 hit = Mseg >= wj;
                 R = Mseg;
             } else if (IDX) {
-                // residuals >= w present in this lane's word (selects, no branches)
-                const uint32_t wi = wj >> 5;
-                const uint32_t x = wb & (ulane < wi ? 0u : ulane == wi ? ~((1u << (wj & 31)) - 1u) : 0xFFFFFFFFu);
-                uint32_t key = x ? 32u * ulane + static_cast<uint32_t>(__ffs(x) - 1) : kNoKey;
+                // residuals >= w present in this lane's word: the least is the
+                // highest bit left
+                const uint32_t x = wb & msk;
+                uint32_t key = x ? 32u * ulane + static_cast<uint32_t>(__clz(x)) : kNoKey;
                 key = __reduce_min_sync(kFull, key);
                 hit = key != kNoKey;
                 R = hit ? key : 0u;
-                rows[pend_at] = pend_word | pend_bit;        // the deferred entry, before any row read
+                // the deferred entry, before any row read
+                if (pend_at != kRowsPad) rows[pend_at] = pend_word | pend_bit;
                 pend_at = kRowsPad;
                 pend_bit = 0;
                 // the row the chosen bin leaves and the row it enters, read together
@@ -243,18 +259,27 @@ struct H1Warp {
                 if constexpr (kLaneRows) {
                     rw[0] = ulane < NS ? rows[R * NS + ulane] : 0u;
                     rn[0] = ulane < NS ? rows[Rn * NS + ulane] : 0u;
-                    const uint32_t sk = rw[0] ? 32u * ulane + static_cast<uint32_t>(__ffs(rw[0]) - 1) : kNoKey;
+                    const uint32_t sk = rw[0] ? 32u * ulane + static_cast<uint32_t>(__clz(rw[0])) : kNoKey;
                     sf = __reduce_min_sync(kFull, sk);
                     sf = hit ? sf : 0u;
                 } else {
+                    if constexpr (NS == 2) {        // a row is one 8-byte word pair
+                        const uint2 ra = *reinterpret_cast<const uint2*>(rows + R * 2u);
+                        const uint2 rb = *reinterpret_cast<const uint2*>(rows + Rn * 2u);
+                        rw[0] = ra.x;
+                        rw[1] = ra.y;
+                        rn[0] = rb.x;
+                        rn[1] = rb.y;
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < NS; ++q) {
-                        rw[q] = rows[R * NS + q];
-                        rn[q] = rows[Rn * NS + q];
+                        for (int q = 0; q < NS; ++q) {
+                            rw[q] = rows[R * NS + q];
+                            rn[q] = rows[Rn * NS + q];
+                        }
                     }
 #pragma unroll
                     for (int q = NS - 1; q >= 0; --q)
-                        sf = rw[q] ? 32u * q + static_cast<uint32_t>(__ffs(rw[q]) - 1) : sf;
+                        sf = rw[q] ? 32u * q + static_cast<uint32_t>(__clz(rw[q])) : sf;
                 }
             } else {
                 const uint32_t key = bf_scan<kR>(wj, L);
@@ -308,7 +333,8 @@ struct H1Warp {
             uint32_t b, r_old, Bt;
             if (W10) {                                 // (index << 20) | (residual << 10) | capacity
                 b = hit ? 128u * sf + (k1 >> 20) : L;
-                r_old = hit ? (k1 >> 10) & 0x3FFu : Bn;
+                // a BF or WF item takes a bin at the residual R it sought
+                r_old = hit ? (c == kFF ? (k1 >> 10) & 0x3FFu : R) : Bn;
                 Bt = hit ? k1 & 0x3FFu : Bn;
             } else {
                 b = hit ? 128u * sf + (k1 >> 16) : L;
@@ -318,11 +344,14 @@ struct H1Warp {
             const uint32_t r_new = r_old - wj;
             const bool fire = (Bt < 2u * r_old) && (2u * r_new <= Bt);     // Rule 5
             const uint32_t Lf = hit ? L : L + 1u;      // where a divided-off bin goes
-            // every lane writes the same words; a bin that does not divide
-            // writes the pad word past the slots
+            // every lane writes the same words (a predicated store for the
+            // divided-off bin: no branch, nothing written when it does not
+            // divide)
             slots[b] = (r_new << kR) | Bt;
-            slots[fire ? Lf : cap_bins] = (Bt << kR) | Bt;
-            const uint32_t sb = b >> 7, sfire = Lf >> 7;
+            if (fire) slots[Lf] = (Bt << kR) | Bt;
+            // the chosen bin lies in segment sf (or is the new bin L): known
+            // before the bin itself, so the updates below need not wait for it
+            const uint32_t sb = hit ? sf : (L >> 7), sfire = Lf >> 7;
 
             // 3. segment maxima
             if (kSeg) {
@@ -360,45 +389,50 @@ struct H1Warp {
                     else
                         cR = cM;
                 }
-                // selects and plain stores only: an update that does not
-                // apply writes the pad word
+                // selects and predicated stores only (no branch): a store that
+                // does not apply is not made, or writes the pad word
                 const bool clear = hit && cR == 1u;
                 bool any;
                 if constexpr (kLaneRows) {
                     // the lane holding word sb / 32 writes both rows' words
                     const bool here = ulane == (sb >> 5);
-                    const uint32_t cl = here ? rw[0] & ~(1u << (sb & 31)) : rw[0];
+                    const uint32_t cl = here ? rw[0] & ~(0x80000000u >> (sb & 31)) : rw[0];
                     any = __any_sync(kFull, cl != 0u);
                     if (here) {
                         rows[clear ? r_old * NS + (sb >> 5) : kRowsPad] = cl;
-                        rows[r_new > 0u ? r_new * NS + (sb >> 5) : kRowsPad] = rn[0] | (1u << (sb & 31));
+                        rows[r_new > 0u ? r_new * NS + (sb >> 5) : kRowsPad] = rn[0] | (0x80000000u >> (sb & 31));
                     }
                 } else {
                     uint32_t anyw = 0, word = 0, wnew = 0;
 #pragma unroll
                     for (int q = 0; q < NS; ++q) {
                         const bool here = (sb >> 5) == static_cast<uint32_t>(q);
-                        const uint32_t cl = here ? rw[q] & ~(1u << (sb & 31)) : rw[q];
+                        const uint32_t cl = here ? rw[q] & ~(0x80000000u >> (sb & 31)) : rw[q];
                         word = here ? cl : word;
                         anyw |= cl;
                         wnew = here ? rn[q] : wnew;
                     }
                     any = anyw != 0u;
-                    rows[clear ? r_old * NS + (sb >> 5) : kRowsPad] = word;
-                    rows[r_new > 0u ? r_new * NS + (sb >> 5) : kRowsPad] = wnew | (1u << (sb & 31));
+                    if (clear) rows[r_old * NS + (sb >> 5)] = word;
+                    rows[r_new > 0u ? r_new * NS + (sb >> 5) : kRowsPad] = wnew | (0x80000000u >> (sb & 31));
                 }
-                wb = (clear && !any && (r_old >> 5) == ulane) ? wb & ~(1u << (r_old & 31)) : wb;
-                wb = (r_new > 0u && (r_new >> 5) == ulane) ? wb | (1u << (r_new & 31)) : wb;
+                wb = (clear && !any && (r_old >> 5) == ulane) ? wb & ~(0x80000000u >> (r_old & 31)) : wb;
+                wb = (r_new > 0u && (r_new >> 5) == ulane) ? wb | (0x80000000u >> (r_new & 31)) : wb;
                 pend_at = fire ? Bt * NS + (sfire >> 5) : kRowsPad;
-                pend_bit = fire ? 1u << (sfire & 31) : 0u;
-                wb = (fire && (Bt >> 5) == ulane) ? wb | (1u << (Bt & 31)) : wb;
+                pend_bit = fire ? 0x80000000u >> (sfire & 31) : 0u;
+                wb = (fire && (Bt >> 5) == ulane) ? wb | (0x80000000u >> (Bt & 31)) : wb;
             }
             L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
             bout = ulane == jj ? b : bout;
             d = dn;
-            __syncwarp();
+            msk = mskn;
+            // with the rows in every lane, each lane stores every word the
+            // item changes and reads only words it stored itself; spread
+            // rows are written by one lane and read by another
+            if constexpr (kLaneRows) __syncwarp();
         }
             if (ulane < cnt) raw[j0 + ulane] = static_cast<int32_t>(bout);
+            fit_tests += fit_blk;
         }
         L_io = L;
         return true;
@@ -700,7 +734,7 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
                 if (use16) s16[lane] = static_cast<uint16_t>((Bl << 8) | Bl);
                 else g.slots[lane] = (Bl << kR) | Bl;
                 if (use16 && H1Warp<NS, CRIT>::kBFItems) atomicOr(&rows16[Bl * kNS16], 1u);   // segment 0
-                else if (use_idx) atomicOr(&g.rows[Bl * NS], 1u);
+                else if (use_idx) atomicOr(&g.rows[Bl * NS], 0x80000000u);   // segment 0, top bit first
             }
             L = static_cast<uint32_t>(n);
             __syncwarp();
