@@ -33,9 +33,13 @@
 // In the chosen sub-segment (FF, WF) or segment (BF) each lane turns its
 // matching slots into (position, slot) keys, and one warp minimum names the
 // bin with its residual and type.  The chain per item is straight-line
-// arithmetic and warp reductions; the stores of an item are ordered before
-// the next item's reads by __syncwarp.  CTA 1's warp only lends its shared
-// memory: it waits at the closing cluster barrier.
+// arithmetic and warp reductions.  In the BF kernel each slot is stored by
+// the lane that reads it and word q of every presence row by lane q (both
+// bitmaps there run from the top bit down, so a count of leading zeros finds
+// a word's least member), so an item needs no barrier; the other kernels
+// order an item's stores before the next item's reads by __syncwarp.  CTA
+// 1's warp only lends its shared memory: it waits at the closing cluster
+// barrier.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -71,7 +75,22 @@ struct KDMem {
         q[lane] = make_uint4(0u, 0u, 0u, 0u);
         q[32 + lane] = make_uint4(0u, 0u, 0u, 0u);
     }
+    // the same, each lane clearing the bytes it reads (its 8 bytes of every
+    // sub-segment): no barrier is needed before its own reads
+    __device__ __forceinline__ void zero_own(uint32_t S, uint32_t lane) const {
+        unsigned char* q = seg(S);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) reinterpret_cast<uint2*>(q + 256 * k)[lane] = make_uint2(0u, 0u);
+    }
 };
+
+// Bit of member x in its 32-bit word of a bitmap: from the top down in the BF
+// kernel (a count of leading zeros then finds a word's least member), from
+// the bottom up otherwise.
+template <bool TOP>
+__device__ __forceinline__ uint32_t kd_bit(uint32_t x) {
+    return TOP ? 0x80000000u >> (x & 31u) : 1u << (x & 31u);
+}
 
 // slot c (0..3) of a lane's 8 bytes
 __device__ __forceinline__ uint32_t kd_half(uint2 v, int c) {
@@ -83,6 +102,7 @@ template <int CRIT>
 __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
     constexpr bool kSeg = CRIT != kBF;                    // FF or WF items occur
     constexpr bool kIdx = CRIT == kBF || CRIT == kRandom;  // BF items occur
+    constexpr bool kTop = CRIT == kBF;                    // bitmaps from the top bit down
     constexpr uint32_t kNo = 0xFFFFFFFFu;
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -150,10 +170,10 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 tm[0] = lane == 0 ? B1 : 0u;
             }
             if (kIdx) {
-                if (lane < static_cast<uint32_t>(n)) atomicOr(&pres[Bl * 32u], 1u);
+                if (lane < static_cast<uint32_t>(n)) atomicOr(&pres[Bl * 32u], kd_bit<kTop>(0));
                 for (int t = 0; t < n; ++t) {
                     const uint32_t r = __shfl_sync(kFull, Bl, t);
-                    gw |= (r >> 5) == lane ? 1u << (r & 31) : 0u;
+                    gw |= (r >> 5) == lane ? kd_bit<kTop>(r) : 0u;
                 }
             }
             below = lane < static_cast<uint32_t>(n) ? 1u : 0u;
@@ -182,6 +202,85 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
             const int cnt = static_cast<int>(min(static_cast<int64_t>(32), m - j0));
             uint32_t bout = 0, fit_blk = 0;          // fit tests of this block (< 2^24)
             for (int jj = 0; jj < cnt; ++jj) {
+              if constexpr (CRIT == kBF) {
+                // BF items only: straight-line, no barrier.  Every slot is
+                // stored by the lane that reads it (the lane holding bins
+                // 4l..4l+3 of each sub-segment), word q of every presence row
+                // by lane q, and a lane reads nothing else.
+                const uint32_t wj = __shfl_sync(kFull, wcur, jj);
+                fit_blk += L;
+                // 1. r* = the least residual >= w present (residual r is bit
+                //    31 - (r & 31) of lane r / 32's word)
+                const uint32_t wi = wj >> 5;
+                const uint32_t mw = gw & (lane < wi ? 0u : lane == wi ? (kNo >> (wj & 31)) : kNo);
+                const uint32_t R = __reduce_min_sync(kFull, mw ? 32u * lane + static_cast<uint32_t>(__clz(mw)) : kNo);
+                const bool hit = R != kNo;
+                // the first segment of row r* and the bins at r* in it; with
+                // nothing fitting, row 0 (never set) and segment 0 are read and
+                // the results go unused (a segment index is kept below 2^10,
+                // the overflow area's reach, whatever the row holds)
+                const uint32_t Rc = hit ? R : 0u;
+                const uint32_t rowv = pres[Rc * 32u + lane];
+                uint32_t S = __reduce_min_sync(kFull, rowv ? 32u * lane + static_cast<uint32_t>(__clz(rowv)) : kNo);
+                S = (hit && S < static_cast<uint32_t>(kKDMaxSegs)) ? S : 0u;
+                const unsigned char* base = M.seg(S);
+                uint2 v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[k] = reinterpret_cast<const uint2*>(base + 256 * k)[lane];
+                const uint32_t R5 = Rc << 5;
+                uint32_t key[16], one[16];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const uint32_t sv = kd_half(v[k], cc);
+                        const bool mt = (sv & 0xFFE0u) == R5;
+                        one[4 * k + cc] = mt ? 1u : 0u;
+                        key[4 * k + cc] = mt ? ((128u * k + 4u * lane + cc) << 16) | sv : kNo;
+                    }
+#pragma unroll
+                for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+                    for (int x = 0; x < h; ++x) {
+                        key[x] = min(key[x], key[x + h]);
+                        one[x] += one[x + h];
+                    }
+                // the chosen bin (least position: the flat scan's first bin at
+                // r*), the bins at r* in S, and whether r* is in another
+                // segment: three collectives issued together
+                const uint32_t k3 = __reduce_min_sync(kFull, key[0]);
+                const uint32_t atR = __reduce_add_sync(kFull, one[0]);
+                const uint32_t nw = lane == (S >> 5) ? rowv & ~(0x80000000u >> (S & 31)) : rowv;
+                const bool elsewhere = __any_sync(kFull, nw != 0u);
+                // nothing fits: a bin of the smallest type holding w
+                const uint32_t tyn = 31u - static_cast<uint32_t>(__clz(__ballot_sync(kFull, Bl >= wj)));
+                const uint32_t ty = hit ? (k3 & 31u) : tyn;
+                const uint32_t b = hit ? S * 512u + ((k3 >> 16) & 511u) : L;
+                const uint32_t Bt = __shfl_sync(kFull, Bl, static_cast<int>(ty));
+                const uint32_t r_old = hit ? R : Bt;
+                const uint32_t r_new = r_old - wj;
+                const bool cross = Bt < 2u * r_old && 2u * r_new <= Bt;        // Rule 5
+                const bool fire = p.remark3 ? remark3_divide(below, Bl, !hit, Bt, cross) : cross;
+                const uint32_t Lf = hit ? L : L + 1u;
+                // 2. slots (a segment a new bin opens is cleared first)
+                if (!hit && (b & 511u) == 0u) M.zero_own(b >> 9, lane);
+                if (fire && (Lf & 511u) == 0u) M.zero_own(Lf >> 9, lane);
+                if (lane == ((b & 127u) >> 2)) *M.slot(b) = static_cast<uint16_t>((r_new << 5) | ty);
+                if (fire && lane == ((Lf & 127u) >> 2)) *M.slot(Lf) = static_cast<uint16_t>((Bt << 5) | ty);
+                // 3. presence: r* leaves S when the chosen bin was S's only bin
+                //    at r* (and leaves the present set when no other segment
+                //    holds it); r_new and a divided-off bin's capacity enter
+                const uint32_t Sb = b >> 9, Sf = Lf >> 9;
+                const bool leave = hit && atR == 1u;
+                if (leave && lane == (S >> 5)) pres[R * 32u + lane] = nw;
+                gw &= (leave && !elsewhere && lane == (R >> 5)) ? ~(0x80000000u >> (R & 31)) : kNo;
+                if (r_new > 0u && lane == (Sb >> 5)) atomicOr(&pres[r_new * 32u + lane], 0x80000000u >> (Sb & 31));
+                gw |= (r_new > 0u && lane == (r_new >> 5)) ? 0x80000000u >> (r_new & 31) : 0u;
+                if (fire && lane == (Sf >> 5)) atomicOr(&pres[Bt * 32u + lane], 0x80000000u >> (Sf & 31));
+                gw |= (fire && lane == (Bt >> 5)) ? 0x80000000u >> (Bt & 31) : 0u;
+                L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
+                bout = lane == static_cast<uint32_t>(jj) ? b : bout;
+              } else {
                 const uint32_t wj = __shfl_sync(kFull, wcur, jj);
                 const int c = CRIT == kRandom ? __shfl_sync(kFull, ccur, jj) : CRIT;
                 fit_blk += L;
@@ -382,6 +481,7 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 __syncwarp();
                 L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
                 bout = lane == static_cast<uint32_t>(jj) ? b : bout;
+              }
             }
             if (lane < static_cast<uint32_t>(cnt)) raw[j0 + lane] = static_cast<int32_t>(bout);
             fit_tests += fit_blk;
