@@ -156,6 +156,14 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 reinterpret_cast<uint32_t*>(submax)[x] = 0u;
         if (kIdx)
             for (uint32_t x = lane; x < (B1 + 1u) * 32u; x += 32) pres[x] = 0u;
+        if constexpr (CRIT == kBF) {
+            // every segment the system can reach (at most 2m + n bins) reads
+            // as empty from the start, each lane clearing the bytes it reads:
+            // no item has to clear a segment it opens
+            const int64_t reach = (2 * m + n + kKDSeg - 1) / kKDSeg + 1;
+            const uint32_t nseg = static_cast<uint32_t>(min(reach, static_cast<int64_t>(kKDMaxSegs)));
+            for (uint32_t S = 0; S < nseg; ++S) M.zero_own(S, lane);
+        }
         __syncwarp();
         int32_t* raw = p.out.bin_of_item + wb;
 
@@ -201,6 +209,11 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
             const int cnext = pick_criterion(p.criterion, p.seed, static_cast<uint64_t>(jn));
             const int cnt = static_cast<int>(min(static_cast<int64_t>(32), m - j0));
             uint32_t bout = 0, fit_blk = 0;          // fit tests of this block (< 2^24)
+            // the block adds at most 64 bins (L + 64 <= 2^19 here), so a new
+            // or divided-off bin lies in segment s0 or s0 + 1
+            const uint32_t s0 = L >> 9;
+            uint16_t* const tail0 = reinterpret_cast<uint16_t*>(M.seg(s0));
+            uint16_t* const tail1 = reinterpret_cast<uint16_t*>(M.seg(s0 + 1u));
             for (int jj = 0; jj < cnt; ++jj) {
               if constexpr (CRIT == kBF) {
                 // BF items only: straight-line, no barrier.  Every slot is
@@ -227,29 +240,41 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 uint2 v[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) v[k] = reinterpret_cast<const uint2*>(base + 256 * k)[lane];
-                const uint32_t R5 = Rc << 5;
-                uint32_t key[16], one[16];
+                // the lane's 16 slots of S as 8 words of two: a half matches r*
+                // when its residual bits equal r*'s; adding 0x7FFF to the
+                // masked difference sets bit 15 (31) exactly when the low
+                // (high) half differs (residuals <= 1023 leave bit 15 clear)
+                const uint32_t R5 = Rc << 5, RR = R5 | (R5 << 16);
+                uint32_t xw[8];
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
+                for (int k = 0; k < 4; ++k) {
+                    xw[2 * k] = v[k].x;
+                    xw[2 * k + 1] = v[k].y;
+                }
+                uint32_t mm = 0;                     // word q's low half at bit q, high half at bit 16 + q
 #pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) {
-                        const uint32_t sv = kd_half(v[k], cc);
-                        const bool mt = (sv & 0xFFE0u) == R5;
-                        one[4 * k + cc] = mt ? 1u : 0u;
-                        key[4 * k + cc] = mt ? ((128u * k + 4u * lane + cc) << 16) | sv : kNo;
-                    }
-#pragma unroll
-                for (int h = 8; h >= 1; h >>= 1)
-#pragma unroll
-                    for (int x = 0; x < h; ++x) {
-                        key[x] = min(key[x], key[x + h]);
-                        one[x] += one[x + h];
-                    }
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t u = ((xw[q] ^ RR) & 0x7FE07FE0u) + 0x7FFF7FFFu;
+                    mm |= (~u >> (15 - q)) & (0x00010001u << q);
+                }
+                // the lane's first match: the least 2 * word + half
+                const uint32_t mlo = mm & 0xFFu, mhi = mm >> 16;
+                const uint32_t vlo = mlo ? 2u * static_cast<uint32_t>(__ffs(mlo) - 1) : 64u;
+                const uint32_t vhi = mhi ? 2u * static_cast<uint32_t>(__ffs(mhi) - 1) + 1u : 64u;
+                const uint32_t vv = min(vlo, vhi);
+                const uint32_t qw = (vv >> 1) & 7u;
+                const uint32_t a0 = (qw & 1u) ? xw[1] : xw[0], a1 = (qw & 1u) ? xw[3] : xw[2];
+                const uint32_t a2 = (qw & 1u) ? xw[5] : xw[4], a3 = (qw & 1u) ? xw[7] : xw[6];
+                const uint32_t b0 = (qw & 2u) ? a1 : a0, b1 = (qw & 2u) ? a3 : a2;
+                const uint32_t cw = (qw & 4u) ? b1 : b0;
+                const uint32_t sv = (vv & 1u) ? (cw >> 16) : (cw & 0xFFFFu);
+                // position in S: sub-segment vv / 4, slot 4 * lane + vv % 4 in it
+                const uint32_t kmin = mm ? (((128u * (vv >> 2) + 4u * lane + (vv & 3u)) << 16) | sv) : kNo;
                 // the chosen bin (least position: the flat scan's first bin at
                 // r*), the bins at r* in S, and whether r* is in another
                 // segment: three collectives issued together
-                const uint32_t k3 = __reduce_min_sync(kFull, key[0]);
-                const uint32_t atR = __reduce_add_sync(kFull, one[0]);
+                const uint32_t k3 = __reduce_min_sync(kFull, kmin);
+                const uint32_t atR = __reduce_add_sync(kFull, static_cast<uint32_t>(__popc(mm)));
                 const uint32_t nw = lane == (S >> 5) ? rowv & ~(0x80000000u >> (S & 31)) : rowv;
                 const bool elsewhere = __any_sync(kFull, nw != 0u);
                 // nothing fits: a bin of the smallest type holding w
@@ -262,11 +287,13 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 const bool cross = Bt < 2u * r_old && 2u * r_new <= Bt;        // Rule 5
                 const bool fire = p.remark3 ? remark3_divide(below, Bl, !hit, Bt, cross) : cross;
                 const uint32_t Lf = hit ? L : L + 1u;
-                // 2. slots (a segment a new bin opens is cleared first)
-                if (!hit && (b & 511u) == 0u) M.zero_own(b >> 9, lane);
-                if (fire && (Lf & 511u) == 0u) M.zero_own(Lf >> 9, lane);
-                if (lane == ((b & 127u) >> 2)) *M.slot(b) = static_cast<uint16_t>((r_new << 5) | ty);
-                if (fire && lane == ((Lf & 127u) >> 2)) *M.slot(Lf) = static_cast<uint16_t>((Bt << 5) | ty);
+                // 2. slots: the chosen bin in S (read above), a new or
+                //    divided-off bin in one of the block's tail segments
+                uint16_t* const pb = hit ? reinterpret_cast<uint16_t*>(const_cast<unsigned char*>(base))
+                                         : ((b >> 9) == s0 ? tail0 : tail1);
+                uint16_t* const pf = (Lf >> 9) == s0 ? tail0 : tail1;
+                if (lane == ((b & 127u) >> 2)) pb[b & 511u] = static_cast<uint16_t>((r_new << 5) | ty);
+                if (fire && lane == ((Lf & 127u) >> 2)) pf[Lf & 511u] = static_cast<uint16_t>((Bt << 5) | ty);
                 // 3. presence: r* leaves S when the chosen bin was S's only bin
                 //    at r* (and leaves the present set when no other segment
                 //    holds it); r_new and a divided-off bin's capacity enter
