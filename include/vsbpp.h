@@ -43,8 +43,11 @@
  *
  * Threading: every entry point may be called from any host thread.  Calls on
  * different streams (or devices) proceed at the same time; calls on the same
- * stream, on the same plan, or host-memory calls on the same device, are
- * serialised by the library.  The launch configuration and the counter and
+ * stream or on the same plan are serialised by the library.  Host-memory
+ * calls (vsbpp_pack, vsbpp_pack_batch_host) from several threads also proceed
+ * at the same time: each borrows a stream, 16 MB of pinned staging and
+ * scratch of the current device for its length (created when all are in use,
+ * kept for reuse until the process exits).  The launch configuration and the counter and
  * timing switches are process-wide.  Device entry points are asynchronous
  * with respect to the host and ordered on the caller's stream.
  *
@@ -224,9 +227,10 @@ int vsbpp_pack_batch(int64_t N, const int32_t *w_all, const int64_t *w_off,
  * synchronous.  Same CSR arguments and results as vsbpp_pack_batch, but every
  * array is a host pointer (pinned, e.g. from cudaHostAlloc, or pageable).
  * The library copies the inputs to device buffers it owns on the current
- * device, packs them with the same kernels on its own stream for that device,
- * copies the results back and returns when they are in place: the whole
- * host-to-host path in one call.  Pinned buffers are copied directly;
+ * device, packs them with the same kernels on a stream of its own that the
+ * call holds alone, copies the results back and returns when they are in
+ * place: the whole host-to-host path in one call.  Calls from several host
+ * threads run side by side on the GPU.  Pinned buffers are copied directly;
  * pageable ones are staged through the library's pinned buffers.  max_m: as
  * for vsbpp_pack_batch (0 lets the library read it off w_off).  Returns a
  * host-side status; per-instance codes are in status[].

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -336,7 +337,7 @@ Scratch& scratch_for(cudaStream_t st) {
 // overlaps the transfer of the other.
 struct HostCtx {
     static constexpr size_t kChunk = size_t(8) << 20;
-    std::recursive_mutex mu;         // held for a whole host-memory call
+    int dev = -1;
     cudaStream_t st = nullptr;
     void* pin[2] = {nullptr, nullptr};
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -395,15 +396,57 @@ struct HostCtx {
     }
 };
 
-// The host context of the current device (created on first use there).
-HostCtx* host_ctx() {
-    static std::map<int, HostCtx> ctx;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::recursive_mutex> lk(g_mu);
-    HostCtx& c = ctx[dev];
-    return c.init() == VSBPP_OK ? &c : nullptr;
+// Host contexts of each device.  A host-memory call borrows one for its
+// whole length (a free one, or a new one when all are in use) and gives it
+// back at the end, so calls from several host threads run side by side, each
+// on its own stream with its own staging and scratch.  Contexts are kept for
+// reuse until the process exits.
+struct HostPool {
+    std::deque<HostCtx> all;        // stable addresses
+    std::vector<HostCtx*> free_list;
+};
+
+std::map<int, HostPool>& host_pools() {
+    static std::map<int, HostPool> pools;
+    return pools;
 }
+
+void host_ctx_release(HostCtx* c) {
+    std::lock_guard<std::recursive_mutex> lk(g_mu);
+    host_pools()[c->dev].free_list.push_back(c);
+}
+
+// A context of the current device, held until the lease ends.
+struct HostLease {
+    HostCtx* c = nullptr;
+    HostLease() {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return;
+        HostCtx* got = nullptr;
+        {
+            std::lock_guard<std::recursive_mutex> lk(g_mu);
+            HostPool& pool = host_pools()[dev];
+            if (!pool.free_list.empty()) {
+                got = pool.free_list.back();
+                pool.free_list.pop_back();
+            } else {
+                pool.all.emplace_back();
+                got = &pool.all.back();
+                got->dev = dev;
+            }
+        }
+        if (got->init() != VSBPP_OK) {
+            host_ctx_release(got);
+            return;
+        }
+        c = got;
+    }
+    ~HostLease() {
+        if (c) host_ctx_release(c);
+    }
+    HostLease(const HostLease&) = delete;
+    HostLease& operator=(const HostLease&) = delete;
+};
 
 // ------------------------------------------------------------ launch plan
 struct Mode {
@@ -1252,9 +1295,9 @@ int vsbpp_pack(const int32_t* w, int64_t m, const int32_t* B, int32_t n, const v
         if ((rc = check_params(p))) return rc;
         *num_bins = 0;
         *total_capacity = 0;
-        HostCtx* hc = host_ctx();                 // this device's own stream and staging
+        HostLease lease;                          // a stream and staging of this device, this call's alone
+        HostCtx* hc = lease.c;
         if (!hc) return VSBPP_ECUDA;
-        std::lock_guard<std::recursive_mutex> lkh(hc->mu);
         cudaStream_t own = hc->st;
         Scratch& sc = scratch_for(own);
         std::lock_guard<std::recursive_mutex> lk(*sc.mu);
@@ -1311,9 +1354,9 @@ int vsbpp_pack_batch_host(int64_t N, const int32_t* w_all, const int64_t* w_off,
         if (max_m == 0) max_m = mm;
         if (mm > max_m) return VSBPP_EINVAL;
         const vsbpp_params prm = defaults(p);
-        HostCtx* hc = host_ctx();
+        HostLease lease;                          // a stream and staging of this device, this call's alone
+        HostCtx* hc = lease.c;
         if (!hc) return VSBPP_ECUDA;
-        std::lock_guard<std::recursive_mutex> lkh(hc->mu);
         cudaStream_t st = hc->st;
         LaunchPlan lp;
         if ((rc = build_plan(prm, max_m, N, lp, snapshot()))) return rc;

@@ -197,6 +197,33 @@ def test_host_batch_equals_device_batch(pinned):
         assert_same(b, got, ref, f"host batch h{h} c{c} pinned={pinned}")
 
 
+def test_host_batch_calls_from_several_threads():
+    """Four host threads call vsbpp_pack_batch_host at once (each call holds
+    a stream and staging the library lends it alone); every result equals the
+    oracle, on two rounds in a row."""
+    from concurrent.futures import ThreadPoolExecutor
+    b = I.config3(N=256, m_hi=4000, seed=98)
+    jobs = [(1, native.FF, 0), (1, native.BF, 0), (1, native.WF, 0), (2, native.BF, 5)]
+    refs = [run_oracle(b, h, c, s) for (h, c, s) in jobs]
+    arrs = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (b.w_all, b.w_off, b.B_all, b.B_off)]
+    dev = torch.cuda.current_device()
+
+    def one(k):
+        torch.cuda.set_device(dev)
+        h, c, s = jobs[k]
+        out = native.HostResult.empty(b.N, b.total_items)
+        return native.pack_batch_host(*arrs, out, h, c, s), out
+
+    with ThreadPoolExecutor(len(jobs)) as ex:
+        for rnd in range(2):
+            for k, (rc, out) in enumerate(ex.map(one, range(len(jobs)))):
+                assert rc == 0, native.strerror(rc)
+                got = oracle.BatchResult(*(np.asarray(x)[:n] for x, n in
+                                           ((out.status, b.N), (out.bin_of_item, b.total_items),
+                                            (out.bin_type, b.total_items), (out.num_bins, b.N), (out.total, b.N))))
+                assert_same(b, got, refs[k], f"threaded host batch {jobs[k]} round {rnd}")
+
+
 def test_server_with_options():
     """Requests with the pre-sort, Remark 3 and a bound, served in the mix."""
     rng = np.random.default_rng(99)
