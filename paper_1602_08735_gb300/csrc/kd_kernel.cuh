@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 reinterpret_cast<uint32_t*>(submax)[x] = 0u;
         if (kIdx)
             for (uint32_t x = lane; x < (B1 + 1u) * 32u; x += 32) pres[x] = 0u;
-        if constexpr (CRIT == kBF) {
+        if constexpr (CRIT != kRandom) {
             // every segment the system can reach (at most 2m + n bins) reads
             // as empty from the start, each lane clearing the bytes it reads:
             // no item has to clear a segment it opens
@@ -305,6 +305,101 @@ __global__ void __launch_bounds__(32) kd_pack_kernel(const KDParams p) {
                 gw |= (r_new > 0u && lane == (r_new >> 5)) ? 0x80000000u >> (r_new & 31) : 0u;
                 if (fire && lane == (Sf >> 5)) atomicOr(&pres[Bt * 32u + lane], 0x80000000u >> (Sf & 31));
                 gw |= (fire && lane == (Bt >> 5)) ? 0x80000000u >> (Bt & 31) : 0u;
+                L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
+                bout = lane == static_cast<uint32_t>(jj) ? b : bout;
+              } else if constexpr (CRIT == kFF || CRIT == kWF) {
+                // FF or WF items only: straight-line, no barrier.  Every slot
+                // is stored by the lane that reads it, the maximum of
+                // sub-segment G by lane G % 32 (the lane that reads it), and a
+                // lane reads nothing else.
+                const uint32_t wj = __shfl_sync(kFull, wcur, jj);
+                fit_blk += L;
+                // 1. the tile, then its sub-segment, then the bin (FF: the first
+                //    with maximum >= w; WF: the largest maximum, then the first
+                //    bin at it); with nothing fitting, sub-segment 0 is read and
+                //    the results go unused
+                bool hit;
+                uint32_t T, Mx = 0u;
+                if constexpr (CRIT == kFF) {
+                    uint32_t key = kNo;
+#pragma unroll
+                    for (int t = 3; t >= 0; --t)
+                        key = tm[t] >= wj ? ((lane + 32u * t) << 16) | tm[t] : key;
+                    key = __reduce_min_sync(kFull, key);
+                    hit = key != kNo;
+                    T = hit ? (key >> 16) & 127u : 0u;
+                } else {
+                    uint32_t key = 0u;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) key = max(key, (tm[t] << 8) | (127u - (lane + 32u * t)));
+                    key = __reduce_max_sync(kFull, key);
+                    Mx = key >> 8;
+                    hit = Mx >= wj;
+                    T = hit ? 127u - (key & 127u) : 0u;
+                }
+                const uint32_t sv = submax[T * 32u + lane];
+                const bool gsel = CRIT == kFF ? sv >= wj : sv == Mx;
+                const uint32_t gl = __reduce_min_sync(kFull, gsel ? lane : 32u);
+                const uint32_t G = hit ? T * 32u + (gl & 31u) : 0u;
+                const unsigned char* gbase = M.seg(G >> 2);
+                const uint2 q4 = reinterpret_cast<const uint2*>(gbase + (G & 3u) * 256u)[lane];
+                const uint32_t W5 = wj << 5;          // residual >= w  <=>  slot >= w << 5
+                uint32_t kk = kNo;
+#pragma unroll
+                for (int cc = 3; cc >= 0; --cc) {
+                    const uint32_t sl4 = kd_half(q4, cc);
+                    const bool mt = CRIT == kFF ? sl4 >= W5 : (sl4 >> 5) == Mx;
+                    kk = mt ? ((4u * lane + cc) << 16) | sl4 : kk;
+                }
+                const uint32_t k3 = __reduce_min_sync(kFull, kk);
+                // nothing fits: a bin of the smallest type holding w
+                const uint32_t tyn = 31u - static_cast<uint32_t>(__clz(__ballot_sync(kFull, Bl >= wj)));
+                const uint32_t ty = hit ? (k3 & 31u) : tyn;
+                const uint32_t b = hit ? G * 128u + ((k3 >> 16) & 127u) : L;
+                const uint32_t Bt = __shfl_sync(kFull, Bl, static_cast<int>(ty));
+                const uint32_t r_old = hit ? ((k3 & 0xFFFFu) >> 5) : Bt;
+                const uint32_t r_new = r_old - wj;
+                const bool cross = Bt < 2u * r_old && 2u * r_new <= Bt;        // Rule 5
+                const bool fire = p.remark3 ? remark3_divide(below, Bl, !hit, Bt, cross) : cross;
+                const uint32_t Lf = hit ? L : L + 1u;
+                // 2. slots: the chosen bin in G's segment, a new or divided-off
+                //    bin in one of the block's tail segments
+                uint16_t* const pb = hit ? reinterpret_cast<uint16_t*>(const_cast<unsigned char*>(gbase))
+                                         : ((b >> 9) == s0 ? tail0 : tail1);
+                uint16_t* const pf = (Lf >> 9) == s0 ? tail0 : tail1;
+                const uint32_t nsv = (r_new << 5) | ty;
+                if (lane == ((b & 127u) >> 2)) pb[b & 511u] = static_cast<uint16_t>(nsv);
+                if (fire && lane == ((Lf & 127u) >> 2)) pf[Lf & 511u] = static_cast<uint16_t>((Bt << 5) | ty);
+                // 3. sub-segment maxima: G's from its four slots a lane (the
+                //    chosen one updated); a new bin's sub-segment from its old
+                //    maximum (lane Gb % 32's own word)
+                const uint32_t Gb = b >> 7, Gf = Lf >> 7;
+                const uint32_t pos = b & 127u;
+                uint32_t mx = 0u;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const uint32_t sl4 = (lane == (pos >> 2) && (pos & 3u) == static_cast<uint32_t>(cc)) ? nsv
+                                                                                                        : kd_half(q4, cc);
+                    mx = max(mx, sl4 >> 5);
+                }
+                const uint32_t nmh = __reduce_max_sync(kFull, mx);
+                const uint32_t rowb = submax[(Gb & ~31u) + lane];
+                uint32_t nmb = hit ? nmh : max(rowb, r_new);
+                if (fire && Gf == Gb) nmb = max(nmb, Bt);
+                if (lane == (Gb & 31u)) submax[Gb] = static_cast<uint16_t>(nmb);
+                if (fire && Gf != Gb && lane == (Gf & 31u))
+                    submax[Gf] = static_cast<uint16_t>(max(static_cast<uint32_t>(submax[Gf]), Bt));
+                // tile maxima from the touched tiles' rows (each lane its own word)
+                const uint32_t Tb = Gb >> 5, Tf = Gf >> 5;
+                const bool two = fire && Tf != Tb;
+                const uint32_t tb = __reduce_max_sync(kFull, static_cast<uint32_t>(submax[Tb * 32u + lane]));
+                const uint32_t tf = two ? __reduce_max_sync(kFull, static_cast<uint32_t>(submax[Tf * 32u + lane])) : 0u;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t tile = lane + 32u * t;
+                    tm[t] = tile == Tb ? tb : tm[t];
+                    tm[t] = (two && tile == Tf) ? tf : tm[t];
+                }
                 L += (hit ? 0u : 1u) + (fire ? 1u : 0u);
                 bout = lane == static_cast<uint32_t>(jj) ? b : bout;
               } else {
