@@ -527,7 +527,7 @@ struct H1Warp {
                 key = __reduce_min_sync(kFull, key);
                 hit = key != kNoKey;
                 R = hit ? key : 0u;
-                r16[pend_at] = pend_word | pend_bit;
+                if (pend_at != kPad16) r16[pend_at] = pend_word | pend_bit;
                 pend_at = kPad16;
                 pend_bit = 0;
                 // the row the chosen bin leaves and the row it enters: word q
@@ -581,14 +581,16 @@ struct H1Warp {
             }
             k1 = __reduce_min_sync(kFull, k1);
             const uint32_t b = hit ? 256u * sf + (k1 >> 16) : L;
-            const uint32_t r_old = hit ? (k1 >> 8) & 0xFFu : Bn;
+            // a BF item takes a bin at the residual R it sought
+            const uint32_t r_old = hit ? (c == kBF ? R : (k1 >> 8) & 0xFFu) : Bn;
             const uint32_t Bt = hit ? k1 & 0xFFu : Bn;
             const uint32_t r_new = r_old - wj;
             const bool fire = (Bt < 2u * r_old) && (2u * r_new <= Bt);     // Rule 5
             const uint32_t Lf = hit ? L : L + 1u;
             s16[b] = static_cast<uint16_t>((r_new << 8) | Bt);
-            s16[fire ? Lf : cap_bins] = static_cast<uint16_t>((Bt << 8) | Bt);
-            const uint32_t sb = b >> 8, sfire = Lf >> 8;
+            if (fire) s16[Lf] = static_cast<uint16_t>((Bt << 8) | Bt);
+            // the chosen bin lies in segment sf (or is the new bin L)
+            const uint32_t sb = hit ? sf : (L >> 8), sfire = Lf >> 8;
 
             // 3. segment maxima
             if (kSeg) {
@@ -605,7 +607,7 @@ struct H1Warp {
             // 4. the BF index
             if (IDX) {
                 if (c != kBF) {
-                    r16[pend_at] = pend_word | pend_bit;
+                    if (pend_at != kPad16) r16[pend_at] = pend_word | pend_bit;
                     pend_at = kPad16;
                     pend_bit = 0;
                     rwl = ulane < kNS16 ? r16[r_old * kNS16 + ulane] : 0u;
@@ -625,7 +627,7 @@ struct H1Warp {
                 const uint32_t cl = here ? rwl & ~(1u << (sb & 31)) : rwl;
                 const bool any = __any_sync(kFull, cl != 0u);
                 if (here) {
-                    r16[clear ? r_old * kNS16 + (sb >> 5) : kPad16] = cl;
+                    if (clear) r16[r_old * kNS16 + (sb >> 5)] = cl;
                     r16[r_new > 0u ? r_new * kNS16 + (sb >> 5) : kPad16] = rnl | (1u << (sb & 31));
                 }
                 wb = (clear && !any && (r_old >> 5) == ulane) ? wb & ~(1u << (r_old & 31)) : wb;
