@@ -257,8 +257,11 @@ def latency_roof(native, batch, dev, stream, flush, name, kernel_ms, sm_mhz, rep
     system is a chain of dependent item steps (Rule 3 takes one item per
     step), so a pass cannot end before its largest system, packed alone.
     Reported: that system's solo kernel time (CUDA events on the launching
-    stream, L2 flushed), its cycles per item at the sampled SM clock, and the
-    batched kernel's time over it."""
+    stream, L2 flushed), its cycles per item at the sampled SM clock, the
+    batched kernel's time over it, and the cycles per item of a system of as
+    many unit items with one capacity of 1000 (a handful of bins alive: the
+    chain's floor, since the kernel's work per item does not grow with the
+    bins)."""
     import torch
     from paper_1602_08735_gb300 import instances as I
     h, c, s_ = dict((p[0], p[1:]) for p in PASSES)[name]
@@ -276,10 +279,26 @@ def latency_roof(native, batch, dev, stream, flush, name, kernel_ms, sm_mhz, rep
     native.kernel_timing_enable(False)
     solo = float(np.mean(t))
     m = db1.total_items
+    # the chain's floor: the same number of unit items into one capacity of
+    # 1000 (at most 2 * ceil(m / 1000) bins ever alive), the same pass
+    few = I.from_instances([(np.ones(m, dtype=np.int32), np.array([1000], dtype=np.int32))])
+    dbf = native.DeviceBatch.from_host(few, device=dev)
+    outf = native.DeviceResult.empty(1, dbf.total_items, device=dev)
+    assert native.pack_batch(dbf, outf, h, c, s_, stream=stream) == 0
+    native.kernel_timing_enable(True)
+    native.kernel_timing_read()
+    for _ in range(reps):
+        flush.zero_()
+        assert native.pack_batch(dbf, outf, h, c, s_, stream=stream) == 0
+    tf = native.kernel_timing_read()
+    native.kernel_timing_enable(False)
+    few_ms = float(np.mean(tf))
     return {"bound": "per-system dependent chain (largest system packed alone)", "pass": name,
             "largest_m": m, "solo_kernel_ms": solo, "sm_mhz": sm_mhz,
             "chain_cycles_per_item": solo * 1e-3 * sm_mhz * 1e6 / m,
-            "batched_kernel_ms": kernel_ms, "kernel_over_solo": kernel_ms / solo if solo else None}
+            "batched_kernel_ms": kernel_ms, "kernel_over_solo": kernel_ms / solo if solo else None,
+            "few_bins": {"items": m, "capacity": 1000, "bins": int(outf.num_bins.cpu()[0]), "kernel_ms": few_ms,
+                         "cycles_per_item": few_ms * 1e-3 * sm_mhz * 1e6 / m}}
 
 
 def serve_stream(native, reqs, rate):
