@@ -30,7 +30,8 @@
 // Within the chosen segment each lane reads one 16-byte quad; one warp
 // minimum over (index, residual or capacity) keys names the bin, and the
 // segment's new maximum comes from the same read (count of bins at the old
-// maximum and the largest other residual, reduced alongside).  Every lane
+// maximum and the largest other residual, reduced alongside; for FF one
+// maximum over the quad with the chosen slot updated).  Every lane
 // makes every shared-memory store of an item with the same value (predicated
 // where a store may not apply), so each lane reads back only what it stored
 // itself and the item needs no barrier; the spread index rows of the larger
@@ -305,7 +306,7 @@ struct H1Warp {
             const uint32_t i0 = (4u * ulane) << 16;
             const uint32_t j0 = (4u * ulane) << 20;          // 10-bit form: index field of a key
             uint32_t k1 = kNoKey, k2 = kNoKey, cR = 0, cM = 0, M2 = 0;
-            if (kSeg) {                     // these need only the quad: issued first
+            if (kSeg && CRIT != kFF) {      // these need only the quad: issued first
                 cM = __reduce_add_sync(kFull, (r0 == Mseg) + (r1 == Mseg) + (r2 == Mseg) + (r3 == Mseg));
                 M2 = __reduce_max_sync(kFull, max(max(r0 != Mseg ? r0 : 0u, r1 != Mseg ? r1 : 0u),
                                                   max(r2 != Mseg ? r2 : 0u, r3 != Mseg ? r3 : 0u)));
@@ -355,7 +356,22 @@ struct H1Warp {
 
             // 3. segment maxima
             if (kSeg) {
-                const uint32_t top = (r_old != Mseg || cM >= 2u) ? Mseg : max(M2, r_new);
+                uint32_t top;
+                if constexpr (CRIT == kFF) {
+                    // the new maximum of segment sf by one warp maximum over
+                    // the quad with the chosen slot updated: one reduction
+                    // fewer per item (WF, whose chosen bin always holds the
+                    // maximum, keeps the count at the maximum and the next
+                    // largest, issued beside the bin's reduction)
+                    const uint32_t pq = b & 127u;
+                    const bool mine = hit && ulane == (pq >> 2);
+                    const uint32_t e = pq & 3u;
+                    const uint32_t u0 = (mine && e == 0u) ? r_new : r0, u1 = (mine && e == 1u) ? r_new : r1;
+                    const uint32_t u2 = (mine && e == 2u) ? r_new : r2, u3 = (mine && e == 3u) ? r_new : r3;
+                    top = __reduce_max_sync(kFull, max(max(u0, u1), max(u2, u3)));
+                } else {
+                    top = (r_old != Mseg || cM >= 2u) ? Mseg : max(M2, r_new);
+                }
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
                     const uint32_t s = 32u * q + ulane;
