@@ -372,11 +372,11 @@ int vsbpp_plan_destroy(vsbpp_plan *plan);
  * Launch configuration and autotuner.
  *
  * The batched first-heuristic kernel runs thread groups of `warps` warps per
- * instance; in batched device calls and plans, instances with m <= small_m
- * go to single-warp groups whose bin slots are sized for small_m, launched on
- * a second stream beside the larger instances' launch (their blocks take the
- * shared memory the larger ones' warps give back as their queue runs dry).
- * Single-instance calls and vsbpp_pack_batch_host pack every instance in the
+ * instance; in batched calls (device or host memory) and plans, instances
+ * with m <= small_m go to single-warp groups whose bin slots are sized for
+ * small_m, launched on a second stream beside the larger instances' launch
+ * (their blocks take the shared memory the larger ones' warps give back as
+ * their queue runs dry).  Single-instance calls pack their instance in the
  * larger groups.  The autotuner times candidate
  * configurations on the caller's batch (device CSR arrays as in
  * vsbpp_pack_batch; the outputs are scratch it may overwrite) and installs

@@ -1097,10 +1097,10 @@ int enqueue_core(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const O
 // back to the item's original position.
 //
 // split_ok: the size-class split (small_m) with its second stream pays off
-// for device-resident batches (batched calls, plans and their graphs) and is
-// measured to cost more than it gains for single-instance calls (the serving
-// lanes) and the host-buffer batch call, which pack every system in the large
-// class instead.
+// for batches (batched device calls, plans and their graphs, the host-buffer
+// batch call: config 3's BF pass through the host call 3.65 -> 3.40 ms) and
+// is measured to cost more than it gains for single-instance calls (the
+// serving lanes), which pack their one system in the large class instead.
 int enqueue(const LaunchPlan& lp, Scratch& sc, const BatchView& in, const OutView& out,
             const vsbpp_params& prm, bool plain, cudaStream_t st, bool split_ok = true) {
     if (!lp.presort) return enqueue_core(lp, sc, in, out, prm, plain, st, split_ok);
@@ -1379,7 +1379,7 @@ int vsbpp_pack_batch_host(int64_t N, const int32_t* w_all, const int64_t* w_off,
             return rc;
         BatchView in{N, sc.h_w, sc.hb_woff, 0, sc.h_B, sc.hb_Boff, 0};
         OutView out{sc.h_boi, sc.h_bt, sc.hb_nb, sc.hb_tot, sc.hb_st, nullptr, nullptr, nullptr};
-        if ((rc = enqueue(lp, sc, in, out, prm, false, st, false))) return rc;
+        if ((rc = enqueue(lp, sc, in, out, prm, false, st, true))) return rc;
         if ((rc = hc->to_host(bin_of_item_all, sc.h_boi, sizeof(int32_t) * total_m)) ||
             (rc = hc->to_host(bin_type_all, sc.h_bt, sizeof(int32_t) * total_m)) ||
             (rc = hc->to_host(num_bins, sc.hb_nb, sizeof(int64_t) * N)) ||
