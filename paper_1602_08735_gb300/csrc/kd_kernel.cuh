@@ -33,13 +33,15 @@
 // In the chosen sub-segment (FF, WF) or segment (BF) each lane turns its
 // matching slots into (position, slot) keys, and one warp minimum names the
 // bin with its residual and type.  The chain per item is straight-line
-// arithmetic and warp reductions.  In the BF kernel each slot is stored by
-// the lane that reads it and word q of every presence row by lane q (both
-// bitmaps there run from the top bit down, so a count of leading zeros finds
-// a word's least member), so an item needs no barrier; the other kernels
-// order an item's stores before the next item's reads by __syncwarp.  CTA
-// 1's warp only lends its shared memory: it waits at the closing cluster
-// barrier.
+// arithmetic and warp reductions.  In the FF, BF and WF kernels each slot is
+// stored by the lane that reads it, the maximum of sub-segment G by lane
+// G % 32 and word q of every presence row by lane q (the BF bitmaps run from
+// the top bit down, so a count of leading zeros finds a word's least
+// member), so an item needs no barrier; every segment a system can reach is
+// cleared when it starts.  The RANDOM kernel, whose items mix the three,
+// clears a segment when a bin opens it and orders an item's stores before the
+// next item's reads by __syncwarp.  CTA 1's warp only lends its shared
+// memory: it waits at the closing cluster barrier.
 #pragma once
 
 #include <cooperative_groups.h>
