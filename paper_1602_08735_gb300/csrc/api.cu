@@ -524,7 +524,7 @@ int round4(int64_t x) { return static_cast<int>((x + 3) & ~int64_t(3)); }
 int round128(int64_t x) { return static_cast<int>((x + 127) & ~int64_t(127)); }
 
 // Shared memory of one group: the one-warp kernel's layout where it applies
-// (h1w_ok: the one-warp kernel may be used; not with VSBPP_REMARK3).
+// (h1w_ok: the one-warp kernel may be used).
 int group_bytes(bool wide, int G, int slot_cap, int chunk, int bf_index, bool h1w_ok) {
     if (h1w_ok && !wide && G == 1 && h1w_supported(slot_cap)) return h1w_bytes(slot_cap, bf_index);
     return h1_group_bytes(slot_cap, chunk, wide ? 8 : 4, G, bf_index);
@@ -678,9 +678,9 @@ int build_plan(const vsbpp_params& prm, int64_t max_m, int64_t N, LaunchPlan& lp
     lp.mode = {VSBPP_H1, 0, 0};
     // the BF residual index is laid out when BF items can occur
     const int bfi = prm.criterion == VSBPP_BF || prm.criterion == VSBPP_RANDOM;
-    // Remark 3 runs in the group kernel (the one-warp kernel has no per-type
-    // count of bins below half)
-    const bool h1w_ok = !lp.remark3;
+    // the one-warp kernel takes every option (Remark 3 in kernels of their
+    // own: a lane-distributed count of each type's bins below half)
+    const bool h1w_ok = true;
     int rc = make_shape(lp.full, false, lp.cfg.large_warps, 1, max_m, chunk, smax, di.sms, 32752, 200, bfi,
                         prm.criterion, false, h1w_ok);
     if (rc != VSBPP_OK) return rc;

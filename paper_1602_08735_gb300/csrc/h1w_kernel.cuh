@@ -148,7 +148,7 @@ struct H1Warp {
     // (B_1 <= 1023), else the full scan.  The item step is straight-line code:
     // the chosen segment's quad is read whether or not a bin fits, and the
     // fitting / new-bin cases are merged by selects.
-    template <bool IDX, bool W10>
+    template <bool IDX, bool W10, bool R3>
     __device__ __forceinline__ bool run(const H1Params& p, int64_t i, const int32_t* w, int64_t key0,
                                         uint32_t k, int32_t* raw, int n, uint32_t& L_io,
                                         unsigned long long& fit_tests) const {
@@ -157,6 +157,10 @@ struct H1Warp {
         uint32_t L = L_io;
         const uint32_t cap_bins = static_cast<uint32_t>(p.slot_cap);
         const uint32_t ulane = static_cast<uint32_t>(lane);
+        // R3 (Remark 3's reading of Rule 5): lane t counts the type-t bins
+        // below half their capacity (a pre-opened bin is empty)
+        const uint32_t Bl = R3 ? Bs[ulane] : 0u;
+        uint32_t below = (R3 && L > 0 && ulane < static_cast<uint32_t>(n)) ? 1u : 0u;
 
         uint32_t sm[NS];                 // segment maxima, segment 32q + lane
         uint32_t wb = 0;                 // residuals 32*lane .. 32*lane+31 present, top bit first
@@ -343,7 +347,8 @@ struct H1Warp {
                 Bt = hit ? ((c == kFF ? k2 : k1) & 0xFFFFu) : Bn;
             }
             const uint32_t r_new = r_old - wj;
-            const bool fire = (Bt < 2u * r_old) && (2u * r_new <= Bt);     // Rule 5
+            const bool cross = (Bt < 2u * r_old) && (2u * r_new <= Bt);    // Rule 5
+            const bool fire = R3 ? remark3_divide(below, Bl, !hit, Bt, cross) : cross;
             const uint32_t Lf = hit ? L : L + 1u;      // where a divided-off bin goes
             // every lane writes the same words (a predicated store for the
             // divided-off bin: no branch, nothing written when it does not
@@ -463,7 +468,7 @@ struct H1Warp {
     // would outgrow the slots, or whose bins so far, extrapolated to all k
     // items, pass them, is appended to spill_list2 and packed in global
     // memory.
-    template <bool IDX>
+    template <bool IDX, bool R3>
     __device__ __forceinline__ bool run16(const H1Params& p, int64_t i, const int32_t* w, uint32_t k,
                                           int32_t* raw, int n, uint32_t& L_io,
                                           unsigned long long& fit_tests, uint32_t* r16) const {
@@ -472,6 +477,8 @@ struct H1Warp {
         uint32_t L = L_io;
         constexpr uint32_t cap_bins = kH16Slots;
         const uint32_t ulane = static_cast<uint32_t>(lane);
+        const uint32_t Bl = R3 ? Bs[ulane] : 0u;      // Remark 3 as in run()
+        uint32_t below = (R3 && L > 0 && ulane < static_cast<uint32_t>(n)) ? 1u : 0u;
 
         uint32_t sm[kNS16];                 // segment maxima, segment 32q + lane
         uint32_t wb = 0;                 // residuals 32*lane .. 32*lane+31 present
@@ -601,7 +608,8 @@ struct H1Warp {
             const uint32_t r_old = hit ? (c == kBF ? R : (k1 >> 8) & 0xFFu) : Bn;
             const uint32_t Bt = hit ? k1 & 0xFFu : Bn;
             const uint32_t r_new = r_old - wj;
-            const bool fire = (Bt < 2u * r_old) && (2u * r_new <= Bt);     // Rule 5
+            const bool cross = (Bt < 2u * r_old) && (2u * r_new <= Bt);    // Rule 5
+            const bool fire = R3 ? remark3_divide(below, Bl, !hit, Bt, cross) : cross;
             const uint32_t Lf = hit ? L : L + 1u;
             s16[b] = static_cast<uint16_t>((r_new << 8) | Bt);
             if (fire) s16[Lf] = static_cast<uint16_t>((Bt << 8) | Bt);
@@ -666,7 +674,9 @@ struct H1Warp {
 
 // One warp per membrane system; blockDim.x / 32 warps per block, each with
 // p.group_bytes of shared memory.  Direct mode only (no sublists).
-template <int NS, int CRIT>
+// R3: Rule 5 with Remark 3's per-type condition (VSBPP_REMARK3), a kernel of
+// its own so that the other kernels' item step is unchanged.
+template <int NS, int CRIT, bool R3>
 __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = static_cast<int>(threadIdx.x) & 31;
@@ -762,14 +772,14 @@ __global__ void __launch_bounds__(512, 1) h1w_pack_kernel(const H1Params p) {
         const uint32_t k32 = static_cast<uint32_t>(k);
         if (use16) {
             if constexpr (NS == 8)
-                done = g.template run16<H1Warp<NS, CRIT>::kBFItems>(p, i, w, k32, raw, n, L, fit_tests, rows16);
+                done = g.template run16<H1Warp<NS, CRIT>::kBFItems, R3>(p, i, w, k32, raw, n, L, fit_tests, rows16);
         } else if constexpr (H1Warp<NS, CRIT>::kBFItems) {
-            done = use_idx ? g.template run<true, true>(p, i, w, 0, k32, raw, n, L, fit_tests)
-                 : w10     ? g.template run<false, true>(p, i, w, 0, k32, raw, n, L, fit_tests)
-                           : g.template run<false, false>(p, i, w, 0, k32, raw, n, L, fit_tests);
+            done = use_idx ? g.template run<true, true, R3>(p, i, w, 0, k32, raw, n, L, fit_tests)
+                 : w10     ? g.template run<false, true, R3>(p, i, w, 0, k32, raw, n, L, fit_tests)
+                           : g.template run<false, false, R3>(p, i, w, 0, k32, raw, n, L, fit_tests);
         } else {
-            done = w10 ? g.template run<false, true>(p, i, w, 0, k32, raw, n, L, fit_tests)
-                       : g.template run<false, false>(p, i, w, 0, k32, raw, n, L, fit_tests);
+            done = w10 ? g.template run<false, true, R3>(p, i, w, 0, k32, raw, n, L, fit_tests)
+                       : g.template run<false, false, R3>(p, i, w, 0, k32, raw, n, L, fit_tests);
         }
         if (!done) continue;                 // spilled: a full-size launch repacks it
 

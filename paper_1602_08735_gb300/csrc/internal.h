@@ -40,6 +40,7 @@ int h1_blocks_per_sm(bool wide, int G, int groups, int smem);
 // One-warp first-heuristic kernel (narrow slots, direct mode, at most
 // 32768 bins per system): `groups` warps per block, each a system at a time.
 int h1w_supported(int slot_cap);
+const void* h1w_r3_kernel_for(int slot_cap, int criterion);   // h1w_r3.cu: the VSBPP_REMARK3 kernels
 int h1w_bytes(int slot_cap, int bf_index);
 cudaError_t h1w_launch(const H1Params& p, int groups, int grid, int smem, cudaStream_t st);
 int h1w_blocks_per_sm(int slot_cap, int criterion, int groups, int smem);
