@@ -113,7 +113,9 @@ typedef struct {
                                fits).  1: literal Rule 2, one empty bin of every type,
                                types in order, before the first item.                    */
     int32_t  flags;         /* VSBPP_REMARK3 | VSBPP_PRESORT, or 0; other bits: EINVAL.
-                               VSBPP_REMARK3 with sublists of 7..12 items: EINVAL         */
+                               Both apply to every heuristic and sublist size (the
+                               exhaustive 7..12-item search included); VSBPP_REMARK3
+                               with max_open > 0: EINVAL                                 */
     uint64_t seed;          /* used by VSBPP_RANDOM only                                 */
     int64_t  max_open;      /* 0: no bound (the method as the paper states it).  K >= 1:
                                the bounded-space variant of Section 1's FF / BF / WF
