@@ -65,7 +65,9 @@
  *       0=FF, 1=BF, 2=WF; key = item index (first heuristic) or
  *       (sublist*720 + rank)*8 + step (second heuristic, s <= 6), or
  *       (sublist*12! + rank)*16 + step (s = 7..12, the exhaustive search of
- *       Section 7's parallel comparison).  SplitMix64 is the
+ *       Section 7's parallel comparison), s being the run's sublist size
+ *       whatever the length of a particular sublist (an instance shorter
+ *       than s, or its last sublist).  SplitMix64 is the
  *       published generator of Steele, Lea & Flood (OOPSLA 2014): the
  *       key-th output (0-based) of the stream seeded with `seed`.
  */
@@ -449,6 +451,9 @@ int oracle_pack_ext(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
         s = sublist_size == 0 ? m : sublist_size;        /* default: one system */
     else
         s = sublist_size == 0 ? OR_H2_DEFAULT_SUBLIST : sublist_size;
+    /* G12: the RANDOM key layout follows the run's sublist size, also for an
+     * instance shorter than it */
+    const int64_t s_run = s;
     if (s > m)
         s = m;
 
@@ -505,7 +510,7 @@ int oracle_pack_ext(const int32_t *w, int64_t m, const int32_t *B, int32_t n,
                     seq[q] = w[a + perm[q]];
                     crit[q] = criterion == OR_RANDOM
                                   ? or_random_criterion(
-                                        seed, s <= 6
+                                        seed, s_run <= 6
                                                   ? (uint64_t)((g * 720 + rank) * 8 + q)
                                                   : ((uint64_t)g * OR_FACT12 + (uint64_t)rank) * 16u + (uint64_t)q)
                                   : criterion;

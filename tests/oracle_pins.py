@@ -324,35 +324,47 @@ def pin_h2_random_key(lib, seed=17):
     for K in (0, 1, 7, 5765, 2**40 + 3):
         assert splitmix64_py(int(d["seed"]), K) == splitmix64_py((int(d["seed"]) + K * SM_GAMMA) & _M64, 0)
     rng = np.random.default_rng(seed)
-    for s, trials in ((3, 6), (5, 3), (6, 2), (7, 1)):
-        for t in range(trials):
+
+    def check(s, m, w=None, B=None, run_seed=None):
+        if w is None:
             n = int(rng.integers(2, 4))
             B = sorted(rng.choice(np.arange(6, 40), size=n, replace=False).tolist(), reverse=True)
-            m = 2 * s + int(rng.integers(1, 3))             # two full sublists and a partial one
             w = rng.integers(1, B[0] + 1, size=m).tolist()
             run_seed = int(rng.integers(0, 2**63))
-            want_boi, want_bt, total, off = [], [], 0, 0
-            for g, a in enumerate(range(0, m, s)):
-                sub = w[a:a + s]
-                k = len(sub)
-                best = None
-                for rank, perm in enumerate(itertools.permutations(range(k))):
-                    seed_p = (run_seed + h2_random_key_base(g, rank, s) * SM_GAMMA) & _M64
-                    r = lib.pack([sub[x] for x in perm], B, 1, 3, 0, 0, seed_p)
-                    if best is None or r.total < best[0]:
-                        item_bin = [0] * k
-                        for q, x in enumerate(perm):
-                            item_bin[x] = int(r.bin_of_item[q])
-                        best = (r.total, item_bin, r.bin_type.tolist(), r.num_bins)
-                want_boi += [off + b for b in best[1]]
-                want_bt += best[2]
-                total += best[0]
-                off += best[3]
-            r2 = lib.pack(w, B, 2, 3, s, 0, run_seed)
-            assert r2.status == 0
-            assert r2.bin_of_item.tolist() == want_boi, (s, w, B, run_seed)
-            assert r2.bin_type.tolist() == want_bt, (s, w, B)
-            assert r2.total == total
+        want_boi, want_bt, total, off = [], [], 0, 0
+        for g, a in enumerate(range(0, m, s)):
+            sub = w[a:a + s]
+            k = len(sub)
+            best = None
+            for rank, perm in enumerate(itertools.permutations(range(k))):
+                # the layout is the run's (sublist size s), whatever k is
+                seed_p = (run_seed + h2_random_key_base(g, rank, s) * SM_GAMMA) & _M64
+                r = lib.pack([sub[x] for x in perm], B, 1, 3, 0, 0, seed_p)
+                if best is None or r.total < best[0]:
+                    item_bin = [0] * k
+                    for q, x in enumerate(perm):
+                        item_bin[x] = int(r.bin_of_item[q])
+                    best = (r.total, item_bin, r.bin_type.tolist(), r.num_bins)
+            want_boi += [off + b for b in best[1]]
+            want_bt += best[2]
+            total += best[0]
+            off += best[3]
+        r2 = lib.pack(w, B, 2, 3, s, 0, run_seed)
+        assert r2.status == 0
+        assert r2.bin_of_item.tolist() == want_boi, (s, w, B, run_seed)
+        assert r2.bin_type.tolist() == want_bt, (s, w, B)
+        assert r2.total == total
+
+    for s, trials in ((3, 6), (5, 3), (6, 2), (7, 1)):
+        for t in range(trials):
+            check(s, 2 * s + int(rng.integers(1, 3)))       # two full sublists and a partial one
+    # an instance shorter than the run's sublist size is one sublist that
+    # still takes the run's layout (7..12: the exhaustive search's keys)
+    for s, m in ((7, 5), (7, 6), (8, 4)):
+        check(s, m)
+    # five items over five capacities, where the two layouts' criteria lead
+    # to different cheapest packings
+    check(7, 5, [38, 22, 33, 26, 32], [58, 57, 36, 28, 5], 6)
 
 
 def pin_invariants(lib, trials=200, seed=15):

@@ -82,7 +82,8 @@ MUTANTS = {
     "h2_random_key_stride_7": ("? (uint64_t)((g * 720 + rank) * 8 + q)", "? (uint64_t)((g * 720 + rank) * 7 + q)"),
     "h2_random_key_rank_dropped": ("? (uint64_t)((g * 720 + rank) * 8 + q)", "? (uint64_t)((g * 720) * 8 + q)"),
     "h2x_random_key_stride_8": ("+ (uint64_t)rank) * 16u + (uint64_t)q)", "+ (uint64_t)rank) * 8u + (uint64_t)q)"),
-    "h2_random_layout_switch_off_by_one": ("seed, s <= 6\n", "seed, s <= 5\n"),
+    "h2_random_layout_switch_off_by_one": ("seed, s_run <= 6\n", "seed, s_run <= 5\n"),
+    "h2_random_layout_by_instance_length": ("seed, s_run <= 6\n", "seed, s <= 6\n"),
     "bounded_newest_closes": ("        or_close_at(active, na, 0);", "        or_close_at(active, na, *na - 1);"),
     "bounded_limit_off_by_one": ("    if (*na >= max_open)\n        or_close_at", "    if (*na > max_open)\n        or_close_at"),
     "bounded_full_bins_stay_open": ("            if (after == cap)              /* completely filled: the bin closes */\n                or_close_at(active, &na, chosen_at);",
