@@ -126,6 +126,17 @@ def test_presort_paths(preopen):
                     f"ps global memory c{crit}")
 
 
+def test_presort_exhaustive_search():
+    """The pre-sort ahead of the exhaustive 7..8-item permutation search
+    (Remark 3 alongside), element by element against the oracle."""
+    b = _fuzz(55, 6, 16, cap_hi=60)
+    for s in (7, 8):
+        for crit in CRITS:
+            for flags in (PS, PS | R3):
+                assert_same(b, run_batch(b, 2, crit, s, 0, 6, flags=flags), run_oracle(b, 2, crit, s, 0, 6, flags),
+                            f"ps h2x s{s} c{crit} flags{flags}")
+
+
 def test_presort_reports_the_callers_first_offender():
     """Validation runs in the caller's order: a zero weight before a too-heavy
     one is EINVAL, the other way round ETOOBIG (sorting would swap them)."""
