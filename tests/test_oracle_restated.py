@@ -5,9 +5,10 @@ type holding the item when nothing fits, the Rule 5 division when a bin's
 load first reaches half its capacity, reading G7), the first heuristic's
 sublists (reading G1), the second heuristic's lexicographic permutations with
 the cheapest winning at the lowest rank (readings G9-G11), the literal Rule 2
-start (reading G3) and the RANDOM criterion's keys (reading G12), on small
-random instances of every shape the library takes (instances shorter than
-the sublist size included).  This is a restatement of the same readings, not
+start (reading G3), the RANDOM criterion's keys (reading G12), Remark 3
+(reading G7), the bounded-space variant (reading G15) and the pre-sort
+(reading G16), on small random instances of every shape the library takes
+(instances shorter than the sublist size included).  This is a restatement of the same readings, not
 a pin: the pins in oracle_pins.py tie the oracle to values fixed outside it.
 """
 import itertools
@@ -20,49 +21,73 @@ from oracle_pins import splitmix64_py
 F12 = 479001600
 
 
-def run_system(items, crits, B, preopen):
+def run_system(items, crits, B, preopen, remark3=False, K=0):
     """Rules 2-6 on one membrane system: the bin each item goes to and the
-    bins [residual, capacity, type] in creation order."""
+    bins [residual, capacity, type] in creation order.  remark3: a division
+    also needs every bin of the type at half its capacity or more (reading
+    G7).  K > 0: only the K or fewer open bins take part, a bin closes when
+    full, and before a bin is created while K are open the oldest open bin
+    closes (reading G15)."""
     bins = []
+    active = []                                       # open bins in creation order
+
+    def new_bin(t):
+        if K and len(active) >= K:
+            active.pop(0)
+        bins.append([B[t], B[t], t])
+        active.append(len(bins) - 1)
+        return len(bins) - 1
+
     if preopen:
-        for t, c in enumerate(B):
-            bins.append([c, c, t])
+        for t in range(len(B)):
+            new_bin(t)
     raw = []
     for x, c in zip(items, crits):
-        fit = [b for b in range(len(bins)) if bins[b][0] >= x]
+        fit = [b for b in (active if K else range(len(bins))) if bins[b][0] >= x]
         if not fit:
-            t = max(i for i in range(len(B)) if B[i] >= x)     # smallest type holding x
-            bins.append([B[t], B[t], t])
-            b = len(bins) - 1
+            b = new_bin(max(i for i in range(len(B)) if B[i] >= x))   # smallest type holding x
         elif c == 0:
             b = fit[0]
         elif c == 1:
             b = min(fit, key=lambda y: (bins[y][0] - x, y))
         else:
             b = min(fit, key=lambda y: (-bins[y][0], y))
-        old, cap = bins[b][0], bins[b][1]
+        old, cap, t = bins[b]
         new = old - x
         bins[b][0] = new
+        if K and new == 0:
+            active.remove(b)                          # a full bin closes first
         if cap < 2 * old and 2 * new <= cap:          # load first reaches half: Rule 5
-            bins.append([cap, cap, bins[b][2]])
+            if not remark3 or all(2 * (y[1] - y[0]) >= y[1] for y in bins if y[2] == t):
+                new_bin(t)
         raw.append(b)
     return raw, bins
 
 
 def dense_of(bins):
     """Dense ids of the used bins (load > 0) in creation order (reading G8)."""
-    d, k = {}, 0
+    d = {}
     for b in range(len(bins)):
         if bins[b][0] < bins[b][1]:
-            d[b] = k; k += 1
+            d[b] = len(d)
     return d
 
-def brute(w, B, h, crit, s, preopen, seed):
+
+def brute(w, B, h, crit, s, preopen, seed, remark3=False, K=0, presort=False):
     """Every sublist packed as the readings state: (bin of each item, bin
-    types, bins, total)."""
+    types, bins, total).  presort: the list in non-increasing weight order,
+    equal weights in list order, each bin id reported at the item's original
+    position (reading G16)."""
     m = len(w)
     if m == 0:
         return [], [], 0, 0
+    if presort:
+        order = sorted(range(m), key=lambda j: (-w[j], j))
+        boi_s, types, nb, tot = brute([w[j] for j in order], B, h, crit, s, preopen, seed, remark3, K)
+        boi = [0] * m
+        for jj, j in enumerate(order):
+            boi[j] = boi_s[jj]
+        return boi, types, nb, tot
     s_ = (m if s == 0 else s) if h == 1 else (5 if s == 0 else s)
     boi, types, total, off = [0] * m, [], 0, 0
 
@@ -73,7 +98,7 @@ def brute(w, B, h, crit, s, preopen, seed):
         sub = w[a:a + s_]
         k = len(sub)
         if h == 1:
-            raw, bins = run_system(sub, [draw(a + q, crit) for q in range(k)], B, preopen)
+            raw, bins = run_system(sub, [draw(a + q, crit) for q in range(k)], B, preopen, remark3, K)
             d = dense_of(bins)
             for q in range(k):
                 boi[a + q] = off + d[raw[q]]
@@ -84,7 +109,7 @@ def brute(w, B, h, crit, s, preopen, seed):
         best = None
         for rank, perm in enumerate(itertools.permutations(range(k))):
             keys = [((g * 720 + rank) * 8 + q) if s_ <= 6 else ((g * F12 + rank) * 16 + q) for q in range(k)]
-            raw, bins = run_system([sub[x] for x in perm], [draw(kq, crit) for kq in keys], B, preopen)
+            raw, bins = run_system([sub[x] for x in perm], [draw(kq, crit) for kq in keys], B, preopen, remark3)
             d = dense_of(bins)
             tot = sum(bins[b][1] for b in d)
             if best is None or tot < best[0]:
@@ -113,13 +138,17 @@ def test_oracle_equals_restatement():
         s = int(rng.choice([0, 1, 2, 3, 5, 6, 7, 8])) if h == 2 else int(rng.choice([0, 0, 1, 3, 4]))
         if h == 2 and s >= 7:
             preopen = 0            # the exhaustive search starts without pre-opened bins
+        remark3 = bool(rng.integers(0, 2))
+        presort = bool(rng.integers(0, 2))
+        K = int(rng.choice([0, 0, 1, 2, 3, 5])) if (h == 1 and not remark3) else 0
         m = int(rng.integers(0, 9 if (h == 2 and s >= 7) else 13))
         w = rng.integers(1, B[0] + 1, size=m).tolist()
         seed = int(rng.integers(0, 2**40))
-        r = oracle.pack(np.array(w, dtype=np.int32), np.array(B, dtype=np.int32), h, crit,
-                        sublist_size=s, preopen=preopen, seed=seed)
-        boi, types, nb, tot = brute(w, B, h, crit, s, preopen, seed)
+        flags = (oracle.REMARK3 if remark3 else 0) | (oracle.PRESORT if presort else 0)
+        r = oracle.pack(np.array(w, dtype=np.int32), np.array(B, dtype=np.int32), h, crit, s, preopen, seed,
+                        flags, K)
+        boi, types, nb, tot = brute(w, B, h, crit, s, preopen, seed, remark3, K, presort)
         if not (r.status == 0 and r.bin_of_item.tolist() == boi and r.bin_type.tolist() == types
                 and r.num_bins == nb and r.total == tot):
-            bad.append(dict(w=w, B=B, h=h, crit=crit, s=s, preopen=preopen, seed=seed))
+            bad.append(dict(w=w, B=B, h=h, crit=crit, s=s, preopen=preopen, seed=seed, flags=flags, K=K))
     assert not bad, bad[:3]
