@@ -338,17 +338,33 @@ Scratch& scratch_for(cudaStream_t st) {
 struct HostCtx {
     static constexpr size_t kChunk = size_t(8) << 20;
     int dev = -1;
+    bool ready = false;              // every resource below exists
     cudaStream_t st = nullptr;
     void* pin[2] = {nullptr, nullptr};
     cudaEvent_t ev[2] = {nullptr, nullptr};
 
+    // Creates whatever is still missing (a failed earlier attempt is
+    // completed, not taken for done).
     int init() {
-        if (st) return VSBPP_OK;
-        VS_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        for (int k = 0; k < 2; ++k) {
-            VS_TRY(cudaHostAlloc(&pin[k], kChunk, cudaHostAllocDefault));
-            VS_TRY(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
+        if (ready) return VSBPP_OK;
+        if (!st) {
+            cudaStream_t x = nullptr;
+            VS_TRY(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+            st = x;
         }
+        for (int k = 0; k < 2; ++k) {
+            if (!pin[k]) {
+                void* x = nullptr;
+                VS_TRY(cudaHostAlloc(&x, kChunk, cudaHostAllocDefault));
+                pin[k] = x;
+            }
+            if (!ev[k]) {
+                cudaEvent_t x = nullptr;
+                VS_TRY(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+                ev[k] = x;
+            }
+        }
+        ready = true;
         return VSBPP_OK;
     }
     static bool pinned(const void* p) {
